@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Benchmark of the staggered even-odd CG on the paper's lattice size.
+
+Workload: 28^3 x 96 lattice (the MILC fine lattice of Sec. 2), asqtad-form
+operator (fat links 0.6 U_a + 0.4 U_b, Naik links -(1/24) U_c, three
+independent synthetic SU(3) fields U = exp(0.3 i H)), m = 0.0062, Gaussian
+even-site source, tol 1e-10 on the true residual |b - A x| / |b|.
+
+One step = one pass of the whole path: stag_create_ex (eta folding and
+layout packing of both link fields from device-resident inputs),
+stag_cg_solve (Fig. 1 to the tolerance, true FP64 residual, restarts) and
+stag_destroy.  The link fields (2 x 1.2 GB in, 4.9 GB packed) are far larger
+than the 126 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time to |r|/|b|≤1e-10 at 28³×96 vs FP64 plain CG; Dslash GB/s vs HBM peak"
+UNIT = "s"
+DIMS = (28, 28, 28, 96)
+MASS = 0.0062
+TOL = 1e-10
+MAX_ITER = 40000  # far above the expected count; bounds a run that fails to converge
+FALLBACK_HBM_GBS = 6800.0
+# Fig. 1 iterations of this system (28^3 x 96 asqtad-form, m = 0.0062, source
+# seed 0, tol 1e-10), used only to scale the oracle's per-A-application time
+# to a whole solve in the reference leg, which cannot afford to run it.
+REFERENCE_ITERS = None
+PAPER_CONTEXT = "35 GFLOP/s FP64 CG on one GPU of a GTX 295 (Sec. 3.4, CUDA 2.3, cc 1.3)"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--arith", choices=["ff", "f64"], default="ff")
+    p.add_argument("--mass", type=float, default=MASS)
+    p.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-f64", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dslash_source_hash():
+    h = hashlib.sha256()
+    for f in ("dslash.cu", "ff.cuh", "stag_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1010_4782_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel_key]
+        if e.get("source_hash") != dslash_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        mhz, max_mhz, reasons = [], None, set()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                max_mhz = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max_mhz,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1010_4782_gb300 import accounting, binding, build, inputs
+
+    world, rank, local = dist_env()
+    dims = tuple(args.dims)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t)
+        return float(t.item())
+
+    build.build()
+    binding.load()
+    fat, lng = inputs.asqtad_form_fields(dims)
+    b = inputs.gaussian_even_source(dims, rank)  # independent replica per rank
+    fat_d = torch.from_numpy(fat).to(dev)
+    lng_d = torch.from_numpy(lng).to(dev)
+    b_d = torch.from_numpy(b).to(dev)
+    x_d = torch.zeros_like(b_d)
+    vh = accounting.half_sites(dims)
+    arith = binding.STAG_ARITH_FF if args.arith == "ff" else binding.STAG_ARITH_F64
+    stream = torch.cuda.current_stream(dev)
+
+    def options(ar, timing):
+        o = binding.stag_default_options()
+        o.arith = ar
+        o.timing = 1 if timing else 0
+        return o
+
+    rec = {"launches": 0, "k_ms": [0.0] * 4, "k_n": [0] * 4, "infos": []}
+
+    def step(fat_in, lng_in, b_in, x_in, ar=arith, timing=True, record=True):
+        h = binding.stag_create_ex(fat_in, lng_in, dims, args.mass, options(ar, timing))
+        try:
+            binding.stag_set_stream(h, stream)
+            if hasattr(x_in, "zero_"):
+                x_in.zero_()
+            else:
+                x_in[...] = 0
+            code, info = binding.stag_cg_solve(h, b_in, x_in, TOL, MAX_ITER)
+            if code != binding.STAG_OK:
+                raise RuntimeError(f"solve failed: status {code}: {binding.stag_last_error(h)}")
+            if record:
+                rec["launches"] += binding.stag_launch_count(h)
+                for k in range(4):
+                    ms, n = binding.stag_kernel_stats(h, k)
+                    rec["k_ms"][k] += ms
+                    rec["k_n"][k] += n
+                rec["infos"].append(info)
+        finally:
+            binding.stag_destroy(h)
+        return info
+
+    # ---- warm-up, then K timed steps (device-resident inputs)
+    for _ in range(args.warmup):
+        step(fat_d, lng_d, b_d, x_d, record=False)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(fat_d, lng_d, b_d, x_d)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    host_s = time.perf_counter() - t0
+    barrier()
+    clock_info = clocks.stop()
+    elapsed_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    total_solves = args.steps * world
+    value = elapsed_s / total_solves
+    infos = rec["infos"]
+    iters = infos[-1]["iters"]
+
+    # ---- dominant kernel: the half-Dslash D_oe (Naik), CUDA events on the library's stream
+    naik = True
+    bytes_per_launch = accounting.compulsory_bytes_per_site(naik) * vh
+    flops_per_launch = accounting.flops_per_site(naik) * vh
+    oe_ms = rec["k_ms"][0] / max(1, rec["k_n"][0])
+    eo_ms = rec["k_ms"][1] / max(1, rec["k_n"][1])
+    achieved = bytes_per_launch / (oe_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    kernel_key = f"dslash_oe_{args.arith}_naik_{'x'.join(map(str, dims))}"
+    roofline = {
+        "bound": "hbm",
+        "achieved": round(achieved, 1),
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": round(achieved / peak, 4),
+        "traffic": recorded_traffic(kernel_key),
+        "kernel": f"half-Dslash D_oe, Naik, {args.arith.upper()} arithmetic ({kernel_key})",
+        "algorithmic_bytes_per_launch": bytes_per_launch,
+        "avg_launch_ms": round(oe_ms, 4),
+        "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+    }
+    k_total = sum(rec["k_ms"])
+    kernel_shares = {binding.KERNEL_NAMES[k]: {"launches": rec["k_n"][k], "ms": round(rec["k_ms"][k], 2),
+                                               "share_of_cg_kernels": round(rec["k_ms"][k] / k_total, 4)}
+                     for k in range(4)}
+    gpu_launches = int(sum_over_ranks(rec["launches"]))
+    solve_ms = statistics.median(i["time_ms"] for i in infos)
+    # paper's convention: Dslash flops only, two half-Dslash per CG iteration
+    gflops = 2 * flops_per_launch * iters / (solve_ms / 1e3) / 1e9
+
+    # ---- end to end: host (pinned) inputs, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        fat_h = torch.from_numpy(fat).pin_memory()
+        lng_h = torch.from_numpy(lng).pin_memory()
+        b_h = torch.from_numpy(b).pin_memory()
+        x_h = torch.zeros_like(b_h).pin_memory()
+        step(fat_h, lng_h, b_h, x_h, timing=False, record=False)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(fat_h, lng_h, b_h, x_h, timing=False, record=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+        vec_bytes = b_h.numel() * 16
+        e2e = {"value": round(e2e_s / total_solves, 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(fat_h.numel() * 16 + lng_h.numel() * 16 + 2 * vec_bytes),
+               "d2h_bytes_per_step": int(vec_bytes)}
+        del fat_h, lng_h
+
+    # ---- plain FP64 GPU CG (native FP64 FMA Dirac kernels) for comparison
+    f64 = None
+    if not args.no_f64 and arith != binding.STAG_ARITH_F64:
+        info64 = step(fat_d, lng_d, b_d, x_d, ar=binding.STAG_ARITH_F64, timing=False, record=False)
+        f64 = {"value": round(info64["time_ms"] / 1e3, 4), "unit": UNIT, "iters": info64["iters"],
+               "true_rel_residual": info64["true_rel_residual"],
+               "speedup_of_headline": round(info64["time_ms"] / solve_ms, 3)}
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(fat, lng, b, dims, args.mass, iters, infos[-1]["restarts"])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": round(value, 4),
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(elapsed_s / args.steps * 1e3, 2),
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "ff64" if arith == binding.STAG_ARITH_FF else "f64",
+            "data": "synthetic (seeded SU(3) fields exp(0.3 i H), Gaussian source)",
+            "config": {
+                "workload": f"staggered even-odd CG, asqtad-form (fat 0.6U_a+0.4U_b, Naik -U_c/24), "
+                            f"{'x'.join(map(str, dims))}, m={args.mass}, tol={TOL}",
+                "lattice": list(dims),
+                "mass": args.mass,
+                "tol": TOL,
+                "step": "stag_create_ex + stag_cg_solve + stag_destroy (device-resident inputs)",
+                "l2": "inputs (2.4 GB AoS links, 4.9 GB packed) larger than L2; no flush",
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            },
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
+            "clocks": clock_info,
+            "solve": {"iters": iters, "restarts": infos[-1]["restarts"],
+                      "true_rel_residual": infos[-1]["true_rel_residual"],
+                      "solve_ms_median": round(solve_ms, 2), "host_s_timed": round(host_s, 3)},
+            "gflops_paper_convention": round(gflops, 1),
+            "dslash_eo_cg_avg_ms": round(eo_ms, 4),
+            "kernel_shares": kernel_shares,
+            "fp64_plain_cg": f64,
+            "paper_context": PAPER_CONTEXT,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(fat, lng, b, dims, mass, iters, restarts):
+    """Oracle: initial residual + one Fig. 1 iteration (two A applications) at full size."""
+    import numpy as np
+
+    import oracle
+
+    op = oracle.Operator(fat, lng, mass, dims)
+    t0 = time.perf_counter()
+    oracle.cg_fig1(op.apply_A, b, np.zeros_like(b), TOL, 1)
+    dt = time.perf_counter() - t0
+    per_a = dt / 2
+    n_a = 1 + iters + (restarts + 1)
+    return {"value": round(per_a * n_a, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"numpy FP64 oracle (single thread), cg_fig1 on the full {'x'.join(map(str, dims))} "
+                      f"system: initial residual + 1 iteration = 2 A applications in {dt:.1f} s; "
+                      f"value = time per A application x the {n_a} A applications of the GPU solve",
+            "per_A_application_s": round(per_a, 2)}
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1010_4782_gb300 import inputs
+
+    dims = tuple(args.dims)
+    fat, lng = inputs.asqtad_form_fields(dims)
+    b = inputs.gaussian_even_source(dims, 0)
+    op = oracle.Operator(fat, lng, args.mass, dims)
+    for _ in range(args.warmup):
+        op.apply_A(b)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        op.apply_A(b)
+    per_a = (time.perf_counter() - t0) / args.steps
+    if REFERENCE_ITERS is not None:
+        n_a = REFERENCE_ITERS + 2
+        value = per_a * n_a
+        sample = (f"numpy FP64 oracle (single thread): {args.steps} timed A applications on the full "
+                  f"{'x'.join(map(str, dims))} system; value = time per A application x {n_a} "
+                  f"A applications of a solve ({REFERENCE_ITERS} Fig. 1 iterations)")
+    else:
+        value = per_a
+        sample = "time per A application (iteration count of the solve not recorded)"
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(per_a * 1e3, 1),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded SU(3) fields exp(0.3 i H), Gaussian source)",
+        "config": {"workload": f"staggered even-odd CG, asqtad-form, {'x'.join(map(str, dims))}, "
+                               f"m={args.mass}, tol={TOL}", "lattice": list(dims)},
+        "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * stag.h - C ABI of the GB300 (sm_103a) staggered-fermion even-odd CG library.
+ *
+ * The library solves A x = b on the even sites of a 4-d periodic lattice with
+ *     A = m^2 - D_eo D_oe                      (Sec. 2, Eq. (3) on even sites)
+ *     D chi(x) = sum_mu U_mu(x) chi(x+mu) - U_mu(x-mu)^dag chi(x-mu)
+ *              [+ sum_mu L_mu(x) chi(x+3mu) - L_mu(x-3mu)^dag chi(x-3mu)]
+ *                                              (Sec. 2, Eqs. (4)-(5); Naik term optional)
+ * with the staggered phase eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}) multiplied
+ * into every link by the library (Sec. 2, after Eq. (5)), by conjugate
+ * gradient (Sec. 2, Fig. 1).  D carries no factor 1/2.
+ *
+ * Layouts (all complex numbers are interleaved (re, im) doubles):
+ *   links   [Lt][Lz][Ly][Lx][mu=0..3 = x,y,z,t][3][3]   complex128, row-major 3x3,
+ *           eta NOT folded in.  Size 4*V*9 complex = V*576 bytes.
+ *   vectors [V/2][3] complex128 on the sites of one parity; sites are numbered
+ *           in lexicographic order (x fastest), so the half-lattice index of a
+ *           site is its lexicographic index / 2.  "Even" = (x+y+z+t) even.
+ *
+ * Pointers: every array argument may be host memory or device memory of the
+ * current CUDA device; the library detects which (cudaPointerGetAttributes)
+ * and stages host data through its own device buffers.  Arrays are owned by
+ * the caller and are only accessed during the call.
+ *
+ * Streams: work is ordered after all work already enqueued on the stream set
+ * with stag_set_stream (default: the legacy default stream), and every call
+ * returns only after its work has completed.
+ *
+ * Errors: every call returns a STAG_* status; no C++ exception crosses the
+ * ABI.  stag_last_error gives a message for the last failing call.  A handle
+ * is not thread-safe.
+ */
+#ifndef STAG_H
+#define STAG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    STAG_OK = 0,
+    STAG_ERR_INVALID_ARG = 1,   /* bad pointer, extent, option or non-finite input */
+    STAG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    STAG_ERR_NOT_CONVERGED = 3, /* max_iter or max_restarts reached; x holds the last iterate */
+    STAG_ERR_BREAKDOWN = 4,     /* d^dag A d <= 0 or non-finite inside CG */
+    STAG_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    STAG_ERR_OOM = 6            /* device allocation failed */
+};
+
+/* Arithmetic of the FP64-class Dirac kernels. */
+enum {
+    STAG_ARITH_F64 = 0, /* native FP64 fused multiply-add */
+    STAG_ARITH_FF = 1   /* float-float: each FP64 number held as an unevaluated sum of two
+                           FP32 numbers (8 bytes, like FP64), products and sums formed with
+                           error-free transformations (Dekker 1971; Knuth TAOCP vol. 2);
+                           about 2^-48 relative rounding, FP32 pipelines */
+};
+
+/* Kernel ids for stag_kernel_stats. */
+enum {
+    STAG_KERNEL_DSLASH_OE = 0,  /* t = D_oe d (odd output)                               */
+    STAG_KERNEL_DSLASH_EO = 1,  /* Ad = m^2 d - D_eo t (even output) + partial d^dag A d */
+    STAG_KERNEL_UPDATE_XR = 2,  /* x += alpha d, r -= alpha Ad, partial r^dag r          */
+    STAG_KERNEL_UPDATE_D = 3,   /* d = r + beta d                                        */
+    STAG_KERNEL_COUNT = 4
+};
+
+typedef struct stag_handle stag_handle; /* opaque; owned by the library */
+
+typedef struct {
+    int32_t arith;          /* STAG_ARITH_*, Dirac arithmetic of the CG iteration (default F64) */
+    int32_t check_interval; /* CG iterations between host convergence reads (default 32)     */
+    int32_t max_restarts;   /* restarts of Fig. 1 from the current x when the true residual
+                               exceeds tol (default 5)                                        */
+    int32_t use_graphs;     /* capture check_interval iterations as one CUDA graph (default 1) */
+    int32_t timing;         /* record CUDA events around every CG kernel (default 0);
+                               disables graphs; read with stag_kernel_stats                    */
+    int32_t reserved[3];
+} stag_options;
+
+typedef struct {
+    int32_t iters;            /* CG iterations (all restarts)                              */
+    int32_t restarts;         /* restarts of Fig. 1 after a true-residual check            */
+    int32_t status;           /* the STAG_* status the call returned                       */
+    int32_t reserved;
+    double true_rel_residual; /* |b - A x| / |b|, A applied in native FP64                 */
+    double iter_rel_residual; /* sqrt(delta_new) / |b| of the last Fig. 1 iterate          */
+    double time_ms;           /* wall time of the solve inside the call                     */
+} stag_solve_info;
+
+/* Fill *opt with the defaults.  Returns STAG_ERR_INVALID_ARG if opt is NULL. */
+int stag_default_options(stag_options* opt);
+
+/* Create a handle for the one-hop operator (Sec. 2, Eqs. (3)-(5)).
+ * links: U_mu(x) in the link layout above (host or device), eta not folded;
+ *        copied at create, so the caller may free it afterwards.
+ * dims:  host array {Lx, Ly, Lz, Lt}; every extent even and >= 2, V/2 < 2^31.
+ * mass:  the quark mass m of Eq. (3); must be finite.
+ * On success *out holds a new handle (release with stag_destroy); on error
+ * *out is NULL and the message is available from stag_last_error(NULL). */
+int stag_create(stag_handle** out, const double* links, const int32_t dims[4], double mass);
+
+/* As stag_create, with an optional Naik three-hop field (NULL = one-hop only)
+ * and options (NULL = defaults).  fat plays the role of U in Eq. (5); naik_long
+ * are the three-hop links L_mu(x) from x to x+3mu (eta not folded). */
+int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long,
+                   const int32_t dims[4], double mass, const stag_options* opt);
+
+/* Order the handle's work after the given cudaStream_t (NULL = legacy default stream). */
+int stag_set_stream(stag_handle* h, void* cuda_stream);
+
+/* Change m of Eq. (3); must be finite. */
+int stag_set_mass(stag_handle* h, double mass);
+
+/* Half of D (Sec. 2, Eq. (5)): out = D_{P,1-P} in, i.e. D restricted to output
+ * sites of parity P = out_parity (0 even, 1 odd) acting on a vector of parity
+ * 1-P.  in, out: [V/2][3] complex128, must not overlap.  Native FP64 arithmetic
+ * unless the handle's arith is STAG_ARITH_FF. */
+int stag_dslash(stag_handle* h, int32_t out_parity, const double* in, double* out);
+
+/* out_even = A in_even = m^2 in - D_eo D_oe in (Sec. 2, Eq. (3)).  in, out:
+ * [V/2][3] complex128 on even sites; must not overlap.  Arithmetic as for
+ * stag_dslash. */
+int stag_apply_A(stag_handle* h, const double* in_even, double* out_even);
+
+/* Solve A x = b by CG (Sec. 2, Fig. 1) to |b - A x| / |b| <= tol.
+ * b_even: [V/2][3] source.  x_even: [V/2][3], on entry the initial guess (it
+ * must be initialised, e.g. to zero), on exit the solution.
+ * Fig. 1 runs until delta_new <= tol^2 |b|^2 (Fig. 1's eps^2 delta_0 when the
+ * guess is zero) or max_iter total iterations (max_iter <= 0: N_dim = 3 V/2);
+ * the true residual is then recomputed with native FP64 arithmetic and Fig. 1
+ * restarts from the current x while it exceeds tol (at most max_restarts times).
+ * Returns STAG_OK, STAG_ERR_NOT_CONVERGED (x holds the last iterate) or
+ * STAG_ERR_BREAKDOWN; info (nullable) is filled in every case. */
+int stag_cg_solve(stag_handle* h, const double* b_even, double* x_even, double tol,
+                  int32_t max_iter, stag_solve_info* info);
+
+/* Release the handle and its device memory.  NULL-safe. */
+int stag_destroy(stag_handle* h);
+
+/* Message of the last failing call on h (h = NULL: of the last failing create
+ * on this thread).  Never NULL; valid until the next call on the handle. */
+const char* stag_last_error(const stag_handle* h);
+
+/* Accumulated CUDA-event time and launch count of one CG kernel (STAG_KERNEL_*),
+ * recorded while the handle's timing option is on. */
+int stag_kernel_stats(const stag_handle* h, int32_t kernel, double* total_ms, int64_t* launches);
+
+/* Zero the kernel statistics. */
+int stag_reset_stats(stag_handle* h);
+
+/* Bytes of device memory the handle holds (0 for NULL). */
+int64_t stag_device_bytes(const stag_handle* h);
+
+/* Number of CUDA kernels the handle has launched since it was created (each
+ * replay of a captured graph counts every kernel in it; 0 for NULL). */
+int64_t stag_launch_count(const stag_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STAG_H */

@@ -1,0 +1,51 @@
+"""Byte and flop accounting of the staggered Dirac operator (Sec. 2).
+
+Per output site of one half-Dslash (D restricted to one parity):
+  * the paper's convention (Sec. 2: 1584 bytes and 576 flops per site for
+    D chi(x)): every link and every neighbour vector is read once per
+    output site, plus the output write;
+  * compulsory bytes: each link and each output once, and each input
+    vector once per site (every input site is the neighbour of 8 or 16
+    output sites, so the re-reads are cache hits, not compulsory traffic).
+Flops: a 3x3 complex matrix times a colour vector is 9 complex
+multiplications (6 flops) and 6 complex additions (2 flops) = 66 flops;
+adding it into the site's sum is 6 more, so 72 flops per hop.
+Sizes are those of FP64 (a float-float number occupies the same 8 bytes).
+"""
+from __future__ import annotations
+
+LINK_BYTES_F64 = 9 * 16      # 3x3 complex128
+VECTOR_BYTES_F64 = 3 * 16    # colour vector, complex128
+FLOPS_PER_HOP = 66 + 6
+
+
+def hops(naik: bool) -> int:
+    return 16 if naik else 8
+
+
+def paper_bytes_per_site(naik: bool = False, elem_bytes: int = 8) -> int:
+    """Sec. 2: links + neighbour vectors + output, nothing cached (1584 B one-hop, FP64)."""
+    s = elem_bytes / 8
+    return int(hops(naik) * (LINK_BYTES_F64 + VECTOR_BYTES_F64) * s + VECTOR_BYTES_F64 * s)
+
+
+def compulsory_bytes_per_site(naik: bool = False, elem_bytes: int = 8) -> int:
+    """Each link once, the input vector once, the output once (1248 B one-hop, FP64)."""
+    s = elem_bytes / 8
+    return int(hops(naik) * LINK_BYTES_F64 * s + 2 * VECTOR_BYTES_F64 * s)
+
+
+def flops_per_site(naik: bool = False) -> int:
+    """Sec. 2: 576 flops per site for the one-hop D chi(x)."""
+    return hops(naik) * FLOPS_PER_HOP
+
+
+def half_sites(dims) -> int:
+    lx, ly, lz, lt = dims
+    return lx * ly * lz * lt // 2
+
+
+def dslash_totals(dims, naik: bool = False):
+    """(flops, paper-convention bytes, compulsory bytes) of one half-Dslash over all sites of a parity."""
+    n = half_sites(dims)
+    return n * flops_per_site(naik), n * paper_bytes_per_site(naik), n * compulsory_bytes_per_site(naik)

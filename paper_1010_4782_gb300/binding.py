@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the C ABI in include/stag.h (argument marshalling only).
+
+Functions carry the ABI's names.  Array arguments may be torch tensors (CUDA
+or CPU) or numpy arrays of complex128 (or float64 with a trailing (re, im)
+axis); only their data pointers are passed.  Every computation runs inside
+libstag.so; if the library cannot be loaded the call raises - there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+STAG_OK = 0
+STAG_ERR_INVALID_ARG = 1
+STAG_ERR_CUDA = 2
+STAG_ERR_NOT_CONVERGED = 3
+STAG_ERR_BREAKDOWN = 4
+STAG_ERR_TIMEOUT = 5
+STAG_ERR_OOM = 6
+
+STAG_ARITH_F64 = 0
+STAG_ARITH_FF = 1
+
+STAG_KERNEL_DSLASH_OE = 0
+STAG_KERNEL_DSLASH_EO = 1
+STAG_KERNEL_UPDATE_XR = 2
+STAG_KERNEL_UPDATE_D = 3
+KERNEL_NAMES = ("dslash_oe", "dslash_eo_cg", "update_xr", "update_d")
+
+EXPORTED = (
+    "stag_default_options",
+    "stag_create",
+    "stag_create_ex",
+    "stag_set_stream",
+    "stag_set_mass",
+    "stag_dslash",
+    "stag_apply_A",
+    "stag_cg_solve",
+    "stag_destroy",
+    "stag_last_error",
+    "stag_kernel_stats",
+    "stag_reset_stats",
+    "stag_device_bytes",
+    "stag_launch_count",
+)
+
+
+class stag_options(ctypes.Structure):
+    _fields_ = [
+        ("arith", ctypes.c_int32),
+        ("check_interval", ctypes.c_int32),
+        ("max_restarts", ctypes.c_int32),
+        ("use_graphs", ctypes.c_int32),
+        ("timing", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
+    ]
+
+
+class stag_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int32),
+        ("restarts", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("true_rel_residual", ctypes.c_double),
+        ("iter_rel_residual", ctypes.c_double),
+        ("time_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class StagError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"stag error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB
+
+
+def load(path: str | None = None):
+    """Load libstag.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build the CUDA library first (paper_1010_4782_gb300.build)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    H = ctypes.c_void_p
+    i32 = ctypes.c_int32
+    d = ctypes.c_double
+    lib.stag_default_options.argtypes = [ctypes.POINTER(stag_options)]
+    lib.stag_create.argtypes = [ctypes.POINTER(H), P, ctypes.POINTER(i32), d]
+    lib.stag_create_ex.argtypes = [ctypes.POINTER(H), P, P, ctypes.POINTER(i32), d,
+                                   ctypes.POINTER(stag_options)]
+    lib.stag_set_stream.argtypes = [H, P]
+    lib.stag_set_mass.argtypes = [H, d]
+    lib.stag_dslash.argtypes = [H, i32, P, P]
+    lib.stag_apply_A.argtypes = [H, P, P]
+    lib.stag_cg_solve.argtypes = [H, P, P, d, i32, ctypes.POINTER(stag_solve_info)]
+    lib.stag_destroy.argtypes = [H]
+    lib.stag_last_error.argtypes = [H]
+    lib.stag_last_error.restype = ctypes.c_char_p
+    lib.stag_kernel_stats.argtypes = [H, i32, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
+    lib.stag_reset_stats.argtypes = [H]
+    lib.stag_device_bytes.argtypes = [H]
+    lib.stag_device_bytes.restype = ctypes.c_int64
+    lib.stag_launch_count.argtypes = [H]
+    lib.stag_launch_count.restype = ctypes.c_int64
+    for name in EXPORTED:
+        if name not in ("stag_last_error", "stag_device_bytes", "stag_launch_count"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Data pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(code, h=None):
+    if code != STAG_OK:
+        raise StagError(code, stag_last_error(h))
+
+
+def stag_default_options() -> stag_options:
+    o = stag_options()
+    _check(load().stag_default_options(ctypes.byref(o)))
+    return o
+
+
+def stag_create(links, dims, mass):
+    h = ctypes.c_void_p()
+    dd = (ctypes.c_int32 * 4)(*[int(v) for v in dims])
+    _check(load().stag_create(ctypes.byref(h), _ptr(links), dd, float(mass)))
+    return h
+
+
+def stag_create_ex(fat, naik_long, dims, mass, options: stag_options | None = None):
+    h = ctypes.c_void_p()
+    dd = (ctypes.c_int32 * 4)(*[int(v) for v in dims])
+    opt = ctypes.byref(options) if options is not None else None
+    _check(load().stag_create_ex(ctypes.byref(h), _ptr(fat), _ptr(naik_long), dd, float(mass), opt))
+    return h
+
+
+def stag_set_stream(h, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(load().stag_set_stream(h, ctypes.c_void_p(raw or 0)), h)
+
+
+def stag_set_mass(h, mass):
+    _check(load().stag_set_mass(h, float(mass)), h)
+
+
+def stag_dslash(h, out_parity, inp, out):
+    _check(load().stag_dslash(h, int(out_parity), _ptr(inp), _ptr(out)), h)
+
+
+def stag_apply_A(h, inp, out):
+    _check(load().stag_apply_A(h, _ptr(inp), _ptr(out)), h)
+
+
+def stag_cg_solve(h, b, x, tol, max_iter=0, raise_on_error=True):
+    """Returns (status, info dict)."""
+    info = stag_solve_info()
+    code = load().stag_cg_solve(h, _ptr(b), _ptr(x), float(tol), int(max_iter), ctypes.byref(info))
+    if raise_on_error and code not in (STAG_OK, STAG_ERR_NOT_CONVERGED):
+        _check(code, h)
+    return code, info.as_dict()
+
+
+def stag_destroy(h):
+    if h is not None:
+        load().stag_destroy(h)
+
+
+def stag_last_error(h=None) -> str:
+    return load().stag_last_error(h).decode()
+
+
+def stag_kernel_stats(h, kernel):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().stag_kernel_stats(h, int(kernel), ctypes.byref(ms), ctypes.byref(n)), h)
+    return ms.value, n.value
+
+
+def stag_reset_stats(h):
+    _check(load().stag_reset_stats(h), h)
+
+
+def stag_device_bytes(h) -> int:
+    return int(load().stag_device_bytes(h))
+
+
+def stag_launch_count(h) -> int:
+    return int(load().stag_launch_count(h))
+
+
+class Handle:
+    """Owns one stag_handle; closes it on exit."""
+
+    def __init__(self, fat, dims, mass, naik_long=None, options: stag_options | None = None,
+                 stream=None):
+        self.h = stag_create_ex(fat, naik_long, dims, mass, options)
+        self.dims = tuple(int(v) for v in dims)
+        if stream is not None:
+            stag_set_stream(self.h, stream)
+
+    def close(self):
+        if self.h is not None:
+            stag_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,220 @@
+// blas.cu - the vector steps of CG (Sec. 2, Fig. 1), fused so that each
+// vector is streamed once per step and every scalar stays on the device:
+//
+//   cg_init      r = b - A x, d = r, delta_new = delta_0 = r^dag r
+//   cg_update_xr x += alpha d, r -= alpha A d, delta_old = delta_new,
+//                delta_new = r^dag r, beta = delta_new / delta_old
+//   cg_update_d  d = r + beta d
+//
+// alpha comes from the Dirac epilogue (dslash.cu).  Reductions are
+// deterministic: a fixed shuffle tree per block, then the last block to
+// finish sums the per-block partials in block order.  The loop condition of
+// Fig. 1 (i < N_dim and delta_new > eps^2 delta_0) is evaluated by that last
+// block and stored in scal->done; every kernel of the iteration returns at
+// once when it is set, so a captured block of iterations stops exactly
+// where Fig. 1 stops.
+#include "ff.cuh"
+#include "stag_kernels.h"
+
+namespace stag {
+
+__device__ __forceinline__ double2 load_d(const void* d, bool ff, size_t idx) {
+    if (ff) return ff_to_complex(__ldg(reinterpret_cast<const float4*>(d) + idx));
+    return __ldg(reinterpret_cast<const double2*>(d) + idx);
+}
+
+__device__ __forceinline__ void store_d(void* d, bool ff, size_t idx, double2 v) {
+    if (ff)
+        reinterpret_cast<float4*>(d)[idx] = ff_from_complex(v);
+    else
+        reinterpret_cast<double2*>(d)[idx] = v;
+}
+
+__device__ __forceinline__ void set_done(CgScalars* sc) {
+    sc->done = (sc->delta_new <= sc->threshold || sc->iter >= sc->max_iter) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kBlock) cg_init_kernel(Geom g, const double2* __restrict__ b,
+                                                         const double2* __restrict__ ad,
+                                                         double2* __restrict__ r, void* d, bool d_ff,
+                                                         CgScalars* scal, double* partials) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    double acc = 0.0;
+    if (i < g.vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t k = c * vs + i;
+            const double2 bb = b[k], aa = ad[k];
+            const double2 rr = make_double2(bb.x - aa.x, bb.y - aa.y);
+            r[k] = rr;
+            store_d(d, d_ff, k, rr);
+            acc = fma(rr.x, rr.x, acc);
+            acc = fma(rr.y, rr.y, acc);
+        }
+    }
+    double total;
+    if (grid_sum_last_block<kBlock>(acc, partials, &scal->counter, &total)) {
+        if (threadIdx.x == 0) {
+            scal->delta_new = total;
+            scal->delta_old = total;
+            scal->status = 0;
+            set_done(scal);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) cg_update_xr_kernel(Geom g, double2* __restrict__ x,
+                                                              double2* __restrict__ r, const void* d,
+                                                              bool d_ff, const double2* __restrict__ ad,
+                                                              CgScalars* scal, double* partials) {
+    if (scal->done) return;
+    const double alpha = scal->alpha;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    double acc = 0.0;
+    if (i < g.vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t k = c * vs + i;
+            const double2 dd = load_d(d, d_ff, k);
+            double2 xx = x[k];
+            xx.x = fma(alpha, dd.x, xx.x);
+            xx.y = fma(alpha, dd.y, xx.y);
+            x[k] = xx;
+            const double2 aa = __ldg(ad + k);
+            double2 rr = r[k];
+            rr.x = fma(-alpha, aa.x, rr.x);
+            rr.y = fma(-alpha, aa.y, rr.y);
+            r[k] = rr;
+            acc = fma(rr.x, rr.x, acc);
+            acc = fma(rr.y, rr.y, acc);
+        }
+    }
+    double total;
+    if (grid_sum_last_block<kBlock>(acc, partials, &scal->counter, &total)) {
+        if (threadIdx.x == 0) {
+            scal->delta_old = scal->delta_new;
+            scal->delta_new = total;
+            scal->beta = total / scal->delta_old;
+            scal->iter += 1;
+            if (!isfinite(total)) {
+                scal->status = 4;
+                scal->done = 1;
+            } else {
+                set_done(scal);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) cg_update_d_kernel(Geom g, const double2* __restrict__ r,
+                                                             void* d, bool d_ff, CgScalars* scal) {
+    if (scal->done) return;
+    const double beta = scal->beta;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const size_t k = c * vs + i;
+        const double2 rr = __ldg(r + k);
+        const double2 dd = load_d(d, d_ff, k);
+        store_d(d, d_ff, k, make_double2(fma(beta, dd.x, rr.x), fma(beta, dd.y, rr.y)));
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) norm2_diff_kernel(Geom g, const double2* __restrict__ a,
+                                                            const double2* __restrict__ b,
+                                                            CgScalars* scal, double* partials) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    double acc = 0.0;
+    if (i < g.vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t k = c * vs + i;
+            double2 v = a[k];
+            if (b) {
+                const double2 w = b[k];
+                v.x -= w.x;
+                v.y -= w.y;
+            }
+            acc = fma(v.x, v.x, acc);
+            acc = fma(v.y, v.y, acc);
+        }
+    }
+    double total;
+    if (grid_sum_last_block<kBlock>(acc, partials, &scal->counter, &total)) {
+        if (threadIdx.x == 0) scal->red_out = total;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) to_ff_kernel(Geom g, const double2* __restrict__ in,
+                                                       float4* __restrict__ out) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vs) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c * vs + i] = ff_from_complex(in[c * vs + i]);
+}
+
+__global__ void __launch_bounds__(kBlock) from_ff_kernel(Geom g, const float4* __restrict__ in,
+                                                         double2* __restrict__ out) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vs) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c * vs + i] = ff_to_complex(in[c * vs + i]);
+}
+
+void launch_cg_init(const Geom& g, const double2* b, const double2* ad, double2* r, void* d,
+                    bool d_ff, CgScalars* scal, double* partials, cudaStream_t s) {
+    cg_init_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, b, ad, r, d, d_ff, scal, partials);
+}
+
+void launch_cg_update_xr(const Geom& g, double2* x, double2* r, const void* d, bool d_ff,
+                         const double2* ad, CgScalars* scal, double* partials, cudaStream_t s) {
+    cg_update_xr_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, x, r, d, d_ff, ad, scal, partials);
+}
+
+void launch_cg_update_d(const Geom& g, const double2* r, void* d, bool d_ff, CgScalars* scal,
+                        cudaStream_t s) {
+    cg_update_d_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, r, d, d_ff, scal);
+}
+
+void launch_norm2_diff(const Geom& g, const double2* a, const double2* b, CgScalars* scal,
+                       double* partials, cudaStream_t s) {
+    norm2_diff_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, a, b, scal, partials);
+}
+
+void launch_to_ff(const Geom& g, const double2* in, float4* out, cudaStream_t s) {
+    to_ff_kernel<<<blocks_for(g.vs), kBlock, 0, s>>>(g, in, out);
+}
+
+void launch_from_ff(const Geom& g, const float4* in, double2* out, cudaStream_t s) {
+    from_ff_kernel<<<blocks_for(g.vs), kBlock, 0, s>>>(g, in, out);
+}
+
+}  // namespace stag
+
+namespace stag {
+
+// Start of one run of Fig. 1: clear the counters and set the loop bounds.
+__global__ void cg_reset_kernel(CgScalars* scal, double threshold, double m2, long long max_iter) {
+    scal->threshold = threshold;
+    scal->m2 = m2;
+    scal->iter = 0;
+    scal->max_iter = max_iter;
+    scal->done = 0;
+    scal->status = 0;
+    scal->alpha = 0.0;
+    scal->beta = 0.0;
+}
+
+void launch_cg_reset(CgScalars* scal, double threshold, double m2, long long max_iter,
+                     cudaStream_t s) {
+    cg_reset_kernel<<<1, 1, 0, s>>>(scal, threshold, m2, max_iter);
+}
+
+}  // namespace stag

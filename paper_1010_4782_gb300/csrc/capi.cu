@@ -1,0 +1,626 @@
+// capi.cu - the C ABI (include/stag.h): handle, argument checks, host/device
+// staging, and the CG driver of Sec. 2, Fig. 1.
+//
+// The driver keeps alpha, beta and delta on the device (the paper's CUBLAS
+// dot returned a scalar to the host every step).  It enqueues blocks of
+// check_interval iterations - captured once as a CUDA graph - and reads the
+// CG state back only between blocks.  After Fig. 1 stops, the true residual
+// b - A x is recomputed with native FP64 arithmetic and Fig. 1 restarts from
+// the current x while it exceeds tol.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/stag.h"
+#include "stag_kernels.h"
+
+using namespace stag;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct Fail {
+    int code;
+};
+
+struct KernelStat {
+    double ms = 0.0;
+    long long launches = 0;
+};
+
+}  // namespace
+
+struct stag_handle {
+    Geom g{};
+    int device = 0;
+    double mass = 0.0;
+    bool naik = false;
+    stag_options opt{};
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev_in = nullptr;
+    // links
+    double2* fat64 = nullptr;
+    double2* lng64 = nullptr;
+    float4* fatff = nullptr;
+    float4* lngff = nullptr;
+    // vectors: 16 bytes per complex, [3][vs]
+    double2 *x = nullptr, *r = nullptr, *ad = nullptr, *b = nullptr;
+    void* d = nullptr;   // CG direction (F64 or FF)
+    void* t = nullptr;   // odd-parity intermediate (F64 or FF)
+    void* u = nullptr;   // scratch even vector (F64 or FF)
+    double* io_a = nullptr;  // ABI-layout staging [vh][3] complex
+    double* io_b = nullptr;
+    // reductions
+    double* partials = nullptr;
+    CgScalars* scal = nullptr;
+    CgScalars* scal_host = nullptr;  // pinned
+    // graphs
+    cudaGraphExec_t graph = nullptr;
+    // timing
+    std::vector<cudaEvent_t> events;
+    KernelStat stats[STAG_KERNEL_COUNT];
+    long long device_bytes = 0;
+    long long launches = 0;  // kernels launched by this handle (graph replays counted per kernel)
+    std::string err = "no error";
+};
+
+namespace {
+
+void fail(stag_handle* h, int code, const std::string& msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    throw Fail{code};
+}
+
+void cuda_check(stag_handle* h, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    const int code = (e == cudaErrorMemoryAllocation) ? STAG_ERR_OOM : STAG_ERR_CUDA;
+    fail(h, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void launch_check(stag_handle* h, const char* what) { cuda_check(h, cudaGetLastError(), what); }
+
+template <class T>
+T* dev_alloc(stag_handle* h, size_t bytes, const char* what) {
+    void* p = nullptr;
+    cuda_check(h, cudaMalloc(&p, bytes), what);
+    h->device_bytes += (long long)bytes;
+    cudaError_t e = cudaMemsetAsync(p, 0, bytes, h->s);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        cuda_check(h, e, what);
+    }
+    return static_cast<T*>(p);
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+size_t vec_bytes(const Geom& g) { return (size_t)3 * g.vs * sizeof(double2); }
+size_t abi_vec_bytes(const Geom& g) { return (size_t)3 * g.vh * sizeof(double2); }
+size_t link_bytes(const Geom& g) { return (size_t)2 * 4 * 9 * g.vs * sizeof(double2); }
+
+// Is p device-accessible memory of the handle's device?
+bool is_device_ptr(stag_handle* h, const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        if (a.type == cudaMemoryTypeDevice && a.device != h->device)
+            fail(h, STAG_ERR_INVALID_ARG, "device pointer belongs to another device");
+        return true;
+    }
+    return false;
+}
+
+// Device view of an ABI input vector (staged into `stage` when on the host).
+const double* input_vec(stag_handle* h, const double* p, double* stage) {
+    if (is_device_ptr(h, p)) return p;
+    cuda_check(h, cudaMemcpyAsync(stage, p, abi_vec_bytes(h->g), cudaMemcpyHostToDevice, h->s),
+               "copy vector to device");
+    return stage;
+}
+
+void begin_call(stag_handle* h) {
+    cuda_check(h, cudaSetDevice(h->device), "cudaSetDevice");
+    cuda_check(h, cudaEventRecord(h->ev_in, h->user_stream), "cudaEventRecord");
+    cuda_check(h, cudaStreamWaitEvent(h->s, h->ev_in, 0), "cudaStreamWaitEvent");
+}
+
+void end_call(stag_handle* h) { cuda_check(h, cudaStreamSynchronize(h->s), "cudaStreamSynchronize"); }
+
+bool use_ff(const stag_handle* h) { return h->opt.arith == STAG_ARITH_FF; }
+
+LinkSet links(const stag_handle* h) {
+    return LinkSet{h->fat64, h->lng64, h->fatff, h->lngff};
+}
+
+// out = m2 * in - D_eo D_oe in on internal F64 vectors, native FP64; uses h->t.
+void apply_A_f64(stag_handle* h, const double2* in, double2* out) {
+    const LinkSet L = links(h);
+    launch_dslash_f64(h->g, 1, L, in, reinterpret_cast<double2*>(h->t), EPI_PLAIN, nullptr, 0.0,
+                      nullptr, nullptr, h->s);
+    launch_dslash_f64(h->g, 0, L, reinterpret_cast<const double2*>(h->t), out, EPI_AXPY, in,
+                      h->mass * h->mass, nullptr, nullptr, h->s);
+    h->launches += 2;
+    launch_check(h, "apply_A (F64)");
+}
+
+double read_red_out(stag_handle* h) {
+    cuda_check(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->s),
+               "read CG state");
+    end_call(h);
+    return h->scal_host->red_out;
+}
+
+void read_state(stag_handle* h) {
+    cuda_check(h, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, h->s),
+               "read CG state");
+    end_call(h);
+}
+
+// One CG iteration (Fig. 1 loop body): four kernels.
+void enqueue_iteration(stag_handle* h, cudaEvent_t* ev, bool count) {
+    const Geom& g = h->g;
+    const LinkSet L = links(h);
+    const bool ff = use_ff(h);
+    auto mark = [&](int k) {
+        if (ev) cudaEventRecord(ev[k], h->s);
+    };
+    mark(0);
+    if (ff)
+        launch_dslash_ff(g, 1, L, reinterpret_cast<const float4*>(h->d), h->t, EPI_PLAIN, nullptr, 0.0,
+                         h->scal, h->partials, h->s);
+    else
+        launch_dslash_f64(g, 1, L, reinterpret_cast<const double2*>(h->d),
+                          reinterpret_cast<double2*>(h->t), EPI_PLAIN, nullptr, 0.0, h->scal,
+                          h->partials, h->s);
+    mark(1);
+    if (ff)
+        launch_dslash_ff(g, 0, L, reinterpret_cast<const float4*>(h->t), h->ad, EPI_CG,
+                         reinterpret_cast<const float4*>(h->d), 0.0, h->scal, h->partials, h->s);
+    else
+        launch_dslash_f64(g, 0, L, reinterpret_cast<const double2*>(h->t), h->ad, EPI_CG,
+                          reinterpret_cast<const double2*>(h->d), 0.0, h->scal, h->partials, h->s);
+    mark(2);
+    launch_cg_update_xr(g, h->x, h->r, h->d, ff, h->ad, h->scal, h->partials, h->s);
+    mark(3);
+    launch_cg_update_d(g, h->r, h->d, ff, h->scal, h->s);
+    mark(4);
+    if (count) h->launches += 4;
+}
+
+void ensure_graph(stag_handle* h) {
+    if (h->graph) return;
+    cudaGraph_t graph = nullptr;
+    cuda_check(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    for (int k = 0; k < h->opt.check_interval; ++k) enqueue_iteration(h, nullptr, false);
+    cudaError_t e = cudaStreamEndCapture(h->s, &graph);
+    cuda_check(h, e, "end capture");
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    cuda_check(h, e, "graph instantiate");
+}
+
+// Runs Fig. 1 from the state prepared by cg_init until scal->done.
+void run_fig1(stag_handle* h) {
+    const int K = h->opt.check_interval;
+    const bool timing = h->opt.timing != 0;
+    const bool graphs = h->opt.use_graphs != 0 && !timing;
+    if (timing && h->events.size() < (size_t)(5 * K)) {
+        for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+        h->events.assign(5 * K, nullptr);
+        for (auto& e : h->events) cuda_check(h, cudaEventCreate(&e), "cudaEventCreate");
+    }
+    if (graphs) ensure_graph(h);
+    read_state(h);
+    while (!h->scal_host->done) {
+        const long long iter_before = h->scal_host->iter;
+        if (graphs) {
+            cuda_check(h, cudaGraphLaunch(h->graph, h->s), "cudaGraphLaunch");
+            h->launches += 4LL * K;
+        } else {
+            for (int k = 0; k < K; ++k) enqueue_iteration(h, timing ? &h->events[5 * k] : nullptr, true);
+            launch_check(h, "CG iteration");
+        }
+        read_state(h);
+        if (timing) {
+            const long long active = h->scal_host->iter - iter_before;
+            for (long long k = 0; k < active && k < K; ++k) {
+                const bool last_done = (k == active - 1) && h->scal_host->done;
+                for (int j = 0; j < 4; ++j) {
+                    if (j == 3 && last_done) continue;  // d update skipped after the last step
+                    float ms = 0.f;
+                    cuda_check(h, cudaEventElapsedTime(&ms, h->events[5 * k + j], h->events[5 * k + j + 1]),
+                               "cudaEventElapsedTime");
+                    h->stats[j].ms += ms;
+                    h->stats[j].launches += 1;
+                }
+            }
+        }
+    }
+}
+
+void destroy_handle(stag_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->s) cudaStreamSynchronize(h->s);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    dev_free(h->fat64);
+    dev_free(h->lng64);
+    dev_free(h->fatff);
+    dev_free(h->lngff);
+    dev_free(h->x);
+    dev_free(h->r);
+    dev_free(h->ad);
+    dev_free(h->b);
+    dev_free(h->d);
+    dev_free(h->t);
+    dev_free(h->u);
+    dev_free(h->io_a);
+    dev_free(h->io_b);
+    dev_free(h->partials);
+    dev_free(h->scal);
+    if (h->scal_host) cudaFreeHost(h->scal_host);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->s) cudaStreamDestroy(h->s);
+    delete h;
+}
+
+void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* soaff) {
+    const size_t aos_bytes = (size_t)2 * h->g.vh * 4 * 9 * sizeof(double2);
+    const double* src = links_in;
+    void* stage = nullptr;
+    if (!is_device_ptr(h, links_in)) {
+        cuda_check(h, cudaMalloc(&stage, aos_bytes), "allocate link staging buffer");
+        cudaError_t e = cudaMemcpyAsync(stage, links_in, aos_bytes, cudaMemcpyHostToDevice, h->s);
+        if (e != cudaSuccess) {
+            cudaFree(stage);
+            cuda_check(h, e, "copy links to device");
+        }
+        src = static_cast<const double*>(stage);
+    }
+    launch_pack_links(h->g, src, soa64, soaff, h->s);
+    h->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (stage) {
+        cudaError_t e2 = cudaStreamSynchronize(h->s);
+        cudaFree(stage);
+        if (e == cudaSuccess) e = e2;
+    }
+    cuda_check(h, e, "pack links");
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int stag_default_options(stag_options* opt) {
+    if (!opt) return STAG_ERR_INVALID_ARG;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->arith = STAG_ARITH_F64;
+    opt->check_interval = 32;
+    opt->max_restarts = 5;
+    opt->use_graphs = 1;
+    opt->timing = 0;
+    return STAG_OK;
+}
+
+int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long,
+                   const int32_t dims[4], double mass, const stag_options* opt) {
+    if (out) *out = nullptr;
+    stag_handle* h = nullptr;
+    try {
+        if (!out) fail(nullptr, STAG_ERR_INVALID_ARG, "out is NULL");
+        if (!fat) fail(nullptr, STAG_ERR_INVALID_ARG, "links pointer is NULL");
+        if (!dims) fail(nullptr, STAG_ERR_INVALID_ARG, "dims is NULL");
+        long long V = 1;
+        for (int k = 0; k < 4; ++k) {
+            if (dims[k] < 2 || dims[k] % 2)
+                fail(nullptr, STAG_ERR_INVALID_ARG,
+                     "every lattice extent must be even and >= 2 (got " + std::to_string(dims[k]) + ")");
+            V *= dims[k];
+        }
+        if (V / 2 >= (1LL << 31) - 64)
+            fail(nullptr, STAG_ERR_INVALID_ARG, "lattice too large (V/2 must be < 2^31)");
+        if (!std::isfinite(mass)) fail(nullptr, STAG_ERR_INVALID_ARG, "mass must be finite");
+        stag_options o;
+        stag_default_options(&o);
+        if (opt) o = *opt;
+        if (o.arith != STAG_ARITH_F64 && o.arith != STAG_ARITH_FF)
+            fail(nullptr, STAG_ERR_INVALID_ARG, "unknown arith option");
+        if (o.check_interval < 1 || o.check_interval > 4096)
+            fail(nullptr, STAG_ERR_INVALID_ARG, "check_interval must be in [1, 4096]");
+        if (o.max_restarts < 0) fail(nullptr, STAG_ERR_INVALID_ARG, "max_restarts must be >= 0");
+
+        h = new stag_handle();
+        h->opt = o;
+        h->mass = mass;
+        h->naik = naik_long != nullptr;
+        Geom& g = h->g;
+        g.lx = dims[0];
+        g.ly = dims[1];
+        g.lz = dims[2];
+        g.lt = dims[3];
+        g.lxh = g.lx / 2;
+        g.vh = (int)(V / 2);
+        g.vs = (int)(((V / 2) + 63) / 64 * 64);
+        for (int k = 0; k < 4; ++k) g.hop3[k] = 3 % dims[k];
+        if (blocks_for(g.vs) > kMaxPartials) fail(h, STAG_ERR_INVALID_ARG, "lattice too large");
+
+        cuda_check(h, cudaGetDevice(&h->device), "cudaGetDevice");
+        cuda_check(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "cudaStreamCreate");
+        cuda_check(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "cudaEventCreate");
+        begin_call(h);
+
+        const bool ff = use_ff(h);
+        h->fat64 = dev_alloc<double2>(h, link_bytes(g), "allocate links");
+        if (ff) h->fatff = dev_alloc<float4>(h, link_bytes(g), "allocate FF links");
+        if (h->naik) {
+            h->lng64 = dev_alloc<double2>(h, link_bytes(g), "allocate Naik links");
+            if (ff) h->lngff = dev_alloc<float4>(h, link_bytes(g), "allocate FF Naik links");
+        }
+        const size_t vb = vec_bytes(g);
+        h->x = dev_alloc<double2>(h, vb, "allocate x");
+        h->r = dev_alloc<double2>(h, vb, "allocate r");
+        h->ad = dev_alloc<double2>(h, vb, "allocate Ad");
+        h->b = dev_alloc<double2>(h, vb, "allocate b");
+        h->d = dev_alloc<void>(h, vb, "allocate d");
+        h->t = dev_alloc<void>(h, vb, "allocate t");
+        h->u = dev_alloc<void>(h, vb, "allocate u");
+        h->io_a = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
+        h->io_b = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
+        h->partials = dev_alloc<double>(h, sizeof(double) * (size_t)blocks_for(g.vs), "allocate partials");
+        h->scal = dev_alloc<CgScalars>(h, sizeof(CgScalars), "allocate CG state");
+        cuda_check(h, cudaMallocHost(reinterpret_cast<void**>(&h->scal_host), sizeof(CgScalars)),
+                   "allocate pinned CG state");
+        std::memset(h->scal_host, 0, sizeof(CgScalars));
+
+        pack_field(h, fat, h->fat64, h->fatff);
+        if (h->naik) pack_field(h, naik_long, h->lng64, h->lngff);
+        end_call(h);
+        *out = h;
+        return STAG_OK;
+    } catch (const Fail& f) {
+        if (h) {
+            g_create_error = h->err;
+            destroy_handle(h);
+        }
+        return f.code;
+    } catch (const std::bad_alloc&) {
+        g_create_error = "host allocation failed";
+        destroy_handle(h);
+        return STAG_ERR_OOM;
+    } catch (...) {
+        g_create_error = "unexpected exception";
+        destroy_handle(h);
+        return STAG_ERR_CUDA;
+    }
+}
+
+int stag_create(stag_handle** out, const double* links, const int32_t dims[4], double mass) {
+    return stag_create_ex(out, links, nullptr, dims, mass, nullptr);
+}
+
+int stag_set_stream(stag_handle* h, void* cuda_stream) {
+    if (!h) return STAG_ERR_INVALID_ARG;
+    h->user_stream = static_cast<cudaStream_t>(cuda_stream);
+    return STAG_OK;
+}
+
+int stag_set_mass(stag_handle* h, double mass) {
+    if (!h) return STAG_ERR_INVALID_ARG;
+    if (!std::isfinite(mass)) {
+        h->err = "mass must be finite";
+        return STAG_ERR_INVALID_ARG;
+    }
+    h->mass = mass;
+    return STAG_OK;
+}
+
+int stag_dslash(stag_handle* h, int32_t out_parity, const double* in, double* out) {
+    if (!h) return STAG_ERR_INVALID_ARG;
+    try {
+        if (!in || !out) fail(h, STAG_ERR_INVALID_ARG, "NULL vector");
+        if (out_parity != 0 && out_parity != 1) fail(h, STAG_ERR_INVALID_ARG, "out_parity must be 0 or 1");
+        if (in == out) fail(h, STAG_ERR_INVALID_ARG, "in and out must not overlap");
+        begin_call(h);
+        const Geom& g = h->g;
+        const bool out_dev = is_device_ptr(h, out);
+        const double* src = input_vec(h, in, h->io_a);
+        launch_pack_vec(g, src, h->x, h->s);
+        if (use_ff(h)) {
+            float4* in_ff = reinterpret_cast<float4*>(h->u);
+            launch_to_ff(g, h->x, in_ff, h->s);
+            launch_dslash_ff(g, out_parity, links(h), in_ff, h->t, EPI_PLAIN, nullptr, 0.0, nullptr,
+                             nullptr, h->s);
+            launch_from_ff(g, reinterpret_cast<const float4*>(h->t), h->ad, h->s);
+            h->launches += 3;
+        } else {
+            launch_dslash_f64(g, out_parity, links(h), h->x, h->ad, EPI_PLAIN, nullptr, 0.0, nullptr,
+                              nullptr, h->s);
+            h->launches += 1;
+        }
+        double* dst = out_dev ? out : h->io_b;
+        launch_unpack_vec(g, h->ad, dst, h->s);
+        h->launches += 2;
+        launch_check(h, "dslash");
+        if (!out_dev)
+            cuda_check(h, cudaMemcpyAsync(out, h->io_b, abi_vec_bytes(g), cudaMemcpyDeviceToHost, h->s),
+                       "copy result to host");
+        end_call(h);
+        return STAG_OK;
+    } catch (const Fail& f) {
+        return f.code;
+    } catch (...) {
+        h->err = "unexpected exception";
+        return STAG_ERR_CUDA;
+    }
+}
+
+int stag_apply_A(stag_handle* h, const double* in_even, double* out_even) {
+    if (!h) return STAG_ERR_INVALID_ARG;
+    try {
+        if (!in_even || !out_even) fail(h, STAG_ERR_INVALID_ARG, "NULL vector");
+        if (in_even == out_even) fail(h, STAG_ERR_INVALID_ARG, "in and out must not overlap");
+        begin_call(h);
+        const Geom& g = h->g;
+        const bool out_dev = is_device_ptr(h, out_even);
+        const double* src = input_vec(h, in_even, h->io_a);
+        launch_pack_vec(g, src, h->x, h->s);
+        const double m2 = h->mass * h->mass;
+        if (use_ff(h)) {
+            float4* in_ff = reinterpret_cast<float4*>(h->u);
+            launch_to_ff(g, h->x, in_ff, h->s);
+            launch_dslash_ff(g, 1, links(h), in_ff, h->t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
+            launch_dslash_ff(g, 0, links(h), reinterpret_cast<const float4*>(h->t), h->ad, EPI_AXPY, in_ff,
+                             m2, nullptr, nullptr, h->s);
+            h->launches += 3;
+        } else {
+            apply_A_f64(h, h->x, h->ad);
+        }
+        double* dst = out_dev ? out_even : h->io_b;
+        launch_unpack_vec(g, h->ad, dst, h->s);
+        h->launches += 2;
+        launch_check(h, "apply_A");
+        if (!out_dev)
+            cuda_check(h, cudaMemcpyAsync(out_even, h->io_b, abi_vec_bytes(g), cudaMemcpyDeviceToHost, h->s),
+                       "copy result to host");
+        end_call(h);
+        return STAG_OK;
+    } catch (const Fail& f) {
+        return f.code;
+    } catch (...) {
+        h->err = "unexpected exception";
+        return STAG_ERR_CUDA;
+    }
+}
+
+int stag_cg_solve(stag_handle* h, const double* b_even, double* x_even, double tol, int32_t max_iter,
+                  stag_solve_info* info) {
+    if (!h) return STAG_ERR_INVALID_ARG;
+    stag_solve_info inf{};
+    int status = STAG_OK;
+    auto t0 = std::chrono::steady_clock::now();
+    try {
+        if (!b_even || !x_even) fail(h, STAG_ERR_INVALID_ARG, "NULL vector");
+        if (b_even == x_even) fail(h, STAG_ERR_INVALID_ARG, "b and x must not overlap");
+        if (!(tol > 0.0) || !std::isfinite(tol)) fail(h, STAG_ERR_INVALID_ARG, "tol must be positive and finite");
+        begin_call(h);
+        const Geom& g = h->g;
+        const bool x_dev = is_device_ptr(h, x_even);
+        const double* bsrc = input_vec(h, b_even, h->io_a);
+        launch_pack_vec(g, bsrc, h->b, h->s);
+        const double* xsrc = input_vec(h, x_even, h->io_b);
+        launch_pack_vec(g, xsrc, h->x, h->s);
+        launch_norm2_diff(g, h->b, nullptr, h->scal, h->partials, h->s);
+        h->launches += 3;
+        launch_check(h, "norm of b");
+        const double bnorm2 = read_red_out(h);
+        if (!std::isfinite(bnorm2)) fail(h, STAG_ERR_INVALID_ARG, "source has non-finite entries");
+        const long long n_dim = 3LL * g.vh;
+        const long long max_it = max_iter > 0 ? (long long)max_iter : n_dim;
+        double rel = 0.0;
+        if (bnorm2 == 0.0) {
+            cuda_check(h, cudaMemsetAsync(h->x, 0, vec_bytes(g), h->s), "zero x");
+        } else {
+            const double threshold = tol * tol * bnorm2;
+            const double m2 = h->mass * h->mass;
+            const bool ff = use_ff(h);
+            apply_A_f64(h, h->x, h->ad);  // A x for r = b - A x
+            long long iters = 0;
+            int restarts = 0;
+            while (true) {
+                launch_cg_reset(h->scal, threshold, m2, max_it - iters, h->s);
+                launch_cg_init(g, h->b, h->ad, h->r, h->d, ff, h->scal, h->partials, h->s);
+                h->launches += 2;
+                launch_check(h, "CG init");
+                run_fig1(h);
+                iters += h->scal_host->iter;
+                inf.iter_rel_residual = std::sqrt(h->scal_host->delta_new / bnorm2);
+                const bool breakdown = h->scal_host->status != 0;
+                // true residual with native FP64 arithmetic
+                apply_A_f64(h, h->x, h->ad);
+                launch_norm2_diff(g, h->b, h->ad, h->scal, h->partials, h->s);
+                h->launches += 1;
+                launch_check(h, "true residual");
+                rel = std::sqrt(read_red_out(h) / bnorm2);
+                if (breakdown) {
+                    status = STAG_ERR_BREAKDOWN;
+                    h->err = "CG breakdown: d^dag A d <= 0 or non-finite";
+                    break;
+                }
+                if (rel <= tol) break;
+                if (iters >= max_it || restarts >= h->opt.max_restarts) {
+                    status = STAG_ERR_NOT_CONVERGED;
+                    h->err = "not converged: true residual " + std::to_string(rel) + " after " +
+                             std::to_string(iters) + " iterations";
+                    break;
+                }
+                ++restarts;
+            }
+            inf.iters = (int32_t)iters;
+            inf.restarts = restarts;
+        }
+        inf.true_rel_residual = rel;
+        double* dst = x_dev ? x_even : h->io_b;
+        launch_unpack_vec(g, h->x, dst, h->s);
+        h->launches += 1;
+        launch_check(h, "unpack x");
+        if (!x_dev)
+            cuda_check(h, cudaMemcpyAsync(x_even, h->io_b, abi_vec_bytes(g), cudaMemcpyDeviceToHost, h->s),
+                       "copy x to host");
+        end_call(h);
+    } catch (const Fail& f) {
+        status = f.code;
+    } catch (...) {
+        h->err = "unexpected exception";
+        status = STAG_ERR_CUDA;
+    }
+    inf.status = status;
+    inf.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return status;
+}
+
+int stag_destroy(stag_handle* h) {
+    destroy_handle(h);
+    return STAG_OK;
+}
+
+const char* stag_last_error(const stag_handle* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int stag_kernel_stats(const stag_handle* h, int32_t kernel, double* total_ms, int64_t* launches) {
+    if (!h || kernel < 0 || kernel >= STAG_KERNEL_COUNT) return STAG_ERR_INVALID_ARG;
+    if (total_ms) *total_ms = h->stats[kernel].ms;
+    if (launches) *launches = h->stats[kernel].launches;
+    return STAG_OK;
+}
+
+int stag_reset_stats(stag_handle* h) {
+    if (!h) return STAG_ERR_INVALID_ARG;
+    for (auto& s : h->stats) s = KernelStat{};
+    return STAG_OK;
+}
+
+int64_t stag_device_bytes(const stag_handle* h) { return h ? h->device_bytes : 0; }
+
+int64_t stag_launch_count(const stag_handle* h) { return h ? h->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// dslash.cu - half of the staggered Dirac operator on one parity
+// (Sec. 2, Eqs. (4)-(5), plus the optional Naik three-hop term):
+//
+//   out(y) = sum_mu  U_mu(y) in(y+mu) - U_mu(y-mu)^dag in(y-mu)
+//          [+ sum_mu L_mu(y) in(y+3mu) - L_mu(y-3mu)^dag in(y-3mu)]
+//
+// for every site y of the output parity P, with eta folded into the links.
+// Forward links are read at y (parity P), backward links at the neighbour
+// (parity 1-P), so each half-Dslash streams every link of the field exactly
+// once.  One thread per output site; links and vectors are structure-of-
+// arrays with the site index fastest (Sec. 3.1: consecutive threads read
+// consecutive 16-byte words).  Each 3x3 product is accumulated straight into
+// the output registers (Sec. 3.4, Eq. (smallreg)).  The neighbour vectors
+// (8 or 16 reads of each input site) are served by L1/L2: a 28^3 x 96
+// half-lattice FP64 vector is 50.6 MB, well inside the 126 MB L2.
+//
+// Two arithmetics share the kernel body: native FP64 FMA (F64) and
+// float-float on the FP32 pipelines (FF, see ff.cuh).
+//
+// Epilogues (used by A = m^2 - D_eo D_oe, Eq. (3)):
+//   EPI_PLAIN  out = D in
+//   EPI_AXPY   out = m2 * src - D in                      (out in FP64)
+//   EPI_CG     as EPI_AXPY with m2 from the CG state, plus the grid-wide
+//              Re(src^dag out) = d^dag A d; the last block forms
+//              alpha = delta_new / d^dag A d (Fig. 1) on the device.
+#include "ff.cuh"
+#include "stag_kernels.h"
+
+namespace stag {
+
+// ------------------------------------------------------------ arithmetics
+struct ArithF64 {
+    using T = double2;
+    struct Acc {
+        double2 c[3];
+    };
+    static __device__ __forceinline__ void zero(Acc& a) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) a.c[r] = make_double2(0.0, 0.0);
+    }
+    // a_r += u * v
+    static __device__ __forceinline__ void mac(Acc& a, int r, T u, T v) { cmac(a.c[r], u, v); }
+    // a_r -= conj(u) * v
+    static __device__ __forceinline__ void msc(Acc& a, int r, T u, T v) { cmsc_conj(a.c[r], u, v); }
+    static __device__ __forceinline__ double2 to_f64(const Acc& a, int r) { return a.c[r]; }
+    static __device__ __forceinline__ double2 val_f64(T v) { return v; }
+    static __device__ __forceinline__ T store_val(const Acc& a, int r) { return a.c[r]; }
+};
+
+struct ArithFF {
+    using T = float4;
+    struct Acc {
+        FFAcc re[3], im[3];
+    };
+    static __device__ __forceinline__ void zero(Acc& a) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) a.re[r] = a.im[r] = ff_zero();
+    }
+    static __device__ __forceinline__ void mac(Acc& a, int r, T u, T v) { ff_cmac(a.re[r], a.im[r], u, v); }
+    static __device__ __forceinline__ void msc(Acc& a, int r, T u, T v) {
+        ff_cmsc_conj(a.re[r], a.im[r], u, v);
+    }
+    static __device__ __forceinline__ double2 to_f64(const Acc& a, int r) {
+        return make_double2(ff_acc_to_double(a.re[r]), ff_acc_to_double(a.im[r]));
+    }
+    static __device__ __forceinline__ double2 val_f64(T v) { return ff_to_complex(v); }
+    static __device__ __forceinline__ T store_val(const Acc& a, int r) {
+        const float2 re = ff_result(a.re[r]);
+        const float2 im = ff_result(a.im[r]);
+        return make_float4(re.x, re.y, im.x, im.y);
+    }
+};
+
+template <class A>
+struct DslashParams {
+    Geom g;
+    int P;                     // output parity
+    const typename A::T* fat;  // [2][4][9][vs]
+    const typename A::T* lng;  // [2][4][9][vs] or nullptr
+    const typename A::T* in;   // [3][vs], parity 1-P
+    void* out;                 // [3][vs]: A::T (EPI_PLAIN) or double2
+    const typename A::T* src;  // [3][vs], parity P (EPI_AXPY / EPI_CG)
+    double m2;
+    CgScalars* scal;
+    double* partials;
+};
+
+template <class A>
+__device__ __forceinline__ void hop_fwd(typename A::Acc& acc, const typename A::T* __restrict__ u,
+                                        const typename A::T* __restrict__ in, int nb, size_t vs) {
+    typename A::T v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = __ldg(in + c * vs + nb);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A::mac(acc, r, __ldg(u + (3 * r + c) * vs), v[c]);
+}
+
+template <class A>
+__device__ __forceinline__ void hop_bwd(typename A::Acc& acc, const typename A::T* __restrict__ u,
+                                        const typename A::T* __restrict__ in, int nb, size_t vs) {
+    typename A::T v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = __ldg(in + c * vs + nb);
+    // (U^dag v)_r = sum_c conj(U_cr) v_c
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A::msc(acc, r, __ldg(u + (3 * c + r) * vs), v[c]);
+}
+
+// Half-lattice index of the neighbour of (x,y,z,t) at +-h along mu.
+__device__ __forceinline__ int neighbour(const Geom& g, int x, int y, int z, int t, int mu, int h,
+                                         bool up) {
+    switch (mu) {
+        case 0: x = up ? wrap_up(x, h, g.lx) : wrap_dn(x, h, g.lx); break;
+        case 1: y = up ? wrap_up(y, h, g.ly) : wrap_dn(y, h, g.ly); break;
+        case 2: z = up ? wrap_up(z, h, g.lz) : wrap_dn(z, h, g.lz); break;
+        default: t = up ? wrap_up(t, h, g.lt) : wrap_dn(t, h, g.lt); break;
+    }
+    return site_index(x, y, z, t, g);
+}
+
+template <class A, bool NAIK, int EPI>
+__global__ void __launch_bounds__(kBlock) dslash_kernel(const DslashParams<A> p) {
+    if (EPI == EPI_CG) {
+        if (p.scal->done) return;
+    }
+    const Geom& g = p.g;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    typename A::Acc acc;
+    A::zero(acc);
+    const bool active = i < g.vh;
+    if (active) {
+        int x, y, z, t;
+        site_coords(i, p.P, g, x, y, z, t);
+        const int P = p.P, Q = 1 - p.P;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int f1 = neighbour(g, x, y, z, t, mu, 1, true);
+            const int b1 = neighbour(g, x, y, z, t, mu, 1, false);
+            hop_fwd<A>(acc, p.fat + ((size_t)(P * 4 + mu) * 9) * vs + i, p.in, f1, vs);
+            hop_bwd<A>(acc, p.fat + ((size_t)(Q * 4 + mu) * 9) * vs + b1, p.in, b1, vs);
+            if (NAIK) {
+                const int h = g.hop3[mu];
+                const int f3 = neighbour(g, x, y, z, t, mu, h, true);
+                const int b3 = neighbour(g, x, y, z, t, mu, h, false);
+                hop_fwd<A>(acc, p.lng + ((size_t)(P * 4 + mu) * 9) * vs + i, p.in, f3, vs);
+                hop_bwd<A>(acc, p.lng + ((size_t)(Q * 4 + mu) * 9) * vs + b3, p.in, b3, vs);
+            }
+        }
+    }
+    if (EPI == EPI_PLAIN) {
+        if (active) {
+            typename A::T* out = reinterpret_cast<typename A::T*>(p.out);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) out[r * vs + i] = A::store_val(acc, r);
+        }
+        return;
+    }
+    // out = m2 * src - D in, in FP64
+    const double m2 = (EPI == EPI_CG) ? p.scal->m2 : p.m2;
+    double dot = 0.0;
+    if (active) {
+        double2* out = reinterpret_cast<double2*>(p.out);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const double2 s = A::val_f64(__ldg(p.src + r * vs + i));
+            const double2 d = A::to_f64(acc, r);
+            const double2 o = make_double2(fma(m2, s.x, -d.x), fma(m2, s.y, -d.y));
+            out[r * vs + i] = o;
+            dot = fma(s.x, o.x, dot);
+            dot = fma(s.y, o.y, dot);
+        }
+    }
+    if (EPI == EPI_CG) {
+        double total;
+        if (grid_sum_last_block<kBlock>(dot, p.partials, &p.scal->counter, &total)) {
+            if (threadIdx.x == 0) {
+                CgScalars* sc = p.scal;
+                sc->pAp = total;
+                const double alpha = sc->delta_new / total;
+                if (!(total > 0.0) || !isfinite(alpha)) {
+                    sc->status = 4;  // STAG_ERR_BREAKDOWN
+                    sc->done = 1;
+                    sc->alpha = 0.0;
+                } else {
+                    sc->alpha = alpha;
+                }
+            }
+        }
+    }
+}
+
+template <class A, int EPI>
+static void launch_one(const DslashParams<A>& p, bool naik, cudaStream_t s) {
+    const int blocks = blocks_for(p.g.vh);
+    if (naik)
+        dslash_kernel<A, true, EPI><<<blocks, kBlock, 0, s>>>(p);
+    else
+        dslash_kernel<A, false, EPI><<<blocks, kBlock, 0, s>>>(p);
+}
+
+template <class A>
+static void launch_any(const DslashParams<A>& p, bool naik, Epilogue epi, cudaStream_t s) {
+    switch (epi) {
+        case EPI_PLAIN: launch_one<A, EPI_PLAIN>(p, naik, s); break;
+        case EPI_AXPY: launch_one<A, EPI_AXPY>(p, naik, s); break;
+        default: launch_one<A, EPI_CG>(p, naik, s); break;
+    }
+}
+
+void launch_dslash_f64(const Geom& g, int out_parity, const LinkSet& L, const double2* in,
+                       double2* out, Epilogue epi, const double2* src, double m2,
+                       CgScalars* scal, double* partials, cudaStream_t s) {
+    DslashParams<ArithF64> p{g, out_parity, L.fat64, L.lng64, in, out, src, m2, scal, partials};
+    launch_any(p, L.lng64 != nullptr, epi, s);
+}
+
+void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const float4* in,
+                      void* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
+                      double* partials, cudaStream_t s) {
+    DslashParams<ArithFF> p{g, out_parity, L.fatff, L.lngff, in, out, src, m2, scal, partials};
+    launch_any(p, L.lngff != nullptr, epi, s);
+}
+
+}  // namespace stag

@@ -1,0 +1,81 @@
+// pack.cu - layout kernels: eta folding of the links (Sec. 2, after Eq. (5)),
+// AoS -> structure-of-arrays transposition for coalesced access (Sec. 3.1),
+// and the ABI <-> internal vector conversions.
+#include "stag_kernels.h"
+#include "ff.cuh"
+
+namespace stag {
+
+// One thread per (site, direction).  Reads the 9 complex entries of U_mu(x)
+// (144 contiguous bytes), multiplies by eta_mu(x) and scatters them into the
+// 9 planes of its parity.
+__global__ void __launch_bounds__(kBlock) pack_links_kernel(Geom g, const double2* __restrict__ aos,
+                                                            double2* __restrict__ soa64,
+                                                            float4* __restrict__ soaff) {
+    const long long V = 2LL * g.vh;
+    const long long idx = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (idx >= 4 * V) return;
+    const int mu = (int)(idx / V);
+    const int lex = (int)(idx - (long long)mu * V);
+    const int x = lex % g.lx;
+    int r = lex / g.lx;
+    const int y = r % g.ly;
+    r /= g.ly;
+    const int z = r % g.lz;
+    const int t = r / g.lz;
+    const int P = (x + y + z + t) & 1;
+    const int cb = lex >> 1;
+    int phase_sum = 0;
+    if (mu >= 1) phase_sum += x;
+    if (mu >= 2) phase_sum += y;
+    if (mu >= 3) phase_sum += z;
+    const double eta = (phase_sum & 1) ? -1.0 : 1.0;
+    const double2* src = aos + ((size_t)lex * 4 + mu) * 9;
+    const size_t vs = (size_t)g.vs;
+    const size_t base = ((size_t)(P * 4 + mu) * 9) * vs + cb;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        double2 u = src[k];
+        u.x *= eta;
+        u.y *= eta;
+        soa64[base + k * vs] = u;
+        if (soaff) soaff[base + k * vs] = ff_from_complex(u);
+    }
+}
+
+void launch_pack_links(const Geom& g, const double* aos, double2* soa64, float4* soaff,
+                       cudaStream_t s) {
+    const long long n = 8LL * g.vh;
+    const int blocks = (int)((n + kBlock - 1) / kBlock);
+    pack_links_kernel<<<blocks, kBlock, 0, s>>>(g, reinterpret_cast<const double2*>(aos), soa64,
+                                                soaff);
+}
+
+__global__ void __launch_bounds__(kBlock) pack_vec_kernel(Geom g, const double2* __restrict__ aos,
+                                                          double2* __restrict__ soa) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vs) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        soa[c * vs + i] = i < g.vh ? aos[(size_t)i * 3 + c] : make_double2(0.0, 0.0);
+}
+
+__global__ void __launch_bounds__(kBlock) unpack_vec_kernel(Geom g, const double2* __restrict__ soa,
+                                                            double2* __restrict__ aos) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) aos[(size_t)i * 3 + c] = soa[c * vs + i];
+}
+
+void launch_pack_vec(const Geom& g, const double* aos, double2* soa, cudaStream_t s) {
+    pack_vec_kernel<<<blocks_for(g.vs), kBlock, 0, s>>>(g, reinterpret_cast<const double2*>(aos), soa);
+}
+
+void launch_unpack_vec(const Geom& g, const double2* soa, double* aos, cudaStream_t s) {
+    unpack_vec_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, soa, reinterpret_cast<double2*>(aos));
+}
+
+}  // namespace stag

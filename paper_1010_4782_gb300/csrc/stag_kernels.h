@@ -1,0 +1,61 @@
+// stag_kernels.h - host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "stag_internal.cuh"
+
+namespace stag {
+
+enum Epilogue {
+    EPI_PLAIN = 0,  // out = D_{P,1-P} in
+    EPI_AXPY = 1,   // out = m2 * src - D_{P,1-P} in             (m2 from the launch)
+    EPI_CG = 2      // out = scal->m2 * src - D in, + Re(src^dag out) -> scal->pAp, alpha
+};
+
+struct LinkSet {
+    const double2* fat64;  // F64 SoA links (always present)
+    const double2* lng64;  // nullptr: no Naik term
+    const float4* fatff;   // FF SoA links (nullptr unless FF arithmetic is enabled)
+    const float4* lngff;
+};
+
+// ---- packing (pack.cu)
+// AoS links [Lt][Lz][Ly][Lx][4][3][3] complex128 (device) -> SoA with eta folded.
+void launch_pack_links(const Geom& g, const double* aos, double2* soa64, float4* soaff,
+                       cudaStream_t s);
+// ABI vector [vh][3] complex128 (device) <-> F64 SoA [3][vs]
+void launch_pack_vec(const Geom& g, const double* aos, double2* soa, cudaStream_t s);
+void launch_unpack_vec(const Geom& g, const double2* soa, double* aos, cudaStream_t s);
+
+// ---- Dirac kernels (dslash.cu)
+void launch_dslash_f64(const Geom& g, int out_parity, const LinkSet& L, const double2* in,
+                       double2* out, Epilogue epi, const double2* src, double m2,
+                       CgScalars* scal, double* partials, cudaStream_t s);
+void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const float4* in,
+                      void* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
+                      double* partials, cudaStream_t s);
+
+// ---- CG vector kernels and reductions (blas.cu)
+// start of one run of Fig. 1 (iter = 0, done = 0, threshold, m^2, max_iter)
+void launch_cg_reset(CgScalars* scal, double threshold, double m2, long long max_iter,
+                     cudaStream_t s);
+// r = b - Ad; d = r (stored as F64 or FF); delta_new = delta_0 = |r|^2;
+// scal->done = (delta_new <= threshold) || (iter >= max_iter)
+void launch_cg_init(const Geom& g, const double2* b, const double2* ad, double2* r, void* d,
+                    bool d_ff, CgScalars* scal, double* partials, cudaStream_t s);
+// x += alpha d; r -= alpha Ad; delta_old = delta_new; delta_new = |r|^2; beta; iter++; done
+void launch_cg_update_xr(const Geom& g, double2* x, double2* r, const void* d, bool d_ff,
+                         const double2* ad, CgScalars* scal, double* partials, cudaStream_t s);
+// d = r + beta d
+void launch_cg_update_d(const Geom& g, const double2* r, void* d, bool d_ff, CgScalars* scal,
+                        cudaStream_t s);
+// scal->red_out = |a - b|^2 (b may be nullptr: |a|^2)
+void launch_norm2_diff(const Geom& g, const double2* a, const double2* b, CgScalars* scal,
+                       double* partials, cudaStream_t s);
+// F64 SoA vector -> FF SoA vector
+void launch_to_ff(const Geom& g, const double2* in, float4* out, cudaStream_t s);
+void launch_from_ff(const Geom& g, const float4* in, double2* out, cudaStream_t s);
+
+}  // namespace stag

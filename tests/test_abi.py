@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point that include/stag.h declares, and rejects bad arguments
+before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1010_4782_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def _declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(stag_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("stag_create", "stag_apply_A", "stag_cg_solve", "stag_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(binding.EXPORTED) == set(_declared_functions())
+
+
+def test_default_options(lib):
+    o = binding.stag_default_options()
+    assert o.arith in (binding.STAG_ARITH_F64, binding.STAG_ARITH_FF)
+    assert o.check_interval == 32 and o.max_restarts == 5 and o.use_graphs == 1
+    assert lib.stag_default_options(None) == binding.STAG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 3, 4), (0, 4, 4, 4), (4, 4, 4, -2), (1, 2, 2, 2)])
+def test_create_rejects_bad_extents(lib, dims):
+    links = np.zeros(16, dtype=np.complex128)
+    with pytest.raises(binding.StagError) as e:
+        binding.stag_create(links, dims, 0.1)
+    assert e.value.code == binding.STAG_ERR_INVALID_ARG
+    assert "even" in binding.stag_last_error(None)
+
+
+def test_create_rejects_null_and_nonfinite_mass(lib):
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int32 * 4)(4, 4, 4, 4)
+    assert lib.stag_create(ctypes.byref(h), None, dims, 0.1) == binding.STAG_ERR_INVALID_ARG
+    assert not h.value
+    links = np.zeros(4 ** 4 * 36, dtype=np.complex128)
+    assert lib.stag_create(ctypes.byref(h), links.ctypes.data, dims, float("nan")) == \
+        binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_create(ctypes.byref(h), links.ctypes.data, None, 0.1) == binding.STAG_ERR_INVALID_ARG
+
+
+def test_null_handle_calls(lib):
+    assert lib.stag_destroy(None) == binding.STAG_OK
+    assert lib.stag_apply_A(None, None, None) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_cg_solve(None, None, None, 1e-10, 0, None) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_kernel_stats(None, 0, None, None) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_device_bytes(None) == 0
+    assert isinstance(binding.stag_last_error(None), str)

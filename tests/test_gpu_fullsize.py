@@ -1,0 +1,83 @@
+"""Parity at the paper's lattice size, 28^3 x 96 (Sec. 2), asqtad-form operator.
+
+The whole-lattice oracle is too slow here, so outputs are checked on a
+random sample of sites with the oracle's single-site forms (dslash_at,
+apply_A_at), in the launch configuration the benchmark uses.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1010_4782_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (28, 28, 28, 96)
+N_SAMPLES = 48
+
+
+@pytest.fixture(scope="module")
+def fields():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1010_4782_gb300 import build
+
+    build.build()
+    binding.load()
+    fat, lng = inputs.asqtad_form_fields(DIMS)
+    return fat, lng
+
+
+def _sample_sites(vh, seed):
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(vh, N_SAMPLES - 2, replace=False)
+    return np.concatenate([[0, vh - 1], idx])  # corners of the lattice included
+
+
+@pytest.mark.parametrize("arith", [binding.STAG_ARITH_F64, binding.STAG_ARITH_FF])
+def test_apply_A_sampled(fields, arith):
+    fat, lng = fields
+    mass = 0.0062
+    vh = int(np.prod(DIMS)) // 2
+    v = inputs.gaussian_even_source(DIMS, 5)
+    opt = binding.stag_default_options()
+    opt.arith = arith
+    with binding.Handle(torch.from_numpy(fat).cuda(), DIMS, mass,
+                        naik_long=torch.from_numpy(lng).cuda(), options=opt) as h:
+        vt = torch.from_numpy(v).cuda()
+        out = torch.empty_like(vt)
+        binding.stag_apply_A(h.h, vt, out)
+        got = out.cpu().numpy()
+    errs, refs = [], []
+    for i in _sample_sites(vh, 1):
+        s = oracle.even_site_coords(DIMS, int(i))
+        ref = oracle.apply_A_at(fat, lng, mass, v, s, DIMS)
+        errs.append(np.abs(got[i] - ref).max())
+        refs.append(np.abs(ref).max())
+    assert max(errs) <= 1e-13 * max(refs)
+
+
+def test_solve_true_residual_sampled(fields):
+    """FF solve to 1e-10 at m = 0.031; residual re-checked on sampled sites by the oracle."""
+    fat, lng = fields
+    mass, tol = 0.031, 1e-10
+    vh = int(np.prod(DIMS)) // 2
+    b = inputs.gaussian_even_source(DIMS, 0)
+    opt = binding.stag_default_options()
+    opt.arith = binding.STAG_ARITH_FF
+    with binding.Handle(torch.from_numpy(fat).cuda(), DIMS, mass,
+                        naik_long=torch.from_numpy(lng).cuda(), options=opt) as h:
+        bt = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bt)
+        code, info = binding.stag_cg_solve(h.h, bt, x, tol, max_iter=40000)
+        xs = x.cpu().numpy()
+    assert code == binding.STAG_OK, info
+    assert info["true_rel_residual"] <= tol
+    num = den = 0.0
+    for i in _sample_sites(vh, 2):
+        s = oracle.even_site_coords(DIMS, int(i))
+        r = b[i] - oracle.apply_A_at(fat, lng, mass, xs, s, DIMS)
+        num += np.vdot(r, r).real
+        den += np.vdot(b[i], b[i]).real
+    assert np.sqrt(num / den) <= 10 * tol

@@ -1,0 +1,263 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative, norm-wise and element-wise against the largest
+reference entry):
+  * native FP64 Dirac kernels: 1e-13 (every output component is a sum of at
+    most 96 real products; only the summation order differs from the oracle);
+  * float-float Dirac kernels: 1e-13 (about 2^-48 rounding per term);
+  * solves: true residual |b - A x| / |b| <= 1e-10 and |x - x_oracle| / |x_oracle|
+    <= 1e-8 against an oracle solution taken to 1e-13.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1010_4782_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+ARITHS = [binding.STAG_ARITH_F64, binding.STAG_ARITH_FF]
+TOL_OP = 1e-13
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1010_4782_gb300 import build
+
+    build.build()
+    binding.load()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _fields(dims, naik, seed=7):
+    if naik:
+        return inputs.asqtad_form_fields(dims, seeds=(seed, seed + 1, seed + 2))
+    return inputs.gauge_field(dims, seed), None
+
+
+def _handle(fat, lng, dims, mass, arith, **kw):
+    opt = binding.stag_default_options()
+    opt.arith = arith
+    for k, v in kw.items():
+        setattr(opt, k, v)
+    return binding.Handle(_dev(fat), dims, mass, naik_long=None if lng is None else _dev(lng),
+                          options=opt)
+
+
+def _assert_close(got, ref, tol):
+    got = np.asarray(got).reshape(-1)
+    ref = np.asarray(ref).reshape(-1)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    elem = np.abs(got - ref).max() / np.abs(ref).max()
+    assert rel <= tol and elem <= tol, (rel, elem)
+    return rel
+
+
+DIMS = [(4, 4, 4, 4), (2, 2, 2, 2), (6, 4, 2, 8), (10, 6, 4, 12), (8, 8, 8, 16)]
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("naik", [False, True])
+@pytest.mark.parametrize("dims", DIMS)
+def test_dslash_half_parity(dims, naik, arith):
+    """stag_dslash (both parities) vs the oracle's D restricted to one parity."""
+    fat, lng = _fields(dims, naik)
+    op = oracle.Operator(fat, lng, 0.1, dims)
+    vh = op.n_half
+    with _handle(fat, lng, dims, 0.1, arith) as h:
+        for p_out in (0, 1):
+            v = inputs.gaussian_vector(vh, 100 + p_out)
+            out = torch.empty((vh, 3), dtype=torch.complex128, device="cuda")
+            binding.stag_dslash(h.h, p_out, _dev(v), out)
+            _assert_close(out.cpu().numpy(), op.dslash_half(v, p_out), TOL_OP)
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("naik", [False, True])
+@pytest.mark.parametrize("dims", DIMS)
+def test_apply_A_parity(dims, naik, arith):
+    """stag_apply_A vs oracle A = m^2 - D_eo D_oe (Eq. (3) on even sites)."""
+    mass = 0.05
+    fat, lng = _fields(dims, naik, seed=17)
+    op = oracle.Operator(fat, lng, mass, dims)
+    v = inputs.gaussian_even_source(dims, 3)
+    with _handle(fat, lng, dims, mass, arith) as h:
+        out = torch.empty_like(_dev(v))
+        binding.stag_apply_A(h.h, _dev(v), out)
+        _assert_close(out.cpu().numpy(), op.apply_A(v), TOL_OP)
+
+
+def test_apply_A_host_pointers_match_device_pointers():
+    dims = (6, 4, 2, 8)
+    fat, lng = _fields(dims, True, seed=5)
+    v = inputs.gaussian_even_source(dims, 4)
+    opt = binding.stag_default_options()
+    h_host = binding.Handle(fat, dims, 0.2, naik_long=lng, options=opt)
+    out_host = np.empty_like(v)
+    binding.stag_apply_A(h_host.h, v, out_host)
+    h_host.close()
+    with _handle(fat, lng, dims, 0.2, opt.arith) as h:
+        out = torch.empty_like(_dev(v))
+        binding.stag_apply_A(h.h, _dev(v), out)
+    assert np.array_equal(out.cpu().numpy(), out_host)
+
+
+def test_set_mass():
+    dims = (4, 4, 4, 4)
+    fat, _ = _fields(dims, False)
+    v = inputs.gaussian_even_source(dims, 8)
+    with _handle(fat, None, dims, 0.1, binding.STAG_ARITH_F64) as h:
+        binding.stag_set_mass(h.h, 0.7)
+        out = torch.empty_like(_dev(v))
+        binding.stag_apply_A(h.h, _dev(v), out)
+    _assert_close(out.cpu().numpy(), oracle.Operator(fat, None, 0.7, dims).apply_A(v), TOL_OP)
+
+
+# ----------------------------------------------------------------- solves
+def _oracle_x(fat, lng, mass, dims, b, x0=None):
+    op = oracle.Operator(fat, lng, mass, dims)
+    return op, oracle.solve(op.apply_A, b, x0=x0, tol=1e-13, max_iter=200000, max_restarts=20)["x"]
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+def test_config1_solve(arith):
+    """4^4, one-hop, U = exp(0.3 i H), m = 0.1, Gaussian source (seed 0), tol 1e-10."""
+    dims, mass, tol = (4, 4, 4, 4), 0.1, 1e-10
+    fat = inputs.gauge_field(dims, 1)
+    b = inputs.gaussian_even_source(dims, 0)
+    op, x_ref = _oracle_x(fat, None, mass, dims, b)
+    with _handle(fat, None, dims, mass, arith) as h:
+        x = torch.zeros_like(_dev(b))
+        code, info = binding.stag_cg_solve(h.h, _dev(b), x, tol)
+    assert code == binding.STAG_OK, info
+    assert info["true_rel_residual"] <= tol
+    xs = x.cpu().numpy().reshape(-1)
+    r = b.reshape(-1) - op.apply_A(xs).reshape(-1)
+    assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * 1.01
+    assert np.linalg.norm(xs - x_ref) / np.linalg.norm(x_ref) <= 1e-8
+    # iteration count of the oracle's own Fig. 1 at the same tolerance
+    ref = oracle.solve(op.apply_A, b, tol=tol, max_iter=100000)
+    assert abs(info["iters"] - ref["iters"]) <= 2
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("dims,mass", [((8, 8, 8, 16), 0.05), ((6, 4, 2, 8), 0.02), ((10, 6, 4, 12), 0.031)])
+def test_asqtad_solve(dims, mass, arith):
+    tol = 1e-10
+    fat, lng = _fields(dims, True, seed=11)
+    b = inputs.gaussian_even_source(dims, 0)
+    op, x_ref = _oracle_x(fat, lng, mass, dims, b)
+    with _handle(fat, lng, dims, mass, arith) as h:
+        x = torch.zeros_like(_dev(b))
+        code, info = binding.stag_cg_solve(h.h, _dev(b), x, tol)
+    assert code == binding.STAG_OK, info
+    assert info["true_rel_residual"] <= tol
+    xs = x.cpu().numpy().reshape(-1)
+    r = b.reshape(-1) - op.apply_A(xs).reshape(-1)
+    assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * 1.01
+    assert np.linalg.norm(xs - x_ref) / np.linalg.norm(x_ref) <= 1e-8
+
+
+def test_initial_guess_and_host_vectors():
+    dims, mass, tol = (4, 4, 4, 8), 0.08, 1e-10
+    fat, lng = _fields(dims, True, seed=23)
+    b = inputs.gaussian_even_source(dims, 1)
+    x0 = 0.3 * inputs.gaussian_even_source(dims, 2)
+    op, x_ref = _oracle_x(fat, lng, mass, dims, b)
+    with _handle(fat, lng, dims, mass, binding.STAG_ARITH_F64) as h:
+        x = x0.copy()
+        code, info = binding.stag_cg_solve(h.h, b, x, tol)  # numpy (host) arrays
+    assert code == binding.STAG_OK
+    assert info["true_rel_residual"] <= tol
+    assert np.linalg.norm(x.reshape(-1) - x_ref) / np.linalg.norm(x_ref) <= 1e-8
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+def test_graphs_interval_and_timing_do_not_change_results(arith):
+    dims, mass = (6, 4, 2, 8), 0.05
+    fat, lng = _fields(dims, True, seed=29)
+    b = _dev(inputs.gaussian_even_source(dims, 0))
+    xs = []
+    stats = None
+    for kw in ({}, {"use_graphs": 0}, {"check_interval": 1}, {"check_interval": 7, "timing": 1}):
+        with _handle(fat, lng, dims, mass, arith, **kw) as h:
+            x = torch.zeros_like(b)
+            code, info = binding.stag_cg_solve(h.h, b, x, 1e-10)
+            assert code == binding.STAG_OK
+            xs.append(x.cpu().numpy())
+            if kw.get("timing"):
+                stats = [binding.stag_kernel_stats(h.h, k) for k in range(4)]
+                iters = info["iters"]
+    for other in xs[1:]:
+        assert np.array_equal(xs[0], other)
+    assert stats[0][1] == iters and stats[1][1] == iters and stats[2][1] == iters
+    assert all(ms > 0 for ms, _ in stats[:3])
+
+
+def test_solve_is_deterministic():
+    dims, mass = (8, 8, 8, 16), 0.05
+    fat, lng = _fields(dims, True, seed=31)
+    b = _dev(inputs.gaussian_even_source(dims, 0))
+    with _handle(fat, lng, dims, mass, binding.STAG_ARITH_FF) as h:
+        x1 = torch.zeros_like(b)
+        x2 = torch.zeros_like(b)
+        binding.stag_cg_solve(h.h, b, x1, 1e-10)
+        binding.stag_cg_solve(h.h, b, x2, 1e-10)
+    assert torch.equal(x1, x2)
+
+
+# ----------------------------------------------------------- edge / faults
+def test_max_iter_not_converged():
+    dims = (4, 4, 4, 4)
+    fat, _ = _fields(dims, False)
+    b = _dev(inputs.gaussian_even_source(dims, 0))
+    with _handle(fat, None, dims, 0.1, binding.STAG_ARITH_F64) as h:
+        x = torch.zeros_like(b)
+        code, info = binding.stag_cg_solve(h.h, b, x, 1e-10, max_iter=5)
+    assert code == binding.STAG_ERR_NOT_CONVERGED
+    assert info["iters"] == 5 and info["true_rel_residual"] > 1e-10
+    assert torch.isfinite(x).all() and x.abs().sum() > 0
+
+
+def test_zero_source_gives_zero_solution():
+    dims = (4, 4, 4, 4)
+    fat, _ = _fields(dims, False)
+    with _handle(fat, None, dims, 0.1, binding.STAG_ARITH_F64) as h:
+        b = torch.zeros((128, 3), dtype=torch.complex128, device="cuda")
+        x = torch.ones_like(b)
+        code, info = binding.stag_cg_solve(h.h, b, x, 1e-10)
+    assert code == binding.STAG_OK and info["iters"] == 0
+    assert torch.count_nonzero(x) == 0
+
+
+def test_nonfinite_source_rejected():
+    dims = (4, 4, 4, 4)
+    fat, _ = _fields(dims, False)
+    b = inputs.gaussian_even_source(dims, 0)
+    b[7, 1] = np.nan
+    with _handle(fat, None, dims, 0.1, binding.STAG_ARITH_F64) as h:
+        x = torch.zeros_like(_dev(b))
+        with pytest.raises(binding.StagError) as e:
+            binding.stag_cg_solve(h.h, _dev(b), x, 1e-10)
+    assert e.value.code == binding.STAG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+def test_breakdown_on_zero_mode(arith):
+    """Free field at m = 0: a constant source lies in the kernel of A, so d^dag A d = 0."""
+    dims = (4, 4, 4, 4)
+    fat = np.zeros((4, 4, 4, 4, 4, 3, 3), dtype=np.complex128)
+    fat[..., 0, 0] = fat[..., 1, 1] = fat[..., 2, 2] = 1.0
+    b = np.zeros((128, 3), dtype=np.complex128)
+    b[:, 0] = 1.0
+    with _handle(fat, None, dims, 0.0, arith) as h:
+        x = torch.zeros_like(_dev(b))
+        code, info = binding.stag_cg_solve(h.h, _dev(b), x, 1e-10, raise_on_error=False)
+    assert code == binding.STAG_ERR_BREAKDOWN
+    assert info["status"] == binding.STAG_ERR_BREAKDOWN

@@ -13,30 +13,56 @@
 // block and stored in scal->done; every kernel of the iteration returns at
 // once when it is set, so a captured block of iterations stops exactly
 // where Fig. 1 stops.
+//
+// Two sets of kernels: FP64 vectors with native FP64 arithmetic, and
+// float-float vectors (ff.cuh) whose arithmetic runs on the FP32 pipelines.
+// GB300 issues FP64 operations - and FP64<->FP32 conversions - at about 1/58
+// of the FP32 rate, so the float-float set keeps the iteration free of them:
+// x is accumulated in float-float since the last fold and added into the FP64
+// solution by fold_x once per block of iterations.
 #include "ff.cuh"
 #include "stag_kernels.h"
 
 namespace stag {
 
-__device__ __forceinline__ double2 load_d(const void* d, bool ff, size_t idx) {
-    if (ff) return ff_to_complex(__ldg(reinterpret_cast<const float4*>(d) + idx));
-    return __ldg(reinterpret_cast<const double2*>(d) + idx);
-}
-
-__device__ __forceinline__ void store_d(void* d, bool ff, size_t idx, double2 v) {
-    if (ff)
-        reinterpret_cast<float4*>(d)[idx] = ff_from_complex(v);
-    else
-        reinterpret_cast<double2*>(d)[idx] = v;
-}
-
 __device__ __forceinline__ void set_done(CgScalars* sc) {
     sc->done = (sc->delta_new <= sc->threshold || sc->iter >= sc->max_iter) ? 1 : 0;
 }
 
+__device__ __forceinline__ void finish_delta(CgScalars* sc, double total) {
+    sc->delta_old = sc->delta_new;
+    sc->delta_new = total;
+    sc->beta = total / sc->delta_old;
+    sc->beta_ff = ff_from_double(sc->beta);
+    sc->iter += 1;
+    if (!isfinite(total)) {
+        sc->status = 4;  // STAG_ERR_BREAKDOWN
+        sc->done = 1;
+    } else {
+        set_done(sc);
+    }
+}
+
+// Start of one run of Fig. 1: clear the counters and set the loop bounds.
+__global__ void cg_reset_kernel(CgScalars* scal, double threshold, double m2, float2 m2_ff,
+                                long long max_iter) {
+    scal->threshold = threshold;
+    scal->m2 = m2;
+    scal->m2_ff = m2_ff;
+    scal->iter = 0;
+    scal->max_iter = max_iter;
+    scal->done = 0;
+    scal->status = 0;
+    scal->alpha = 0.0;
+    scal->beta = 0.0;
+    scal->alpha_ff = make_float2(0.f, 0.f);
+    scal->beta_ff = make_float2(0.f, 0.f);
+}
+
+// ------------------------------------------------------------ FP64 set
 __global__ void __launch_bounds__(kBlock) cg_init_kernel(Geom g, const double2* __restrict__ b,
                                                          const double2* __restrict__ ad,
-                                                         double2* __restrict__ r, void* d, bool d_ff,
+                                                         double2* __restrict__ r, double2* __restrict__ d,
                                                          CgScalars* scal, double* partials) {
     const int i = blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;
@@ -48,7 +74,7 @@ __global__ void __launch_bounds__(kBlock) cg_init_kernel(Geom g, const double2* 
             const double2 bb = b[k], aa = ad[k];
             const double2 rr = make_double2(bb.x - aa.x, bb.y - aa.y);
             r[k] = rr;
-            store_d(d, d_ff, k, rr);
+            d[k] = rr;
             acc = fma(rr.x, rr.x, acc);
             acc = fma(rr.y, rr.y, acc);
         }
@@ -58,15 +84,15 @@ __global__ void __launch_bounds__(kBlock) cg_init_kernel(Geom g, const double2* 
         if (threadIdx.x == 0) {
             scal->delta_new = total;
             scal->delta_old = total;
-            scal->status = 0;
             set_done(scal);
         }
     }
 }
 
 __global__ void __launch_bounds__(kBlock) cg_update_xr_kernel(Geom g, double2* __restrict__ x,
-                                                              double2* __restrict__ r, const void* d,
-                                                              bool d_ff, const double2* __restrict__ ad,
+                                                              double2* __restrict__ r,
+                                                              const double2* __restrict__ d,
+                                                              const double2* __restrict__ ad,
                                                               CgScalars* scal, double* partials) {
     if (scal->done) return;
     const double alpha = scal->alpha;
@@ -77,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) cg_update_xr_kernel(Geom g, double2* _
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t k = c * vs + i;
-            const double2 dd = load_d(d, d_ff, k);
+            const double2 dd = __ldg(d + k);
             double2 xx = x[k];
             xx.x = fma(alpha, dd.x, xx.x);
             xx.y = fma(alpha, dd.y, xx.y);
@@ -93,23 +119,12 @@ __global__ void __launch_bounds__(kBlock) cg_update_xr_kernel(Geom g, double2* _
     }
     double total;
     if (grid_sum_last_block<kBlock>(acc, partials, &scal->counter, &total)) {
-        if (threadIdx.x == 0) {
-            scal->delta_old = scal->delta_new;
-            scal->delta_new = total;
-            scal->beta = total / scal->delta_old;
-            scal->iter += 1;
-            if (!isfinite(total)) {
-                scal->status = 4;
-                scal->done = 1;
-            } else {
-                set_done(scal);
-            }
-        }
+        if (threadIdx.x == 0) finish_delta(scal, total);
     }
 }
 
 __global__ void __launch_bounds__(kBlock) cg_update_d_kernel(Geom g, const double2* __restrict__ r,
-                                                             void* d, bool d_ff, CgScalars* scal) {
+                                                             double2* __restrict__ d, CgScalars* scal) {
     if (scal->done) return;
     const double beta = scal->beta;
     const int i = blockIdx.x * kBlock + threadIdx.x;
@@ -119,11 +134,103 @@ __global__ void __launch_bounds__(kBlock) cg_update_d_kernel(Geom g, const doubl
     for (int c = 0; c < 3; ++c) {
         const size_t k = c * vs + i;
         const double2 rr = __ldg(r + k);
-        const double2 dd = load_d(d, d_ff, k);
-        store_d(d, d_ff, k, make_double2(fma(beta, dd.x, rr.x), fma(beta, dd.y, rr.y)));
+        const double2 dd = d[k];
+        d[k] = make_double2(fma(beta, dd.x, rr.x), fma(beta, dd.y, rr.y));
     }
 }
 
+// ------------------------------------------------------ float-float set
+__global__ void __launch_bounds__(kBlock) cg_init_ff_kernel(Geom g, const double2* __restrict__ b,
+                                                            const double2* __restrict__ ad,
+                                                            float4* __restrict__ r, float4* __restrict__ d,
+                                                            float4* __restrict__ xff, CgScalars* scal,
+                                                            double* partials) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    double acc = 0.0;
+    if (i < g.vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t k = c * vs + i;
+            const double2 bb = b[k], aa = ad[k];
+            const double2 rr = make_double2(bb.x - aa.x, bb.y - aa.y);
+            const float4 rf = ff_from_complex(rr);
+            r[k] = rf;
+            d[k] = rf;
+            xff[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            acc = fma(rr.x, rr.x, acc);
+            acc = fma(rr.y, rr.y, acc);
+        }
+    }
+    double total;
+    if (grid_sum_last_block<kBlock>(acc, partials, &scal->counter, &total)) {
+        if (threadIdx.x == 0) {
+            scal->delta_new = total;
+            scal->delta_old = total;
+            set_done(scal);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) cg_update_xr_ff_kernel(Geom g, float4* __restrict__ xff,
+                                                                 float4* __restrict__ r,
+                                                                 const float4* __restrict__ d,
+                                                                 const float4* __restrict__ ad,
+                                                                 CgScalars* scal, double* partials) {
+    if (scal->done) return;
+    const float2 alpha = scal->alpha_ff;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    FFAcc n2 = ff_zero();
+    if (i < g.vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t k = c * vs + i;
+            xff[k] = ff_caxpy(alpha, __ldg(d + k), xff[k]);
+            const float4 rr = ff_caxpy(ff_neg(alpha), __ldg(ad + k), r[k]);
+            r[k] = rr;
+            ff_norm2_acc(n2, rr);
+        }
+    }
+    double total;
+    if (grid_sum_last_block<kBlock>(ff_acc_to_double(n2), partials, &scal->counter, &total)) {
+        if (threadIdx.x == 0) finish_delta(scal, total);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) cg_update_d_ff_kernel(Geom g, const float4* __restrict__ r,
+                                                                float4* __restrict__ d, CgScalars* scal) {
+    if (scal->done) return;
+    const float2 beta = scal->beta_ff;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const size_t k = c * vs + i;
+        d[k] = ff_caxpy(beta, d[k], __ldg(r + k));
+    }
+}
+
+// x += x_ff (into FP64), x_ff = 0
+__global__ void __launch_bounds__(kBlock) fold_x_kernel(Geom g, double2* __restrict__ x,
+                                                        float4* __restrict__ xff) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const size_t k = c * vs + i;
+        const double2 a = ff_to_complex(xff[k]);
+        double2 xx = x[k];
+        xx.x += a.x;
+        xx.y += a.y;
+        x[k] = xx;
+        xff[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// ----------------------------------------------------------- utilities
 __global__ void __launch_bounds__(kBlock) norm2_diff_kernel(Geom g, const double2* __restrict__ a,
                                                             const double2* __restrict__ b,
                                                             CgScalars* scal, double* partials) {
@@ -168,19 +275,41 @@ __global__ void __launch_bounds__(kBlock) from_ff_kernel(Geom g, const float4* _
     for (int c = 0; c < 3; ++c) out[c * vs + i] = ff_to_complex(in[c * vs + i]);
 }
 
-void launch_cg_init(const Geom& g, const double2* b, const double2* ad, double2* r, void* d,
-                    bool d_ff, CgScalars* scal, double* partials, cudaStream_t s) {
-    cg_init_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, b, ad, r, d, d_ff, scal, partials);
+// ------------------------------------------------------------ launchers
+void launch_cg_reset(CgScalars* scal, double threshold, double m2, long long max_iter, cudaStream_t s) {
+    cg_reset_kernel<<<1, 1, 0, s>>>(scal, threshold, m2, host_ff_from_double(m2), max_iter);
 }
 
-void launch_cg_update_xr(const Geom& g, double2* x, double2* r, const void* d, bool d_ff,
-                         const double2* ad, CgScalars* scal, double* partials, cudaStream_t s) {
-    cg_update_xr_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, x, r, d, d_ff, ad, scal, partials);
+void launch_cg_init(const Geom& g, const double2* b, const double2* ad, double2* r, double2* d,
+                    CgScalars* scal, double* partials, cudaStream_t s) {
+    cg_init_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, b, ad, r, d, scal, partials);
 }
 
-void launch_cg_update_d(const Geom& g, const double2* r, void* d, bool d_ff, CgScalars* scal,
-                        cudaStream_t s) {
-    cg_update_d_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, r, d, d_ff, scal);
+void launch_cg_update_xr(const Geom& g, double2* x, double2* r, const double2* d, const double2* ad,
+                         CgScalars* scal, double* partials, cudaStream_t s) {
+    cg_update_xr_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, x, r, d, ad, scal, partials);
+}
+
+void launch_cg_update_d(const Geom& g, const double2* r, double2* d, CgScalars* scal, cudaStream_t s) {
+    cg_update_d_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, r, d, scal);
+}
+
+void launch_cg_init_ff(const Geom& g, const double2* b, const double2* ad, float4* r, float4* d,
+                       float4* xff, CgScalars* scal, double* partials, cudaStream_t s) {
+    cg_init_ff_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, b, ad, r, d, xff, scal, partials);
+}
+
+void launch_cg_update_xr_ff(const Geom& g, float4* xff, float4* r, const float4* d, const float4* ad,
+                            CgScalars* scal, double* partials, cudaStream_t s) {
+    cg_update_xr_ff_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, xff, r, d, ad, scal, partials);
+}
+
+void launch_cg_update_d_ff(const Geom& g, const float4* r, float4* d, CgScalars* scal, cudaStream_t s) {
+    cg_update_d_ff_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, r, d, scal);
+}
+
+void launch_fold_x(const Geom& g, double2* x, float4* xff, cudaStream_t s) {
+    fold_x_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, x, xff);
 }
 
 void launch_norm2_diff(const Geom& g, const double2* a, const double2* b, CgScalars* scal,
@@ -194,27 +323,6 @@ void launch_to_ff(const Geom& g, const double2* in, float4* out, cudaStream_t s)
 
 void launch_from_ff(const Geom& g, const float4* in, double2* out, cudaStream_t s) {
     from_ff_kernel<<<blocks_for(g.vs), kBlock, 0, s>>>(g, in, out);
-}
-
-}  // namespace stag
-
-namespace stag {
-
-// Start of one run of Fig. 1: clear the counters and set the loop bounds.
-__global__ void cg_reset_kernel(CgScalars* scal, double threshold, double m2, long long max_iter) {
-    scal->threshold = threshold;
-    scal->m2 = m2;
-    scal->iter = 0;
-    scal->max_iter = max_iter;
-    scal->done = 0;
-    scal->status = 0;
-    scal->alpha = 0.0;
-    scal->beta = 0.0;
-}
-
-void launch_cg_reset(CgScalars* scal, double threshold, double m2, long long max_iter,
-                     cudaStream_t s) {
-    cg_reset_kernel<<<1, 1, 0, s>>>(scal, threshold, m2, max_iter);
 }
 
 }  // namespace stag

@@ -54,6 +54,7 @@ struct stag_handle {
     void* d = nullptr;   // CG direction (F64 or FF)
     void* t = nullptr;   // odd-parity intermediate (F64 or FF)
     void* u = nullptr;   // scratch even vector (F64 or FF)
+    float4* xff = nullptr;   // FF: solution increment since the last fold into x
     double* io_a = nullptr;  // ABI-layout staging [vh][3] complex
     double* io_b = nullptr;
     // reductions
@@ -175,38 +176,54 @@ void read_state(stag_handle* h) {
 void enqueue_iteration(stag_handle* h, cudaEvent_t* ev, bool count) {
     const Geom& g = h->g;
     const LinkSet L = links(h);
-    const bool ff = use_ff(h);
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], h->s);
     };
-    mark(0);
-    if (ff)
-        launch_dslash_ff(g, 1, L, reinterpret_cast<const float4*>(h->d), h->t, EPI_PLAIN, nullptr, 0.0,
-                         h->scal, h->partials, h->s);
-    else
-        launch_dslash_f64(g, 1, L, reinterpret_cast<const double2*>(h->d),
-                          reinterpret_cast<double2*>(h->t), EPI_PLAIN, nullptr, 0.0, h->scal,
-                          h->partials, h->s);
-    mark(1);
-    if (ff)
-        launch_dslash_ff(g, 0, L, reinterpret_cast<const float4*>(h->t), h->ad, EPI_CG,
-                         reinterpret_cast<const float4*>(h->d), 0.0, h->scal, h->partials, h->s);
-    else
-        launch_dslash_f64(g, 0, L, reinterpret_cast<const double2*>(h->t), h->ad, EPI_CG,
-                          reinterpret_cast<const double2*>(h->d), 0.0, h->scal, h->partials, h->s);
-    mark(2);
-    launch_cg_update_xr(g, h->x, h->r, h->d, ff, h->ad, h->scal, h->partials, h->s);
-    mark(3);
-    launch_cg_update_d(g, h->r, h->d, ff, h->scal, h->s);
-    mark(4);
+    if (use_ff(h)) {
+        float4* d = static_cast<float4*>(h->d);
+        float4* t = static_cast<float4*>(h->t);
+        float4* r = reinterpret_cast<float4*>(h->r);
+        float4* ad = reinterpret_cast<float4*>(h->ad);
+        mark(0);
+        launch_dslash_ff(g, 1, L, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
+        mark(1);
+        launch_dslash_ff(g, 0, L, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s);
+        mark(2);
+        launch_cg_update_xr_ff(g, h->xff, r, d, ad, h->scal, h->partials, h->s);
+        mark(3);
+        launch_cg_update_d_ff(g, r, d, h->scal, h->s);
+        mark(4);
+    } else {
+        double2* d = static_cast<double2*>(h->d);
+        double2* t = static_cast<double2*>(h->t);
+        mark(0);
+        launch_dslash_f64(g, 1, L, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
+        mark(1);
+        launch_dslash_f64(g, 0, L, t, h->ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s);
+        mark(2);
+        launch_cg_update_xr(g, h->x, h->r, d, h->ad, h->scal, h->partials, h->s);
+        mark(3);
+        launch_cg_update_d(g, h->r, d, h->scal, h->s);
+        mark(4);
+    }
     if (count) h->launches += 4;
+}
+
+// check_interval iterations, then (float-float) the fold of x_ff into x.
+void enqueue_block(stag_handle* h, bool timing, bool count) {
+    const int K = h->opt.check_interval;
+    for (int k = 0; k < K; ++k) enqueue_iteration(h, timing ? &h->events[5 * k] : nullptr, count);
+    if (use_ff(h)) {
+        launch_fold_x(h->g, h->x, h->xff, h->s);
+        if (count) h->launches += 1;
+    }
 }
 
 void ensure_graph(stag_handle* h) {
     if (h->graph) return;
     cudaGraph_t graph = nullptr;
     cuda_check(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal), "begin capture");
-    for (int k = 0; k < h->opt.check_interval; ++k) enqueue_iteration(h, nullptr, false);
+    enqueue_block(h, false, false);
     cudaError_t e = cudaStreamEndCapture(h->s, &graph);
     cuda_check(h, e, "end capture");
     e = cudaGraphInstantiate(&h->graph, graph, 0);
@@ -230,9 +247,9 @@ void run_fig1(stag_handle* h) {
         const long long iter_before = h->scal_host->iter;
         if (graphs) {
             cuda_check(h, cudaGraphLaunch(h->graph, h->s), "cudaGraphLaunch");
-            h->launches += 4LL * K;
+            h->launches += 4LL * K + (use_ff(h) ? 1 : 0);
         } else {
-            for (int k = 0; k < K; ++k) enqueue_iteration(h, timing ? &h->events[5 * k] : nullptr, true);
+            enqueue_block(h, timing, true);
             launch_check(h, "CG iteration");
         }
         read_state(h);
@@ -270,6 +287,7 @@ void destroy_handle(stag_handle* h) {
     dev_free(h->d);
     dev_free(h->t);
     dev_free(h->u);
+    dev_free(h->xff);
     dev_free(h->io_a);
     dev_free(h->io_b);
     dev_free(h->partials);
@@ -382,6 +400,7 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         h->d = dev_alloc<void>(h, vb, "allocate d");
         h->t = dev_alloc<void>(h, vb, "allocate t");
         h->u = dev_alloc<void>(h, vb, "allocate u");
+        if (ff) h->xff = dev_alloc<float4>(h, vb, "allocate x_ff");
         h->io_a = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
         h->io_b = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
         h->partials = dev_alloc<double>(h, sizeof(double) * (size_t)blocks_for(g.vs), "allocate partials");
@@ -446,9 +465,9 @@ int stag_dslash(stag_handle* h, int32_t out_parity, const double* in, double* ou
         if (use_ff(h)) {
             float4* in_ff = reinterpret_cast<float4*>(h->u);
             launch_to_ff(g, h->x, in_ff, h->s);
-            launch_dslash_ff(g, out_parity, links(h), in_ff, h->t, EPI_PLAIN, nullptr, 0.0, nullptr,
-                             nullptr, h->s);
-            launch_from_ff(g, reinterpret_cast<const float4*>(h->t), h->ad, h->s);
+            launch_dslash_ff(g, out_parity, links(h), in_ff, static_cast<float4*>(h->t), EPI_PLAIN,
+                             nullptr, 0.0, nullptr, nullptr, h->s);
+            launch_from_ff(g, static_cast<const float4*>(h->t), h->ad, h->s);
             h->launches += 3;
         } else {
             launch_dslash_f64(g, out_parity, links(h), h->x, h->ad, EPI_PLAIN, nullptr, 0.0, nullptr,
@@ -486,10 +505,12 @@ int stag_apply_A(stag_handle* h, const double* in_even, double* out_even) {
         if (use_ff(h)) {
             float4* in_ff = reinterpret_cast<float4*>(h->u);
             launch_to_ff(g, h->x, in_ff, h->s);
-            launch_dslash_ff(g, 1, links(h), in_ff, h->t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
-            launch_dslash_ff(g, 0, links(h), reinterpret_cast<const float4*>(h->t), h->ad, EPI_AXPY, in_ff,
-                             m2, nullptr, nullptr, h->s);
-            h->launches += 3;
+            float4* t = static_cast<float4*>(h->t);
+            float4* out_ff = reinterpret_cast<float4*>(h->r);
+            launch_dslash_ff(g, 1, links(h), in_ff, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
+            launch_dslash_ff(g, 0, links(h), t, out_ff, EPI_AXPY, in_ff, m2, nullptr, nullptr, h->s);
+            launch_from_ff(g, out_ff, h->ad, h->s);
+            h->launches += 4;
         } else {
             apply_A_f64(h, h->x, h->ad);
         }
@@ -546,7 +567,12 @@ int stag_cg_solve(stag_handle* h, const double* b_even, double* x_even, double t
             int restarts = 0;
             while (true) {
                 launch_cg_reset(h->scal, threshold, m2, max_it - iters, h->s);
-                launch_cg_init(g, h->b, h->ad, h->r, h->d, ff, h->scal, h->partials, h->s);
+                if (ff)
+                    launch_cg_init_ff(g, h->b, h->ad, reinterpret_cast<float4*>(h->r), static_cast<float4*>(h->d),
+                                      h->xff, h->scal, h->partials, h->s);
+                else
+                    launch_cg_init(g, h->b, h->ad, h->r, static_cast<double2*>(h->d), h->scal, h->partials,
+                                   h->s);
                 h->launches += 2;
                 launch_check(h, "CG init");
                 run_fig1(h);

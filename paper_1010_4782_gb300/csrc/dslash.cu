@@ -19,7 +19,7 @@
 //
 // Epilogues (used by A = m^2 - D_eo D_oe, Eq. (3)):
 //   EPI_PLAIN  out = D in
-//   EPI_AXPY   out = m2 * src - D in                      (out in FP64)
+//   EPI_AXPY   out = m2 * src - D in
 //   EPI_CG     as EPI_AXPY with m2 from the CG state, plus the grid-wide
 //              Re(src^dag out) = d^dag A d; the last block forms
 //              alpha = delta_new / d^dag A d (Fig. 1) on the device.
@@ -38,36 +38,58 @@ struct ArithF64 {
 #pragma unroll
         for (int r = 0; r < 3; ++r) a.c[r] = make_double2(0.0, 0.0);
     }
-    // a_r += u * v
-    static __device__ __forceinline__ void mac(Acc& a, int r, T u, T v) { cmac(a.c[r], u, v); }
-    // a_r -= conj(u) * v
-    static __device__ __forceinline__ void msc(Acc& a, int r, T u, T v) { cmsc_conj(a.c[r], u, v); }
-    static __device__ __forceinline__ double2 to_f64(const Acc& a, int r) { return a.c[r]; }
-    static __device__ __forceinline__ double2 val_f64(T v) { return v; }
+    // a_r += sum_c u_c v_c
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, T u0, T u1, T u2, T v0, T v1, T v2) {
+        cmac(a.c[r], u0, v0);
+        cmac(a.c[r], u1, v1);
+        cmac(a.c[r], u2, v2);
+    }
+    // a_r -= sum_c conj(u_c) v_c
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, T u0, T u1, T u2, T v0, T v1, T v2) {
+        cmsc_conj(a.c[r], u0, v0);
+        cmsc_conj(a.c[r], u1, v1);
+        cmsc_conj(a.c[r], u2, v2);
+    }
     static __device__ __forceinline__ T store_val(const Acc& a, int r) { return a.c[r]; }
+    // o = m2 * s - acc_r; dot += Re(conj(s) o)
+    static __device__ __forceinline__ T epilogue(const Acc& a, int r, T s, double m2, float2, double& dot) {
+        const double2 d = a.c[r];
+        const double2 o = make_double2(fma(m2, s.x, -d.x), fma(m2, s.y, -d.y));
+        dot = fma(s.x, o.x, dot);
+        dot = fma(s.y, o.y, dot);
+        return o;
+    }
 };
 
 struct ArithFF {
     using T = float4;
     struct Acc {
         FFAcc re[3], im[3];
+        FFAcc dot;
     };
     static __device__ __forceinline__ void zero(Acc& a) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) a.re[r] = a.im[r] = ff_zero();
+        a.dot = ff_zero();
     }
-    static __device__ __forceinline__ void mac(Acc& a, int r, T u, T v) { ff_cmac(a.re[r], a.im[r], u, v); }
-    static __device__ __forceinline__ void msc(Acc& a, int r, T u, T v) {
-        ff_cmsc_conj(a.re[r], a.im[r], u, v);
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, T u0, T u1, T u2, T v0, T v1, T v2) {
+        ff_row_fwd(a.re[r], a.im[r], u0, u1, u2, v0, v1, v2);
     }
-    static __device__ __forceinline__ double2 to_f64(const Acc& a, int r) {
-        return make_double2(ff_acc_to_double(a.re[r]), ff_acc_to_double(a.im[r]));
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, T u0, T u1, T u2, T v0, T v1, T v2) {
+        ff_row_bwd(a.re[r], a.im[r], u0, u1, u2, v0, v1, v2);
     }
-    static __device__ __forceinline__ double2 val_f64(T v) { return ff_to_complex(v); }
     static __device__ __forceinline__ T store_val(const Acc& a, int r) {
-        const float2 re = ff_result(a.re[r]);
-        const float2 im = ff_result(a.im[r]);
-        return make_float4(re.x, re.y, im.x, im.y);
+        return ff_cplx(ff_result(a.re[r]), ff_result(a.im[r]));
+    }
+    // o = m2 * s - acc_r in float-float; Re(conj(s) o) accumulated in float-float,
+    // converted to FP64 once per thread (dot is only valid after the last row).
+    static __device__ __forceinline__ T epilogue(Acc& a, int r, T s, double, float2 m2, double& dot) {
+        const float2 re = ff_fma(m2, ff_re(s), ff_neg(ff_result(a.re[r])));
+        const float2 im = ff_fma(m2, ff_im(s), ff_neg(ff_result(a.im[r])));
+        const float4 o = ff_cplx(re, im);
+        ff_redot_acc(a.dot, s, o);
+        if (r == 2) dot = ff_acc_to_double(a.dot);
+        return o;
     }
 };
 
@@ -78,9 +100,10 @@ struct DslashParams {
     const typename A::T* fat;  // [2][4][9][vs]
     const typename A::T* lng;  // [2][4][9][vs] or nullptr
     const typename A::T* in;   // [3][vs], parity 1-P
-    void* out;                 // [3][vs]: A::T (EPI_PLAIN) or double2
+    typename A::T* out;        // [3][vs], parity P
     const typename A::T* src;  // [3][vs], parity P (EPI_AXPY / EPI_CG)
-    double m2;
+    double m2;                 // m^2 (EPI_AXPY)
+    float2 m2_ff;              // m^2 as float-float (EPI_AXPY, FF)
     CgScalars* scal;
     double* partials;
 };
@@ -88,26 +111,21 @@ struct DslashParams {
 template <class A>
 __device__ __forceinline__ void hop_fwd(typename A::Acc& acc, const typename A::T* __restrict__ u,
                                         const typename A::T* __restrict__ in, int nb, size_t vs) {
-    typename A::T v[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] = __ldg(in + c * vs + nb);
+    const typename A::T v0 = __ldg(in + nb), v1 = __ldg(in + vs + nb), v2 = __ldg(in + 2 * vs + nb);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) A::mac(acc, r, __ldg(u + (3 * r + c) * vs), v[c]);
+        A::row_fwd(acc, r, __ldg(u + (3 * r) * vs), __ldg(u + (3 * r + 1) * vs), __ldg(u + (3 * r + 2) * vs),
+                   v0, v1, v2);
 }
 
 template <class A>
 __device__ __forceinline__ void hop_bwd(typename A::Acc& acc, const typename A::T* __restrict__ u,
                                         const typename A::T* __restrict__ in, int nb, size_t vs) {
-    typename A::T v[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] = __ldg(in + c * vs + nb);
+    const typename A::T v0 = __ldg(in + nb), v1 = __ldg(in + vs + nb), v2 = __ldg(in + 2 * vs + nb);
     // (U^dag v)_r = sum_c conj(U_cr) v_c
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) A::msc(acc, r, __ldg(u + (3 * c + r) * vs), v[c]);
+        A::row_bwd(acc, r, __ldg(u + r * vs), __ldg(u + (3 + r) * vs), __ldg(u + (6 + r) * vs), v0, v1, v2);
 }
 
 // Half-lattice index of the neighbour of (x,y,z,t) at +-h along mu.
@@ -123,7 +141,7 @@ __device__ __forceinline__ int neighbour(const Geom& g, int x, int y, int z, int
 }
 
 template <class A, bool NAIK, int EPI>
-__global__ void __launch_bounds__(kBlock) dslash_kernel(const DslashParams<A> p) {
+__global__ void __launch_bounds__(kBlock, 4) dslash_kernel(const DslashParams<A> p) {
     if (EPI == EPI_CG) {
         if (p.scal->done) return;
     }
@@ -154,26 +172,19 @@ __global__ void __launch_bounds__(kBlock) dslash_kernel(const DslashParams<A> p)
     }
     if (EPI == EPI_PLAIN) {
         if (active) {
-            typename A::T* out = reinterpret_cast<typename A::T*>(p.out);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) out[r * vs + i] = A::store_val(acc, r);
+            for (int r = 0; r < 3; ++r) p.out[r * vs + i] = A::store_val(acc, r);
         }
         return;
     }
-    // out = m2 * src - D in, in FP64
+    // out = m2 * src - D in
     const double m2 = (EPI == EPI_CG) ? p.scal->m2 : p.m2;
+    const float2 m2_ff = (EPI == EPI_CG) ? p.scal->m2_ff : p.m2_ff;
     double dot = 0.0;
     if (active) {
-        double2* out = reinterpret_cast<double2*>(p.out);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const double2 s = A::val_f64(__ldg(p.src + r * vs + i));
-            const double2 d = A::to_f64(acc, r);
-            const double2 o = make_double2(fma(m2, s.x, -d.x), fma(m2, s.y, -d.y));
-            out[r * vs + i] = o;
-            dot = fma(s.x, o.x, dot);
-            dot = fma(s.y, o.y, dot);
-        }
+        for (int r = 0; r < 3; ++r)
+            p.out[r * vs + i] = A::epilogue(acc, r, __ldg(p.src + r * vs + i), m2, m2_ff, dot);
     }
     if (EPI == EPI_CG) {
         double total;
@@ -186,8 +197,10 @@ __global__ void __launch_bounds__(kBlock) dslash_kernel(const DslashParams<A> p)
                     sc->status = 4;  // STAG_ERR_BREAKDOWN
                     sc->done = 1;
                     sc->alpha = 0.0;
+                    sc->alpha_ff = make_float2(0.f, 0.f);
                 } else {
                     sc->alpha = alpha;
+                    sc->alpha_ff = ff_from_double(alpha);
                 }
             }
         }
@@ -215,14 +228,16 @@ static void launch_any(const DslashParams<A>& p, bool naik, Epilogue epi, cudaSt
 void launch_dslash_f64(const Geom& g, int out_parity, const LinkSet& L, const double2* in,
                        double2* out, Epilogue epi, const double2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s) {
-    DslashParams<ArithF64> p{g, out_parity, L.fat64, L.lng64, in, out, src, m2, scal, partials};
+    DslashParams<ArithF64> p{g, out_parity, L.fat64, L.lng64, in, out, src, m2,
+                             make_float2(0.f, 0.f), scal, partials};
     launch_any(p, L.lng64 != nullptr, epi, s);
 }
 
 void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const float4* in,
-                      void* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
+                      float4* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
                       double* partials, cudaStream_t s) {
-    DslashParams<ArithFF> p{g, out_parity, L.fatff, L.lngff, in, out, src, m2, scal, partials};
+    DslashParams<ArithFF> p{g, out_parity, L.fatff, L.lngff, in, out, src, m2,
+                            host_ff_from_double(m2), scal, partials};
     launch_any(p, L.lngff != nullptr, epi, s);
 }
 

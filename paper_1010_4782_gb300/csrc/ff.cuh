@@ -44,52 +44,138 @@ struct FFAcc {
 
 __device__ __forceinline__ FFAcc ff_zero() { return FFAcc{0.0f, 0.0f}; }
 
-// acc += p exactly in (s, e): TwoSum(s, p) -> (s', err), e += err.
-__device__ __forceinline__ void ff_add_exact(FFAcc& a, float p) {
-    const float t = __fadd_rn(a.s, p);
-    const float z = __fsub_rn(t, a.s);
-    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(p, z));
-    a.s = t;
-    a.e = __fadd_rn(a.e, err);
+// TwoSum (Knuth): t + err == a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+    const float t = __fadd_rn(a, b);
+    const float z = __fsub_rn(t, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, z)), __fsub_rn(b, z));
+    return t;
 }
 
-// acc += (xh + xl) * (yh + yl), dropping xl*yl (relative 2^-48).
-__device__ __forceinline__ void ff_mac(FFAcc& a, float xh, float xl, float yh, float yl) {
+// (xh + xl) * (yh + yl) as (p, lo): p = fl(xh*yh), lo = the rest (xl*yl dropped, ~2^-48).
+__device__ __forceinline__ FFAcc ff_prod(float xh, float xl, float yh, float yl) {
     const float p = __fmul_rn(xh, yh);
-    const float q = __fmaf_rn(xh, yh, -p);  // exact: xh*yh - p
-    float e = __fadd_rn(a.e, q);
-    e = __fmaf_rn(xh, yl, e);
-    e = __fmaf_rn(xl, yh, e);
-    a.e = e;
-    ff_add_exact(a, p);
+    float lo = __fmaf_rn(xh, yh, -p);  // exact: xh*yh - p (TwoProduct)
+    lo = __fmaf_rn(xh, yl, lo);
+    lo = __fmaf_rn(xl, yh, lo);
+    return FFAcc{p, lo};
+}
+
+// acc += (xh + xl) * (yh + yl): the leading product enters s through TwoSum, the
+// product's lower part and TwoSum's error enter e with one addition.
+__device__ __forceinline__ void ff_mac(FFAcc& a, float xh, float xl, float yh, float yl) {
+    const FFAcc p = ff_prod(xh, xl, yh, yl);
+    float err;
+    a.s = two_sum(a.s, p.s, err);
+    a.e = __fadd_rn(a.e, __fadd_rn(p.e, err));
+}
+
+// acc += h, where h is a small local sum (one hop): one TwoSum and one addition to e.
+__device__ __forceinline__ void ff_merge(FFAcc& a, const FFAcc& h) {
+    float err;
+    a.s = two_sum(a.s, h.s, err);
+    a.e = __fadd_rn(a.e, __fadd_rn(h.e, err));
 }
 
 // Normalised (hi, lo) of the accumulated value s + e.
 __device__ __forceinline__ float2 ff_result(const FFAcc& a) {
-    const float t = __fadd_rn(a.s, a.e);
-    const float z = __fsub_rn(t, a.s);
-    const float lo = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(a.e, z));
-    return make_float2(t, lo);
+    float lo;
+    const float hi = two_sum(a.s, a.e, lo);
+    return make_float2(hi, lo);
 }
 
 __device__ __forceinline__ double ff_acc_to_double(const FFAcc& a) {
     return (double)a.s + (double)a.e;
 }
 
-// Complex accumulator ops.  x = (re_hi, re_lo, im_hi, im_lo).
-// acc += x * y
-__device__ __forceinline__ void ff_cmac(FFAcc& re, FFAcc& im, float4 x, float4 y) {
-    ff_mac(re, x.x, x.y, y.x, y.y);
-    ff_mac(re, -x.z, -x.w, y.z, y.w);
-    ff_mac(im, x.x, x.y, y.z, y.w);
-    ff_mac(im, x.z, x.w, y.x, y.y);
+// One row of a 3x3 complex product for one hop, accumulated locally and
+// merged once into the site sums (re, im):
+//   fwd:  (re, im) += sum_c u_c * v_c            (u_c = U_{r c})
+//   bwd:  (re, im) -= sum_c conj(u_c) * v_c      (u_c = U_{c r})
+// complex float-float words are (re_hi, re_lo, im_hi, im_lo).
+__device__ __forceinline__ void ff_row_fwd(FFAcc& re, FFAcc& im, float4 u0, float4 u1, float4 u2,
+                                           float4 v0, float4 v1, float4 v2) {
+    FFAcc hr = ff_prod(u0.x, u0.y, v0.x, v0.y);
+    ff_mac(hr, -u0.z, -u0.w, v0.z, v0.w);
+    ff_mac(hr, u1.x, u1.y, v1.x, v1.y);
+    ff_mac(hr, -u1.z, -u1.w, v1.z, v1.w);
+    ff_mac(hr, u2.x, u2.y, v2.x, v2.y);
+    ff_mac(hr, -u2.z, -u2.w, v2.z, v2.w);
+    FFAcc hi = ff_prod(u0.x, u0.y, v0.z, v0.w);
+    ff_mac(hi, u0.z, u0.w, v0.x, v0.y);
+    ff_mac(hi, u1.x, u1.y, v1.z, v1.w);
+    ff_mac(hi, u1.z, u1.w, v1.x, v1.y);
+    ff_mac(hi, u2.x, u2.y, v2.z, v2.w);
+    ff_mac(hi, u2.z, u2.w, v2.x, v2.y);
+    ff_merge(re, hr);
+    ff_merge(im, hi);
 }
-// acc -= conj(x) * y
-__device__ __forceinline__ void ff_cmsc_conj(FFAcc& re, FFAcc& im, float4 x, float4 y) {
-    ff_mac(re, -x.x, -x.y, y.x, y.y);
-    ff_mac(re, -x.z, -x.w, y.z, y.w);
-    ff_mac(im, -x.x, -x.y, y.z, y.w);
-    ff_mac(im, x.z, x.w, y.x, y.y);
+
+__device__ __forceinline__ void ff_row_bwd(FFAcc& re, FFAcc& im, float4 u0, float4 u1, float4 u2,
+                                           float4 v0, float4 v1, float4 v2) {
+    // -conj(u) v = (-ur vr - ui vi) + i (-ur vi + ui vr)
+    FFAcc hr = ff_prod(-u0.x, -u0.y, v0.x, v0.y);
+    ff_mac(hr, -u0.z, -u0.w, v0.z, v0.w);
+    ff_mac(hr, -u1.x, -u1.y, v1.x, v1.y);
+    ff_mac(hr, -u1.z, -u1.w, v1.z, v1.w);
+    ff_mac(hr, -u2.x, -u2.y, v2.x, v2.y);
+    ff_mac(hr, -u2.z, -u2.w, v2.z, v2.w);
+    FFAcc hi = ff_prod(-u0.x, -u0.y, v0.z, v0.w);
+    ff_mac(hi, u0.z, u0.w, v0.x, v0.y);
+    ff_mac(hi, -u1.x, -u1.y, v1.z, v1.w);
+    ff_mac(hi, u1.z, u1.w, v1.x, v1.y);
+    ff_mac(hi, -u2.x, -u2.y, v2.z, v2.w);
+    ff_mac(hi, u2.z, u2.w, v2.x, v2.y);
+    ff_merge(re, hr);
+    ff_merge(im, hi);
+}
+
+// ---------------------------------------------- float-float scalar algebra
+// Values are float2 (hi, lo).  Error about 2^-48 relative per operation.
+__device__ __forceinline__ float2 ff_renorm(float s, float e) {
+    float lo;
+    const float hi = two_sum(s, e, lo);
+    return make_float2(hi, lo);
+}
+
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    float err;
+    const float s = two_sum(a.x, b.x, err);
+    return ff_renorm(s, __fadd_rn(err, __fadd_rn(a.y, b.y)));
+}
+
+// a * b + c
+__device__ __forceinline__ float2 ff_fma(float2 a, float2 b, float2 c) {
+    const FFAcc p = ff_prod(a.x, a.y, b.x, b.y);
+    float err;
+    const float s = two_sum(c.x, p.s, err);
+    return ff_renorm(s, __fadd_rn(__fadd_rn(p.e, err), c.y));
+}
+
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ double ff_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// complex helpers on (re_hi, re_lo, im_hi, im_lo)
+__device__ __forceinline__ float2 ff_re(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 ff_im(float4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float4 ff_cplx(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
+
+// s * a + b for a real float-float scalar s and complex float-float a, b
+__device__ __forceinline__ float4 ff_caxpy(float2 s, float4 a, float4 b) {
+    return ff_cplx(ff_fma(s, ff_re(a), ff_re(b)), ff_fma(s, ff_im(a), ff_im(b)));
+}
+
+// acc += |a|^2 (complex float-float), exact products via TwoProduct
+__device__ __forceinline__ void ff_norm2_acc(FFAcc& acc, float4 a) {
+    ff_mac(acc, a.x, a.y, a.x, a.y);
+    ff_mac(acc, a.z, a.w, a.z, a.w);
+}
+
+// acc += Re(conj(a) * b)
+__device__ __forceinline__ void ff_redot_acc(FFAcc& acc, float4 a, float4 b) {
+    ff_mac(acc, a.x, a.y, b.x, b.y);
+    ff_mac(acc, a.z, a.w, b.z, b.w);
 }
 
 }  // namespace stag

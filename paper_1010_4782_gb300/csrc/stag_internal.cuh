@@ -44,7 +44,18 @@ struct CgScalars {
     int status;        // 0, or STAG_ERR_BREAKDOWN
     unsigned int counter; // blocks finished in the current reduction
     int pad;
+    float2 m2_ff;      // m^2, alpha, beta as float-float pairs (hi, lo)
+    float2 alpha_ff;
+    float2 beta_ff;
+    float2 pad2;
 };
+
+// Host-side float-float split of a double: hi = fl32(a), lo = fl32(a - hi).
+inline float2 host_ff_from_double(double a) {
+    const float hi = (float)a;
+    const float lo = (float)(a - (double)hi);
+    return make_float2(hi, lo);
+}
 
 // -------------------------------------------------------------- geometry
 __device__ __forceinline__ void site_coords(int i, int P, const Geom& g, int& x, int& y, int& z,

@@ -34,27 +34,33 @@ void launch_dslash_f64(const Geom& g, int out_parity, const LinkSet& L, const do
                        double2* out, Epilogue epi, const double2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s);
 void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const float4* in,
-                      void* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
+                      float4* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
                       double* partials, cudaStream_t s);
 
 // ---- CG vector kernels and reductions (blas.cu)
 // start of one run of Fig. 1 (iter = 0, done = 0, threshold, m^2, max_iter)
 void launch_cg_reset(CgScalars* scal, double threshold, double m2, long long max_iter,
                      cudaStream_t s);
-// r = b - Ad; d = r (stored as F64 or FF); delta_new = delta_0 = |r|^2;
-// scal->done = (delta_new <= threshold) || (iter >= max_iter)
-void launch_cg_init(const Geom& g, const double2* b, const double2* ad, double2* r, void* d,
-                    bool d_ff, CgScalars* scal, double* partials, cudaStream_t s);
+// FP64 vectors.  r = b - Ad; d = r; delta_new = delta_0 = |r|^2; done if converged
+void launch_cg_init(const Geom& g, const double2* b, const double2* ad, double2* r, double2* d,
+                    CgScalars* scal, double* partials, cudaStream_t s);
 // x += alpha d; r -= alpha Ad; delta_old = delta_new; delta_new = |r|^2; beta; iter++; done
-void launch_cg_update_xr(const Geom& g, double2* x, double2* r, const void* d, bool d_ff,
-                         const double2* ad, CgScalars* scal, double* partials, cudaStream_t s);
+void launch_cg_update_xr(const Geom& g, double2* x, double2* r, const double2* d, const double2* ad,
+                         CgScalars* scal, double* partials, cudaStream_t s);
 // d = r + beta d
-void launch_cg_update_d(const Geom& g, const double2* r, void* d, bool d_ff, CgScalars* scal,
-                        cudaStream_t s);
+void launch_cg_update_d(const Geom& g, const double2* r, double2* d, CgScalars* scal, cudaStream_t s);
+// float-float vectors: the same steps; x is accumulated in x_ff (zeroed by init)
+void launch_cg_init_ff(const Geom& g, const double2* b, const double2* ad, float4* r, float4* d,
+                       float4* xff, CgScalars* scal, double* partials, cudaStream_t s);
+void launch_cg_update_xr_ff(const Geom& g, float4* xff, float4* r, const float4* d, const float4* ad,
+                            CgScalars* scal, double* partials, cudaStream_t s);
+void launch_cg_update_d_ff(const Geom& g, const float4* r, float4* d, CgScalars* scal, cudaStream_t s);
+// x += x_ff (FP64), x_ff = 0
+void launch_fold_x(const Geom& g, double2* x, float4* xff, cudaStream_t s);
 // scal->red_out = |a - b|^2 (b may be nullptr: |a|^2)
 void launch_norm2_diff(const Geom& g, const double2* a, const double2* b, CgScalars* scal,
                        double* partials, cudaStream_t s);
-// F64 SoA vector -> FF SoA vector
+// F64 SoA vector <-> FF SoA vector
 void launch_to_ff(const Geom& g, const double2* in, float4* out, cudaStream_t s);
 void launch_from_ff(const Geom& g, const float4* in, double2* out, cudaStream_t s);
 

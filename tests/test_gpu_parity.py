@@ -1,10 +1,15 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances (relative, norm-wise and element-wise against the largest
-reference entry):
-  * native FP64 Dirac kernels: 1e-13 (every output component is a sum of at
-    most 96 real products; only the summation order differs from the oracle);
-  * float-float Dirac kernels: 1e-13 (about 2^-48 rounding per term);
+Tolerances (relative; "norm" = |got - ref| / |ref|, "elem" = max |got - ref| /
+max |ref|):
+  * native FP64 Dirac kernels: norm and elem <= 1e-13.  Every output
+    component is a sum of at most 96 real products and only the summation
+    order differs from the oracle, so the error is a few units of 2^-53
+    times sqrt(96) - far below the bar.
+  * float-float Dirac kernels: norm <= 1e-13 (the FP64 bar), elem <= 5e-13.
+    Each product and sum carries about 2^-48 = 3.6e-15 relative rounding;
+    96 terms per component give a worst case of 96 * 2^-48 = 3.4e-13 of the
+    largest term, which bounds the element-wise error.
   * solves: true residual |b - A x| / |b| <= 1e-10 and |x - x_oracle| / |x_oracle|
     <= 1e-8 against an oracle solution taken to 1e-13.
 """
@@ -19,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 ARITHS = [binding.STAG_ARITH_F64, binding.STAG_ARITH_FF]
 TOL_OP = 1e-13
+TOL_ELEM = {binding.STAG_ARITH_F64: 1e-13, binding.STAG_ARITH_FF: 5e-13}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -50,12 +56,12 @@ def _handle(fat, lng, dims, mass, arith, **kw):
                           options=opt)
 
 
-def _assert_close(got, ref, tol):
+def _assert_close(got, ref, tol, tol_elem=None):
     got = np.asarray(got).reshape(-1)
     ref = np.asarray(ref).reshape(-1)
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     elem = np.abs(got - ref).max() / np.abs(ref).max()
-    assert rel <= tol and elem <= tol, (rel, elem)
+    assert rel <= tol and elem <= (tol if tol_elem is None else tol_elem), (rel, elem)
     return rel
 
 
@@ -75,7 +81,7 @@ def test_dslash_half_parity(dims, naik, arith):
             v = inputs.gaussian_vector(vh, 100 + p_out)
             out = torch.empty((vh, 3), dtype=torch.complex128, device="cuda")
             binding.stag_dslash(h.h, p_out, _dev(v), out)
-            _assert_close(out.cpu().numpy(), op.dslash_half(v, p_out), TOL_OP)
+            _assert_close(out.cpu().numpy(), op.dslash_half(v, p_out), TOL_OP, TOL_ELEM[arith])
 
 
 @pytest.mark.parametrize("arith", ARITHS)
@@ -90,7 +96,7 @@ def test_apply_A_parity(dims, naik, arith):
     with _handle(fat, lng, dims, mass, arith) as h:
         out = torch.empty_like(_dev(v))
         binding.stag_apply_A(h.h, _dev(v), out)
-        _assert_close(out.cpu().numpy(), op.apply_A(v), TOL_OP)
+        _assert_close(out.cpu().numpy(), op.apply_A(v), TOL_OP, TOL_ELEM[arith])
 
 
 def test_apply_A_host_pointers_match_device_pointers():
@@ -180,10 +186,13 @@ def test_initial_guess_and_host_vectors():
 
 @pytest.mark.parametrize("arith", ARITHS)
 def test_graphs_interval_and_timing_do_not_change_results(arith):
+    """Graph capture vs direct launches: bit-identical.  Another check interval or the
+    timing mode: bit-identical in FP64; in float-float the fold of x_ff into x happens
+    once per block, so x may differ in the last bits (r, d and the iteration count not)."""
     dims, mass = (6, 4, 2, 8), 0.05
     fat, lng = _fields(dims, True, seed=29)
     b = _dev(inputs.gaussian_even_source(dims, 0))
-    xs = []
+    xs, its = [], []
     stats = None
     for kw in ({}, {"use_graphs": 0}, {"check_interval": 1}, {"check_interval": 7, "timing": 1}):
         with _handle(fat, lng, dims, mass, arith, **kw) as h:
@@ -191,11 +200,17 @@ def test_graphs_interval_and_timing_do_not_change_results(arith):
             code, info = binding.stag_cg_solve(h.h, b, x, 1e-10)
             assert code == binding.STAG_OK
             xs.append(x.cpu().numpy())
+            its.append(info["iters"])
             if kw.get("timing"):
                 stats = [binding.stag_kernel_stats(h.h, k) for k in range(4)]
-                iters = info["iters"]
-    for other in xs[1:]:
-        assert np.array_equal(xs[0], other)
+    assert np.array_equal(xs[0], xs[1])
+    assert len(set(its)) == 1
+    for other in xs[2:]:
+        if arith == binding.STAG_ARITH_F64:
+            assert np.array_equal(xs[0], other)
+        else:
+            assert np.linalg.norm(other - xs[0]) <= 1e-13 * np.linalg.norm(xs[0])
+    iters = its[0]
     assert stats[0][1] == iters and stats[1][1] == iters and stats[2][1] == iters
     assert all(ms > 0 for ms, _ in stats[:3])
 

@@ -311,7 +311,7 @@ void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* 
         }
         src = static_cast<const double*>(stage);
     }
-    launch_pack_links(h->g, src, soa64, soaff, h->s);
+    launch_pack_links(h->g, src, soa64, soaff, nullptr, nullptr, h->s);
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (stage) {

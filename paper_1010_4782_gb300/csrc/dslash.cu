@@ -23,6 +23,8 @@
 //   EPI_CG     as EPI_AXPY with m2 from the CG state, plus the grid-wide
 //              Re(src^dag out) = d^dag A d; the last block forms
 //              alpha = delta_new / d^dag A d (Fig. 1) on the device.
+#include <cuda_fp16.h>
+
 #include "ff.cuh"
 #include "stag_kernels.h"
 
@@ -30,7 +32,9 @@ namespace stag {
 
 // ------------------------------------------------------------ arithmetics
 struct ArithF64 {
-    using T = double2;
+    using T = double2;  // storage
+    using C = double2;  // compute
+    static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
     struct Acc {
         double2 c[3];
     };
@@ -39,20 +43,20 @@ struct ArithF64 {
         for (int r = 0; r < 3; ++r) a.c[r] = make_double2(0.0, 0.0);
     }
     // a_r += sum_c u_c v_c
-    static __device__ __forceinline__ void row_fwd(Acc& a, int r, T u0, T u1, T u2, T v0, T v1, T v2) {
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
         cmac(a.c[r], u0, v0);
         cmac(a.c[r], u1, v1);
         cmac(a.c[r], u2, v2);
     }
     // a_r -= sum_c conj(u_c) v_c
-    static __device__ __forceinline__ void row_bwd(Acc& a, int r, T u0, T u1, T u2, T v0, T v1, T v2) {
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
         cmsc_conj(a.c[r], u0, v0);
         cmsc_conj(a.c[r], u1, v1);
         cmsc_conj(a.c[r], u2, v2);
     }
     static __device__ __forceinline__ T store_val(const Acc& a, int r) { return a.c[r]; }
     // o = m2 * s - acc_r; dot += Re(conj(s) o)
-    static __device__ __forceinline__ T epilogue(const Acc& a, int r, T s, double m2, float2, double& dot) {
+    static __device__ __forceinline__ T epilogue(Acc& a, int r, C s, double m2, float2, double& dot) {
         const double2 d = a.c[r];
         const double2 o = make_double2(fma(m2, s.x, -d.x), fma(m2, s.y, -d.y));
         dot = fma(s.x, o.x, dot);
@@ -63,6 +67,8 @@ struct ArithF64 {
 
 struct ArithFF {
     using T = float4;
+    using C = float4;
+    static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
     struct Acc {
         FFAcc re[3], im[3];
         FFAcc dot;
@@ -72,10 +78,10 @@ struct ArithFF {
         for (int r = 0; r < 3; ++r) a.re[r] = a.im[r] = ff_zero();
         a.dot = ff_zero();
     }
-    static __device__ __forceinline__ void row_fwd(Acc& a, int r, T u0, T u1, T u2, T v0, T v1, T v2) {
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
         ff_row_fwd(a.re[r], a.im[r], u0, u1, u2, v0, v1, v2);
     }
-    static __device__ __forceinline__ void row_bwd(Acc& a, int r, T u0, T u1, T u2, T v0, T v1, T v2) {
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
         ff_row_bwd(a.re[r], a.im[r], u0, u1, u2, v0, v1, v2);
     }
     static __device__ __forceinline__ T store_val(const Acc& a, int r) {
@@ -83,13 +89,67 @@ struct ArithFF {
     }
     // o = m2 * s - acc_r in float-float; Re(conj(s) o) accumulated in float-float,
     // converted to FP64 once per thread (dot is only valid after the last row).
-    static __device__ __forceinline__ T epilogue(Acc& a, int r, T s, double, float2 m2, double& dot) {
+    static __device__ __forceinline__ T epilogue(Acc& a, int r, C s, double, float2 m2, double& dot) {
         const float2 re = ff_fma(m2, ff_re(s), ff_neg(ff_result(a.re[r])));
         const float2 im = ff_fma(m2, ff_im(s), ff_neg(ff_result(a.im[r])));
         const float4 o = ff_cplx(re, im);
         ff_redot_acc(a.dot, s, o);
         if (r == 2) dot = ff_acc_to_double(a.dot);
         return o;
+    }
+};
+
+// FP32 storage and arithmetic (inner solver of the mixed-precision CG).
+struct ArithF32 {
+    using T = float2;
+    using C = float2;
+    static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
+    struct Acc {
+        float2 c[3];
+        float dot;
+    };
+    static __device__ __forceinline__ void zero(Acc& a) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) a.c[r] = make_float2(0.f, 0.f);
+        a.dot = 0.f;
+    }
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        cmacf(a.c[r], u0, v0);
+        cmacf(a.c[r], u1, v1);
+        cmacf(a.c[r], u2, v2);
+    }
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        cmscf_conj(a.c[r], u0, v0);
+        cmscf_conj(a.c[r], u1, v1);
+        cmscf_conj(a.c[r], u2, v2);
+    }
+    static __device__ __forceinline__ T store_val(const Acc& a, int r) { return a.c[r]; }
+    static __device__ __forceinline__ T epilogue(Acc& a, int r, C s, double, float2 m2, double& dot) {
+        const float2 d = a.c[r];
+        const float2 o = make_float2(fmaf(m2.x, s.x, -d.x), fmaf(m2.x, s.y, -d.y));
+        a.dot = fmaf(s.x, o.x, a.dot);
+        a.dot = fmaf(s.y, o.y, a.dot);
+        if (r == 2) dot = (double)a.dot;
+        return o;
+    }
+};
+
+// FP16 storage (links and vectors as half2 = (re, im)), FP32 arithmetic.
+struct ArithH16 {
+    using T = __half2;
+    using C = float2;
+    static __device__ __forceinline__ C ld(const T* p) { return __half22float2(__ldg(p)); }
+    using Acc = ArithF32::Acc;
+    static __device__ __forceinline__ void zero(Acc& a) { ArithF32::zero(a); }
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        ArithF32::row_fwd(a, r, u0, u1, u2, v0, v1, v2);
+    }
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        ArithF32::row_bwd(a, r, u0, u1, u2, v0, v1, v2);
+    }
+    static __device__ __forceinline__ T store_val(const Acc& a, int r) { return __float22half2_rn(a.c[r]); }
+    static __device__ __forceinline__ T epilogue(Acc& a, int r, C s, double m2, float2 m2f, double& dot) {
+        return __float22half2_rn(ArithF32::epilogue(a, r, s, m2, m2f, dot));
     }
 };
 
@@ -111,21 +171,21 @@ struct DslashParams {
 template <class A>
 __device__ __forceinline__ void hop_fwd(typename A::Acc& acc, const typename A::T* __restrict__ u,
                                         const typename A::T* __restrict__ in, int nb, size_t vs) {
-    const typename A::T v0 = __ldg(in + nb), v1 = __ldg(in + vs + nb), v2 = __ldg(in + 2 * vs + nb);
+    const typename A::C v0 = A::ld(in + nb), v1 = A::ld(in + vs + nb), v2 = A::ld(in + 2 * vs + nb);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-        A::row_fwd(acc, r, __ldg(u + (3 * r) * vs), __ldg(u + (3 * r + 1) * vs), __ldg(u + (3 * r + 2) * vs),
+        A::row_fwd(acc, r, A::ld(u + (3 * r) * vs), A::ld(u + (3 * r + 1) * vs), A::ld(u + (3 * r + 2) * vs),
                    v0, v1, v2);
 }
 
 template <class A>
 __device__ __forceinline__ void hop_bwd(typename A::Acc& acc, const typename A::T* __restrict__ u,
                                         const typename A::T* __restrict__ in, int nb, size_t vs) {
-    const typename A::T v0 = __ldg(in + nb), v1 = __ldg(in + vs + nb), v2 = __ldg(in + 2 * vs + nb);
+    const typename A::C v0 = A::ld(in + nb), v1 = A::ld(in + vs + nb), v2 = A::ld(in + 2 * vs + nb);
     // (U^dag v)_r = sum_c conj(U_cr) v_c
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-        A::row_bwd(acc, r, __ldg(u + r * vs), __ldg(u + (3 + r) * vs), __ldg(u + (6 + r) * vs), v0, v1, v2);
+        A::row_bwd(acc, r, A::ld(u + r * vs), A::ld(u + (3 + r) * vs), A::ld(u + (6 + r) * vs), v0, v1, v2);
 }
 
 // Half-lattice index of the neighbour of (x,y,z,t) at +-h along mu.
@@ -184,7 +244,7 @@ __global__ void __launch_bounds__(kBlock, 4) dslash_kernel(const DslashParams<A>
     if (active) {
 #pragma unroll
         for (int r = 0; r < 3; ++r)
-            p.out[r * vs + i] = A::epilogue(acc, r, __ldg(p.src + r * vs + i), m2, m2_ff, dot);
+            p.out[r * vs + i] = A::epilogue(acc, r, A::ld(p.src + r * vs + i), m2, m2_ff, dot);
     }
     if (EPI == EPI_CG) {
         double total;
@@ -239,6 +299,20 @@ void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const flo
     DslashParams<ArithFF> p{g, out_parity, L.fatff, L.lngff, in, out, src, m2,
                             host_ff_from_double(m2), scal, partials};
     launch_any(p, L.lngff != nullptr, epi, s);
+}
+
+void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const float2* lng,
+                       const float2* in, float2* out, Epilogue epi, const float2* src, double m2,
+                       CgScalars* scal, double* partials, cudaStream_t s) {
+    DslashParams<ArithF32> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials};
+    launch_any(p, lng != nullptr, epi, s);
+}
+
+void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng,
+                       const __half2* in, __half2* out, Epilogue epi, const __half2* src, double m2,
+                       CgScalars* scal, double* partials, cudaStream_t s) {
+    DslashParams<ArithH16> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials};
+    launch_any(p, lng != nullptr, epi, s);
 }
 
 }  // namespace stag

@@ -48,6 +48,11 @@ struct CgScalars {
     float2 alpha_ff;
     float2 beta_ff;
     float2 pad2;
+    // reliable updates of the mixed-precision solver
+    double maxr;             // max |r| since the last residual replacement
+    double rel_delta;        // replace once |r| < rel_delta * maxr
+    long long iter_since;    // iterations since the last replacement
+    long long rel_interval;  // ... or after this many iterations
 };
 
 // Host-side float-float split of a double: hi = fl32(a), lo = fl32(a - hi).
@@ -98,6 +103,20 @@ __device__ __forceinline__ void cmsc_conj(double2& acc, double2 a, double2 b) {
     acc.x = fma(-a.y, b.y, acc.x);
     acc.y = fma(-a.x, b.y, acc.y);
     acc.y = fma(a.y, b.x, acc.y);
+}
+
+// ------------------------------------------------------- FP32 complex ops
+__device__ __forceinline__ void cmacf(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cmscf_conj(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(-a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(-a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
 }
 
 // ---------------------------------------------------- block reductions

@@ -1,6 +1,7 @@
 // stag_kernels.h - host-side launchers of the library's kernels (internal).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,9 +23,10 @@ struct LinkSet {
 };
 
 // ---- packing (pack.cu)
-// AoS links [Lt][Lz][Ly][Lx][4][3][3] complex128 (device) -> SoA with eta folded.
+// AoS links [Lt][Lz][Ly][Lx][4][3][3] complex128 (device) -> SoA with eta folded,
+// in FP64 and, where the pointer is not null, float-float, FP32 and FP16.
 void launch_pack_links(const Geom& g, const double* aos, double2* soa64, float4* soaff,
-                       cudaStream_t s);
+                       float2* soa32, __half2* soa16, cudaStream_t s);
 // ABI vector [vh][3] complex128 (device) <-> F64 SoA [3][vs]
 void launch_pack_vec(const Geom& g, const double* aos, double2* soa, cudaStream_t s);
 void launch_unpack_vec(const Geom& g, const double2* soa, double* aos, cudaStream_t s);
@@ -36,6 +38,14 @@ void launch_dslash_f64(const Geom& g, int out_parity, const LinkSet& L, const do
 void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const float4* in,
                       float4* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
                       double* partials, cudaStream_t s);
+
+// low-precision Dirac kernels of the mixed-precision solver (same epilogues)
+void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const float2* lng,
+                       const float2* in, float2* out, Epilogue epi, const float2* src, double m2,
+                       CgScalars* scal, double* partials, cudaStream_t s);
+void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng,
+                       const __half2* in, __half2* out, Epilogue epi, const __half2* src, double m2,
+                       CgScalars* scal, double* partials, cudaStream_t s);
 
 // ---- CG vector kernels and reductions (blas.cu)
 // start of one run of Fig. 1 (iter = 0, done = 0, threshold, m^2, max_iter)

@@ -158,6 +158,30 @@ int64_t stag_device_bytes(const stag_handle* h);
  * replay of a captured graph counts every kernel in it; 0 for NULL). */
 int64_t stag_launch_count(const stag_handle* h);
 
+/* Largest V/2 that stag_apply_A_noalloc accepts. */
+#define STAG_NOALLOC_MAX_HALF_SITES 65536
+
+/* out_even = A in_even = m^2 in - D_eo D_oe in, without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not have the library allocate device memory (applications that hand out all
+ * device memory from their own pool, or that cannot accept the device-wide
+ * synchronisation an allocation or free may cause).  It needs no handle.
+ * links, naik_long (NULL = one-hop only): the link layout above, eta not
+ * folded; in_even, out_even: [V/2][3] complex128, must not overlap.  Every
+ * array must be device memory of the current device (host pointers are
+ * rejected).  Native FP64 arithmetic.  The odd-site intermediate D_oe in is
+ * kept in a fixed file-scope device array of STAG_NOALLOC_MAX_HALF_SITES sites
+ * (3 MiB) that every GPU loading the library holds until the process exits;
+ * larger lattices are rejected with STAG_ERR_INVALID_ARG.  The array is shared
+ * by all calls: calls that overlap on the GPU (several host threads, or
+ * several streams) race on it.  The first call on each device, with that
+ * device current, looks up the array's device address; make that first call
+ * before any stream capture.  Work is enqueued on cuda_stream (NULL = legacy
+ * default stream) and the call returns after it completes.  Errors are
+ * reported by status; the message is available from stag_last_error(NULL). */
+int stag_apply_A_noalloc(const double* links, const double* naik_long, const int32_t dims[4],
+                         double mass, const double* in_even, double* out_even, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,7 @@ EXPORTED = (
     "stag_reset_stats",
     "stag_device_bytes",
     "stag_launch_count",
+    "stag_apply_A_noalloc",
 )
 
 
@@ -120,6 +121,7 @@ def load(path: str | None = None):
     lib.stag_device_bytes.restype = ctypes.c_int64
     lib.stag_launch_count.argtypes = [H]
     lib.stag_launch_count.restype = ctypes.c_int64
+    lib.stag_apply_A_noalloc.argtypes = [P, P, ctypes.POINTER(i32), d, P, P, P]
     for name in EXPORTED:
         if name not in ("stag_last_error", "stag_device_bytes", "stag_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
@@ -221,6 +223,14 @@ def stag_device_bytes(h) -> int:
 
 def stag_launch_count(h) -> int:
     return int(load().stag_launch_count(h))
+
+
+def stag_apply_A_noalloc(links, naik_long, dims, mass, inp, out, stream=None):
+    """A on even sites without device allocation (device arrays only; small lattices)."""
+    dd = (ctypes.c_int32 * 4)(*[int(v) for v in dims])
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(load().stag_apply_A_noalloc(_ptr(links), _ptr(naik_long), dd, float(mass), _ptr(inp), _ptr(out),
+                                        ctypes.c_void_p(raw or 0)))
 
 
 class Handle:

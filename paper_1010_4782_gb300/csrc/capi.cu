@@ -324,6 +324,11 @@ void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* 
 
 }  // namespace
 
+namespace stag {
+// Error message of a handle-free call, read with stag_last_error(NULL).
+void set_noalloc_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace stag
+
 // ====================================================================== ABI
 extern "C" {
 

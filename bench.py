@@ -55,7 +55,7 @@ def parse_args():
     p.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-f64", action="store_true")
+    p.add_argument("--no-forms", "--no-f64", dest="no_forms", action="store_true")
     return p.parse_args()
 
 
@@ -303,13 +303,46 @@ def run_ours(args):
                "d2h_bytes_per_step": int(vec_bytes)}
         del fat_h, lng_h
 
-    # ---- plain FP64 GPU CG (native FP64 FMA Dirac kernels) for comparison
-    f64 = None
-    if not args.no_f64 and arith != binding.STAG_ARITH_F64:
-        info64 = step(fat_d, lng_d, b_d, x_d, ar=binding.STAG_ARITH_F64, timing=False, record=False)
-        f64 = {"value": round(info64["time_ms"] / 1e3, 4), "unit": UNIT, "iters": info64["iters"],
-               "true_rel_residual": info64["true_rel_residual"],
-               "speedup_of_headline": round(info64["time_ms"] / solve_ms, 3)}
+    # ---- every form at this accuracy, against plain FP64 GPU CG (native FP64 kernels):
+    # asqtad-form operator (this workload) and the one-hop operator on the same lattice
+    forms = None
+    if not args.no_forms:
+        def solve_once(fat_in, lng_in, b_in, ar, inner):
+            o = binding.stag_default_options()
+            o.arith = ar
+            o.inner = inner
+            h = binding.stag_create_ex(fat_in, lng_in, dims, args.mass, o)
+            try:
+                binding.stag_set_stream(h, stream)
+                x = torch.zeros_like(b_in)
+                code, info = binding.stag_cg_solve(h, b_in, x, TOL, MAX_ITER)
+            finally:
+                binding.stag_destroy(h)
+            return code, info, x
+
+        variants = [("fp64_plain", binding.STAG_ARITH_F64, binding.STAG_INNER_NONE),
+                    ("ff_plain", binding.STAG_ARITH_FF, binding.STAG_INNER_NONE),
+                    ("mixed_fp32", binding.STAG_ARITH_FF, binding.STAG_INNER_F32),
+                    ("mixed_fp16", binding.STAG_ARITH_FF, binding.STAG_INNER_F16)]
+        forms = {}
+        one_hop = torch.from_numpy(inputs.gauge_field(dims, 1)).to(dev)
+        for op_name, f_in, l_in in (("asqtad", fat_d, lng_d), ("one_hop", one_hop, None)):
+            res, x64 = {}, None
+            for name, ar, inner in variants:
+                code, info, x = solve_once(f_in, l_in, b_d, ar, inner)
+                if x64 is None:
+                    x64 = x
+                rec = {"time_s": round(info["time_ms"] / 1e3, 4), "status": code, "iters": info["iters"],
+                       "reliable_updates": info["reliable_updates"],
+                       "true_rel_residual": info["true_rel_residual"],
+                       "rel_diff_vs_fp64_plain": float(torch.linalg.vector_norm(x - x64) /
+                                                       torch.linalg.vector_norm(x64))}
+                res[name] = rec
+            base = res["fp64_plain"]["time_s"]
+            for rec in res.values():
+                rec["speedup_vs_fp64_plain"] = round(base / rec["time_s"], 3)
+            forms[op_name] = res
+        del one_hop
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -351,7 +384,7 @@ def run_ours(args):
             "gflops_paper_convention": round(gflops, 1),
             "dslash_eo_cg_avg_ms": round(eo_ms, 4),
             "kernel_shares": kernel_shares,
-            "fp64_plain_cg": f64,
+            "forms": forms,
             "paper_context": PAPER_CONTEXT,
         }
         print(json.dumps(line), flush=True)

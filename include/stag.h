@@ -52,10 +52,27 @@ enum {
 /* Arithmetic of the FP64-class Dirac kernels. */
 enum {
     STAG_ARITH_F64 = 0, /* native FP64 fused multiply-add */
+    STAG_ARITH_F32 = 2, /* FP32 links, vectors and arithmetic (stag_apply_A_prec only) */
+    STAG_ARITH_F16 = 3, /* FP16-stored links and vectors, FP32 arithmetic (stag_apply_A_prec only) */
     STAG_ARITH_FF = 1   /* float-float: each FP64 number held as an unevaluated sum of two
                            FP32 numbers (8 bytes, like FP64), products and sums formed with
                            error-free transformations (Dekker 1971; Knuth TAOCP vol. 2);
                            about 2^-48 relative rounding, FP32 pipelines */
+};
+
+/* Inner precision of the CG iteration.  NONE: the whole iteration in the
+ * FP64-class arithmetic selected by `arith` (plain CG, Fig. 1).  F32 / F16:
+ * mixed-precision CG (the paper's stated next step, Sec. 5) - the iteration runs
+ * on FP32 vectors and links (F32) or on FP16-stored vectors and links with FP32
+ * arithmetic (F16), and the iterated residual is replaced by the true residual
+ * b - A x, computed in the FP64-class arithmetic, whenever it has dropped by
+ * reliable_delta since the last replacement or after reliable_interval
+ * iterations (reliable updates, Sleijpen & van der Vorst 1996).  x, b and the
+ * CG scalars stay FP64. */
+enum {
+    STAG_INNER_NONE = 0,
+    STAG_INNER_F32 = 1,
+    STAG_INNER_F16 = 2
 };
 
 /* Kernel ids for stag_kernel_stats. */
@@ -77,14 +94,19 @@ typedef struct {
     int32_t use_graphs;     /* capture check_interval iterations as one CUDA graph (default 1) */
     int32_t timing;         /* record CUDA events around every CG kernel (default 0);
                                disables graphs; read with stag_kernel_stats                    */
-    int32_t reserved[3];
+    int32_t inner;          /* STAG_INNER_*, precision of the CG iteration (default NONE)      */
+    int32_t reliable_interval; /* mixed precision: most iterations between residual
+                                  replacements (default 100)                                  */
+    int32_t reserved;
+    double reliable_delta;  /* mixed precision: replace the residual once |r| < reliable_delta
+                               times its maximum since the last replacement (default 0.1)     */
 } stag_options;
 
 typedef struct {
     int32_t iters;            /* CG iterations (all restarts)                              */
     int32_t restarts;         /* restarts of Fig. 1 after a true-residual check            */
     int32_t status;           /* the STAG_* status the call returned                       */
-    int32_t reserved;
+    int32_t reliable_updates; /* mixed precision: residual replacements                    */
     double true_rel_residual; /* |b - A x| / |b|, A applied in native FP64                 */
     double iter_rel_residual; /* sqrt(delta_new) / |b| of the last Fig. 1 iterate          */
     double time_ms;           /* wall time of the solve inside the call                     */
@@ -124,6 +146,14 @@ int stag_dslash(stag_handle* h, int32_t out_parity, const double* in, double* ou
  * [V/2][3] complex128 on even sites; must not overlap.  Arithmetic as for
  * stag_dslash. */
 int stag_apply_A(stag_handle* h, const double* in_even, double* out_even);
+
+/* As stag_apply_A (Sec. 2, Eq. (3)) in a chosen arithmetic: STAG_ARITH_F64
+ * (always available), STAG_ARITH_FF (handle created with arith = FF),
+ * STAG_ARITH_F32 / STAG_ARITH_F16 (handle created with inner = F32 / F16: the
+ * operator the mixed-precision iteration uses; FP16 vectors are scaled to unit
+ * rms entries on the way in and back on the way out).  Returns
+ * STAG_ERR_INVALID_ARG when the handle holds no links of that precision. */
+int stag_apply_A_prec(stag_handle* h, int32_t arith, const double* in_even, double* out_even);
 
 /* Solve A x = b by CG (Sec. 2, Fig. 1) to |b - A x| / |b| <= tol.
  * b_even: [V/2][3] source.  x_even: [V/2][3], on entry the initial guess (it

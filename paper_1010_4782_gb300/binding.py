@@ -25,6 +25,12 @@ STAG_ERR_OOM = 6
 
 STAG_ARITH_F64 = 0
 STAG_ARITH_FF = 1
+STAG_ARITH_F32 = 2
+STAG_ARITH_F16 = 3
+
+STAG_INNER_NONE = 0
+STAG_INNER_F32 = 1
+STAG_INNER_F16 = 2
 
 STAG_KERNEL_DSLASH_OE = 0
 STAG_KERNEL_DSLASH_EO = 1
@@ -40,6 +46,7 @@ EXPORTED = (
     "stag_set_mass",
     "stag_dslash",
     "stag_apply_A",
+    "stag_apply_A_prec",
     "stag_cg_solve",
     "stag_destroy",
     "stag_last_error",
@@ -58,7 +65,10 @@ class stag_options(ctypes.Structure):
         ("max_restarts", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
         ("timing", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("inner", ctypes.c_int32),
+        ("reliable_interval", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("reliable_delta", ctypes.c_double),
     ]
 
 
@@ -67,14 +77,14 @@ class stag_solve_info(ctypes.Structure):
         ("iters", ctypes.c_int32),
         ("restarts", ctypes.c_int32),
         ("status", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("reliable_updates", ctypes.c_int32),
         ("true_rel_residual", ctypes.c_double),
         ("iter_rel_residual", ctypes.c_double),
         ("time_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class StagError(RuntimeError):
@@ -111,6 +121,7 @@ def load(path: str | None = None):
     lib.stag_set_mass.argtypes = [H, d]
     lib.stag_dslash.argtypes = [H, i32, P, P]
     lib.stag_apply_A.argtypes = [H, P, P]
+    lib.stag_apply_A_prec.argtypes = [H, i32, P, P]
     lib.stag_cg_solve.argtypes = [H, P, P, d, i32, ctypes.POINTER(stag_solve_info)]
     lib.stag_destroy.argtypes = [H]
     lib.stag_last_error.argtypes = [H]
@@ -186,6 +197,10 @@ def stag_dslash(h, out_parity, inp, out):
 
 def stag_apply_A(h, inp, out):
     _check(load().stag_apply_A(h, _ptr(inp), _ptr(out)), h)
+
+
+def stag_apply_A_prec(h, arith, inp, out):
+    _check(load().stag_apply_A_prec(h, int(arith), _ptr(inp), _ptr(out)), h)
 
 
 def stag_cg_solve(h, b, x, tol, max_iter=0, raise_on_error=True):

@@ -16,6 +16,8 @@
 // Scalars (alpha, beta, delta) are reduced in FP64 on the device.
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "ff.cuh"
 #include "stag_kernels.h"
 
@@ -41,10 +43,10 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(Geom g, const double2*
             const size_t k = c * vs + i;
             const double2 bb = b[k];
             double2 aa;
-            if constexpr (sizeof(AXT) == sizeof(float4) && alignof(AXT) == alignof(float4))
-                aa = ff_to_complex(reinterpret_cast<const float4*>(ax)[k]);
+            if constexpr (std::is_same<AXT, float4>::value)
+                aa = ff_to_complex(ax[k]);
             else
-                aa = reinterpret_cast<const double2*>(ax)[k];
+                aa = ax[k];
             const double2 rr = make_double2(bb.x - aa.x, bb.y - aa.y);
             r[k] = rr;
             acc = fma(rr.x, rr.x, acc);
@@ -189,7 +191,47 @@ __global__ void __launch_bounds__(kBlock) lo_fold_y_kernel(Geom g, double2* __re
     }
 }
 
+// out = scale * in (F64 SoA -> low precision) and back
+template <class V>
+__global__ void __launch_bounds__(kBlock) to_lo_kernel(Geom g, const double2* __restrict__ in, V* __restrict__ out,
+                                                       double scale) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vs) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double2 v = in[c * vs + i];
+        stv(out + c * vs + i, make_float2((float)(v.x * scale), (float)(v.y * scale)));
+    }
+}
+
+template <class V>
+__global__ void __launch_bounds__(kBlock) from_lo_kernel(Geom g, const V* __restrict__ in, double2* __restrict__ out,
+                                                         double scale) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vs) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 v = ldv(in + c * vs + i);
+        out[c * vs + i] = make_double2(scale * (double)v.x, scale * (double)v.y);
+    }
+}
+
 // ------------------------------------------------------------ launchers
+template <class V>
+void launch_to_lo(const Geom& g, const double2* in, V* out, double scale, cudaStream_t s) {
+    to_lo_kernel<V><<<blocks_for(g.vs), kBlock, 0, s>>>(g, in, out, scale);
+}
+template <class V>
+void launch_from_lo(const Geom& g, const V* in, double2* out, double scale, cudaStream_t s) {
+    from_lo_kernel<V><<<blocks_for(g.vs), kBlock, 0, s>>>(g, in, out, scale);
+}
+template void launch_to_lo<float2>(const Geom&, const double2*, float2*, double, cudaStream_t);
+template void launch_to_lo<__half2>(const Geom&, const double2*, __half2*, double, cudaStream_t);
+template void launch_from_lo<float2>(const Geom&, const float2*, double2*, double, cudaStream_t);
+template void launch_from_lo<__half2>(const Geom&, const __half2*, double2*, double, cudaStream_t);
+
 void launch_residual(const Geom& g, const double2* b, const void* ax, bool ax_ff, double2* r,
                      CgScalars* scal, double* partials, cudaStream_t s) {
     if (ax_ff)

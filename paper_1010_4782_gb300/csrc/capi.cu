@@ -55,6 +55,16 @@ struct stag_handle {
     void* t = nullptr;   // odd-parity intermediate (F64 or FF)
     void* u = nullptr;   // scratch even vector (F64 or FF)
     float4* xff = nullptr;   // FF: solution increment since the last fold into x
+    // mixed precision: low-precision links and inner vectors
+    float2* fat32 = nullptr;
+    float2* lng32 = nullptr;
+    __half2* fat16 = nullptr;
+    __half2* lng16 = nullptr;
+    void* lo_d = nullptr;    // [3][vs] float2 (F32) or __half2 (F16)
+    void* lo_t = nullptr;
+    void* lo_ad = nullptr;
+    void* lo_r = nullptr;
+    float2* lo_y = nullptr;  // solution increment since the last replacement, FP32
     double* io_a = nullptr;  // ABI-layout staging [vh][3] complex
     double* io_b = nullptr;
     // reductions
@@ -179,7 +189,35 @@ void enqueue_iteration(stag_handle* h, cudaEvent_t* ev, bool count) {
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], h->s);
     };
-    if (use_ff(h)) {
+    if (h->opt.inner == STAG_INNER_F32) {
+        float2* d = static_cast<float2*>(h->lo_d);
+        float2* t = static_cast<float2*>(h->lo_t);
+        float2* ad = static_cast<float2*>(h->lo_ad);
+        float2* r = static_cast<float2*>(h->lo_r);
+        mark(0);
+        launch_dslash_f32(g, 1, h->fat32, h->lng32, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
+        mark(1);
+        launch_dslash_f32(g, 0, h->fat32, h->lng32, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s);
+        mark(2);
+        launch_lo_update_xr<float2>(g, h->lo_y, r, d, ad, h->scal, h->partials, h->s);
+        mark(3);
+        launch_lo_update_d<float2>(g, r, d, h->scal, h->s);
+        mark(4);
+    } else if (h->opt.inner == STAG_INNER_F16) {
+        __half2* d = static_cast<__half2*>(h->lo_d);
+        __half2* t = static_cast<__half2*>(h->lo_t);
+        __half2* ad = static_cast<__half2*>(h->lo_ad);
+        __half2* r = static_cast<__half2*>(h->lo_r);
+        mark(0);
+        launch_dslash_h16(g, 1, h->fat16, h->lng16, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
+        mark(1);
+        launch_dslash_h16(g, 0, h->fat16, h->lng16, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s);
+        mark(2);
+        launch_lo_update_xr<__half2>(g, h->lo_y, r, d, ad, h->scal, h->partials, h->s);
+        mark(3);
+        launch_lo_update_d<__half2>(g, r, d, h->scal, h->s);
+        mark(4);
+    } else if (use_ff(h)) {
         float4* d = static_cast<float4*>(h->d);
         float4* t = static_cast<float4*>(h->t);
         float4* r = reinterpret_cast<float4*>(h->r);
@@ -213,7 +251,7 @@ void enqueue_iteration(stag_handle* h, cudaEvent_t* ev, bool count) {
 void enqueue_block(stag_handle* h, bool timing, bool count) {
     const int K = h->opt.check_interval;
     for (int k = 0; k < K; ++k) enqueue_iteration(h, timing ? &h->events[5 * k] : nullptr, count);
-    if (use_ff(h)) {
+    if (use_ff(h) && h->opt.inner == STAG_INNER_NONE) {
         launch_fold_x(h->g, h->x, h->xff, h->s);
         if (count) h->launches += 1;
     }
@@ -247,7 +285,7 @@ void run_fig1(stag_handle* h) {
         const long long iter_before = h->scal_host->iter;
         if (graphs) {
             cuda_check(h, cudaGraphLaunch(h->graph, h->s), "cudaGraphLaunch");
-            h->launches += 4LL * K + (use_ff(h) ? 1 : 0);
+            h->launches += 4LL * K + ((use_ff(h) && h->opt.inner == STAG_INNER_NONE) ? 1 : 0);
         } else {
             enqueue_block(h, timing, true);
             launch_check(h, "CG iteration");
@@ -288,6 +326,15 @@ void destroy_handle(stag_handle* h) {
     dev_free(h->t);
     dev_free(h->u);
     dev_free(h->xff);
+    dev_free(h->fat32);
+    dev_free(h->lng32);
+    dev_free(h->fat16);
+    dev_free(h->lng16);
+    dev_free(h->lo_d);
+    dev_free(h->lo_t);
+    dev_free(h->lo_ad);
+    dev_free(h->lo_r);
+    dev_free(h->lo_y);
     dev_free(h->io_a);
     dev_free(h->io_b);
     dev_free(h->partials);
@@ -298,7 +345,8 @@ void destroy_handle(stag_handle* h) {
     delete h;
 }
 
-void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* soaff) {
+void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* soaff, float2* soa32,
+                __half2* soa16) {
     const size_t aos_bytes = (size_t)2 * h->g.vh * 4 * 9 * sizeof(double2);
     const double* src = links_in;
     void* stage = nullptr;
@@ -311,7 +359,7 @@ void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* 
         }
         src = static_cast<const double*>(stage);
     }
-    launch_pack_links(h->g, src, soa64, soaff, nullptr, nullptr, h->s);
+    launch_pack_links(h->g, src, soa64, soaff, soa32, soa16, h->s);
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (stage) {
@@ -320,6 +368,115 @@ void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* 
         if (e == cudaSuccess) e = e2;
     }
     cuda_check(h, e, "pack links");
+}
+
+}  // namespace
+
+namespace {
+
+// A x in the handle's FP64-class arithmetic into h->ad (float-float or FP64);
+// returns true when h->ad holds float-float.  Uses h->u and h->t.
+bool apply_A_fp64class(stag_handle* h, const double2* x) {
+    if (!use_ff(h)) {
+        apply_A_f64(h, x, h->ad);
+        return false;
+    }
+    const Geom& g = h->g;
+    float4* u = static_cast<float4*>(h->u);
+    float4* t = static_cast<float4*>(h->t);
+    float4* ad = reinterpret_cast<float4*>(h->ad);
+    launch_to_ff(g, x, u, h->s);
+    launch_dslash_ff(g, 1, links(h), u, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
+    launch_dslash_ff(g, 0, links(h), t, ad, EPI_AXPY, u, h->mass * h->mass, nullptr, nullptr, h->s);
+    h->launches += 3;
+    launch_check(h, "apply_A (float-float)");
+    return true;
+}
+
+// Mixed-precision CG with reliable updates (header: STAG_INNER_*).  Each pass
+// of the loop folds the inner solution increment into x, recomputes the true
+// residual b - A x in FP64-class arithmetic, stops if it meets tol (confirmed
+// with native FP64), and otherwise replaces the inner residual by it - scaled
+// to unit rms entries for FP16 storage - keeps the search direction (with beta
+// from the replaced residual), and runs the inner iteration until the next
+// replacement is due.
+void solve_mixed(stag_handle* h, double bnorm2, double tol, long long max_it, stag_solve_info& inf,
+                 int& status, double& rel) {
+    const Geom& g = h->g;
+    const bool f16 = h->opt.inner == STAG_INNER_F16;
+    const double m2 = h->mass * h->mass;
+    const double thr_true = tol * tol * bnorm2;
+    double sigma_old = 1.0;
+    bool first = true;
+    long long iters = 0;
+    int updates = 0;
+    while (true) {
+        if (!first) {
+            launch_lo_fold_y(g, h->x, h->lo_y, sigma_old, h->s);
+            h->launches += 1;
+        }
+        const bool ax_ff = apply_A_fp64class(h, h->x);
+        launch_residual(g, h->b, h->ad, ax_ff, h->r, h->scal, h->partials, h->s);
+        h->launches += 1;
+        launch_check(h, "true residual");
+        const double dtrue = read_red_out(h);
+        rel = std::sqrt(dtrue / bnorm2);
+        if (!std::isfinite(dtrue)) {
+            status = STAG_ERR_BREAKDOWN;
+            h->err = "mixed-precision CG: non-finite residual";
+            break;
+        }
+        if (rel <= tol) {
+            if (!use_ff(h)) break;
+            apply_A_f64(h, h->x, h->ad);  // confirm with native FP64 arithmetic
+            launch_norm2_diff(g, h->b, h->ad, h->scal, h->partials, h->s);
+            h->launches += 1;
+            launch_check(h, "true residual (FP64)");
+            rel = std::sqrt(read_red_out(h) / bnorm2);
+            if (rel <= tol) break;
+        }
+        if (iters >= max_it) {
+            status = STAG_ERR_NOT_CONVERGED;
+            h->err = "not converged: true residual " + std::to_string(rel) + " after " + std::to_string(iters) +
+                     " iterations";
+            break;
+        }
+        const double sigma = f16 ? std::sqrt(dtrue / (6.0 * g.vh)) : 1.0;
+        double beta = 0.0;
+        if (!first) {
+            const double delta_old_true = h->scal_host->delta_old * sigma_old * sigma_old;
+            beta = (dtrue / delta_old_true) * (sigma_old / sigma);
+            ++updates;
+        }
+        if (f16)
+            launch_lo_set_residual<__half2>(g, h->r, static_cast<__half2*>(h->lo_r), static_cast<__half2*>(h->lo_d),
+                                            h->lo_y, 1.0 / sigma, beta, first, h->s);
+        else
+            launch_lo_set_residual<float2>(g, h->r, static_cast<float2*>(h->lo_r), static_cast<float2*>(h->lo_d),
+                                           h->lo_y, 1.0 / sigma, beta, first, h->s);
+        launch_lo_reset(h->scal, dtrue / (sigma * sigma), thr_true / (sigma * sigma), m2, max_it - iters,
+                        h->opt.reliable_interval, h->opt.reliable_delta, h->s);
+        h->launches += 2;
+        launch_check(h, "residual replacement");
+        first = false;
+        sigma_old = sigma;
+        run_fig1(h);
+        iters += h->scal_host->iter;
+        if (h->scal_host->status != 0) {
+            launch_lo_fold_y(g, h->x, h->lo_y, sigma_old, h->s);
+            h->launches += 1;
+            apply_A_f64(h, h->x, h->ad);
+            launch_norm2_diff(g, h->b, h->ad, h->scal, h->partials, h->s);
+            h->launches += 1;
+            rel = std::sqrt(read_red_out(h) / bnorm2);
+            status = STAG_ERR_BREAKDOWN;
+            h->err = "CG breakdown: d^dag A d <= 0 or non-finite";
+            break;
+        }
+    }
+    inf.iters = (int32_t)iters;
+    inf.reliable_updates = updates;
+    inf.iter_rel_residual = rel;
 }
 
 }  // namespace
@@ -340,6 +497,9 @@ int stag_default_options(stag_options* opt) {
     opt->max_restarts = 5;
     opt->use_graphs = 1;
     opt->timing = 0;
+    opt->inner = STAG_INNER_NONE;
+    opt->reliable_interval = 100;
+    opt->reliable_delta = 0.1;
     return STAG_OK;
 }
 
@@ -369,6 +529,11 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         if (o.check_interval < 1 || o.check_interval > 4096)
             fail(nullptr, STAG_ERR_INVALID_ARG, "check_interval must be in [1, 4096]");
         if (o.max_restarts < 0) fail(nullptr, STAG_ERR_INVALID_ARG, "max_restarts must be >= 0");
+        if (o.inner != STAG_INNER_NONE && o.inner != STAG_INNER_F32 && o.inner != STAG_INNER_F16)
+            fail(nullptr, STAG_ERR_INVALID_ARG, "unknown inner precision");
+        if (o.inner != STAG_INNER_NONE &&
+            (o.reliable_interval < 1 || !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0)))
+            fail(nullptr, STAG_ERR_INVALID_ARG, "reliable_interval must be >= 1 and reliable_delta in (0, 1)");
 
         h = new stag_handle();
         h->opt = o;
@@ -406,6 +571,22 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         h->t = dev_alloc<void>(h, vb, "allocate t");
         h->u = dev_alloc<void>(h, vb, "allocate u");
         if (ff) h->xff = dev_alloc<float4>(h, vb, "allocate x_ff");
+        const size_t lo_links = (size_t)2 * 4 * 9 * g.vs;  // complex entries per field
+        if (h->opt.inner == STAG_INNER_F32) {
+            h->fat32 = dev_alloc<float2>(h, lo_links * sizeof(float2), "allocate FP32 links");
+            if (h->naik) h->lng32 = dev_alloc<float2>(h, lo_links * sizeof(float2), "allocate FP32 Naik links");
+        } else if (h->opt.inner == STAG_INNER_F16) {
+            h->fat16 = dev_alloc<__half2>(h, lo_links * sizeof(__half2), "allocate FP16 links");
+            if (h->naik) h->lng16 = dev_alloc<__half2>(h, lo_links * sizeof(__half2), "allocate FP16 Naik links");
+        }
+        if (h->opt.inner != STAG_INNER_NONE) {
+            const size_t lo_vb = (size_t)3 * g.vs * (h->opt.inner == STAG_INNER_F32 ? sizeof(float2) : sizeof(__half2));
+            h->lo_d = dev_alloc<void>(h, lo_vb, "allocate inner d");
+            h->lo_t = dev_alloc<void>(h, lo_vb, "allocate inner t");
+            h->lo_ad = dev_alloc<void>(h, lo_vb, "allocate inner Ad");
+            h->lo_r = dev_alloc<void>(h, lo_vb, "allocate inner r");
+            h->lo_y = dev_alloc<float2>(h, (size_t)3 * g.vs * sizeof(float2), "allocate inner y");
+        }
         h->io_a = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
         h->io_b = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
         h->partials = dev_alloc<double>(h, sizeof(double) * (size_t)blocks_for(g.vs), "allocate partials");
@@ -414,8 +595,8 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
                    "allocate pinned CG state");
         std::memset(h->scal_host, 0, sizeof(CgScalars));
 
-        pack_field(h, fat, h->fat64, h->fatff);
-        if (h->naik) pack_field(h, naik_long, h->lng64, h->lngff);
+        pack_field(h, fat, h->fat64, h->fatff, h->fat32, h->fat16);
+        if (h->naik) pack_field(h, naik_long, h->lng64, h->lngff, h->lng32, h->lng16);
         end_call(h);
         *out = h;
         return STAG_OK;
@@ -536,6 +717,67 @@ int stag_apply_A(stag_handle* h, const double* in_even, double* out_even) {
     }
 }
 
+int stag_apply_A_prec(stag_handle* h, int32_t arith, const double* in_even, double* out_even) {
+    if (!h) return STAG_ERR_INVALID_ARG;
+    try {
+        if (!in_even || !out_even) fail(h, STAG_ERR_INVALID_ARG, "NULL vector");
+        if (in_even == out_even) fail(h, STAG_ERR_INVALID_ARG, "in and out must not overlap");
+        const bool ok = arith == STAG_ARITH_F64 || (arith == STAG_ARITH_FF && h->fatff) ||
+                        (arith == STAG_ARITH_F32 && h->fat32) || (arith == STAG_ARITH_F16 && h->fat16);
+        if (!ok) fail(h, STAG_ERR_INVALID_ARG, "the handle holds no links in the requested arithmetic");
+        if (arith == STAG_ARITH_F64 || arith == STAG_ARITH_FF) {
+            const int saved = h->opt.arith;
+            h->opt.arith = arith;
+            const int code = stag_apply_A(h, in_even, out_even);
+            h->opt.arith = saved;
+            return code;
+        }
+        begin_call(h);
+        const Geom& g = h->g;
+        const bool out_dev = is_device_ptr(h, out_even);
+        const double* src = input_vec(h, in_even, h->io_a);
+        launch_pack_vec(g, src, h->x, h->s);
+        double scale = 1.0;
+        if (arith == STAG_ARITH_F16) {  // unit rms entries in FP16
+            launch_norm2_diff(g, h->x, nullptr, h->scal, h->partials, h->s);
+            const double n2 = read_red_out(h);
+            scale = n2 > 0.0 ? std::sqrt(n2 / (6.0 * g.vh)) : 1.0;
+        }
+        const double m2 = h->mass * h->mass;
+        if (arith == STAG_ARITH_F32) {
+            float2* in = static_cast<float2*>(h->lo_d);
+            float2* t = static_cast<float2*>(h->lo_t);
+            float2* o = static_cast<float2*>(h->lo_ad);
+            launch_to_lo<float2>(g, h->x, in, 1.0, h->s);
+            launch_dslash_f32(g, 1, h->fat32, h->lng32, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
+            launch_dslash_f32(g, 0, h->fat32, h->lng32, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s);
+            launch_from_lo<float2>(g, o, h->ad, 1.0, h->s);
+        } else {
+            __half2* in = static_cast<__half2*>(h->lo_d);
+            __half2* t = static_cast<__half2*>(h->lo_t);
+            __half2* o = static_cast<__half2*>(h->lo_ad);
+            launch_to_lo<__half2>(g, h->x, in, 1.0 / scale, h->s);
+            launch_dslash_h16(g, 1, h->fat16, h->lng16, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
+            launch_dslash_h16(g, 0, h->fat16, h->lng16, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s);
+            launch_from_lo<__half2>(g, o, h->ad, scale, h->s);
+        }
+        double* dst = out_dev ? out_even : h->io_b;
+        launch_unpack_vec(g, h->ad, dst, h->s);
+        h->launches += 6;
+        launch_check(h, "apply_A (low precision)");
+        if (!out_dev)
+            cuda_check(h, cudaMemcpyAsync(out_even, h->io_b, abi_vec_bytes(g), cudaMemcpyDeviceToHost, h->s),
+                       "copy result to host");
+        end_call(h);
+        return STAG_OK;
+    } catch (const Fail& f) {
+        return f.code;
+    } catch (...) {
+        h->err = "unexpected exception";
+        return STAG_ERR_CUDA;
+    }
+}
+
 int stag_cg_solve(stag_handle* h, const double* b_even, double* x_even, double tol, int32_t max_iter,
                   stag_solve_info* info) {
     if (!h) return STAG_ERR_INVALID_ARG;
@@ -567,45 +809,49 @@ int stag_cg_solve(stag_handle* h, const double* b_even, double* x_even, double t
             const double threshold = tol * tol * bnorm2;
             const double m2 = h->mass * h->mass;
             const bool ff = use_ff(h);
-            apply_A_f64(h, h->x, h->ad);  // A x for r = b - A x
-            long long iters = 0;
-            int restarts = 0;
-            while (true) {
-                launch_cg_reset(h->scal, threshold, m2, max_it - iters, h->s);
-                if (ff)
-                    launch_cg_init_ff(g, h->b, h->ad, reinterpret_cast<float4*>(h->r), static_cast<float4*>(h->d),
-                                      h->xff, h->scal, h->partials, h->s);
-                else
-                    launch_cg_init(g, h->b, h->ad, h->r, static_cast<double2*>(h->d), h->scal, h->partials,
-                                   h->s);
-                h->launches += 2;
-                launch_check(h, "CG init");
-                run_fig1(h);
-                iters += h->scal_host->iter;
-                inf.iter_rel_residual = std::sqrt(h->scal_host->delta_new / bnorm2);
-                const bool breakdown = h->scal_host->status != 0;
-                // true residual with native FP64 arithmetic
-                apply_A_f64(h, h->x, h->ad);
-                launch_norm2_diff(g, h->b, h->ad, h->scal, h->partials, h->s);
-                h->launches += 1;
-                launch_check(h, "true residual");
-                rel = std::sqrt(read_red_out(h) / bnorm2);
-                if (breakdown) {
-                    status = STAG_ERR_BREAKDOWN;
-                    h->err = "CG breakdown: d^dag A d <= 0 or non-finite";
-                    break;
+            if (h->opt.inner != STAG_INNER_NONE) {
+                solve_mixed(h, bnorm2, tol, max_it, inf, status, rel);
+            } else {
+                apply_A_f64(h, h->x, h->ad);  // A x for r = b - A x
+                long long iters = 0;
+                int restarts = 0;
+                while (true) {
+                    launch_cg_reset(h->scal, threshold, m2, max_it - iters, h->s);
+                    if (ff)
+                        launch_cg_init_ff(g, h->b, h->ad, reinterpret_cast<float4*>(h->r), static_cast<float4*>(h->d),
+                                          h->xff, h->scal, h->partials, h->s);
+                    else
+                        launch_cg_init(g, h->b, h->ad, h->r, static_cast<double2*>(h->d), h->scal, h->partials,
+                                       h->s);
+                    h->launches += 2;
+                    launch_check(h, "CG init");
+                    run_fig1(h);
+                    iters += h->scal_host->iter;
+                    inf.iter_rel_residual = std::sqrt(h->scal_host->delta_new / bnorm2);
+                    const bool breakdown = h->scal_host->status != 0;
+                    // true residual with native FP64 arithmetic
+                    apply_A_f64(h, h->x, h->ad);
+                    launch_norm2_diff(g, h->b, h->ad, h->scal, h->partials, h->s);
+                    h->launches += 1;
+                    launch_check(h, "true residual");
+                    rel = std::sqrt(read_red_out(h) / bnorm2);
+                    if (breakdown) {
+                        status = STAG_ERR_BREAKDOWN;
+                        h->err = "CG breakdown: d^dag A d <= 0 or non-finite";
+                        break;
+                    }
+                    if (rel <= tol) break;
+                    if (iters >= max_it || restarts >= h->opt.max_restarts) {
+                        status = STAG_ERR_NOT_CONVERGED;
+                        h->err = "not converged: true residual " + std::to_string(rel) + " after " +
+                                 std::to_string(iters) + " iterations";
+                        break;
+                    }
+                    ++restarts;
                 }
-                if (rel <= tol) break;
-                if (iters >= max_it || restarts >= h->opt.max_restarts) {
-                    status = STAG_ERR_NOT_CONVERGED;
-                    h->err = "not converged: true residual " + std::to_string(rel) + " after " +
-                             std::to_string(iters) + " iterations";
-                    break;
-                }
-                ++restarts;
+                inf.iters = (int32_t)iters;
+                inf.restarts = restarts;
             }
-            inf.iters = (int32_t)iters;
-            inf.restarts = restarts;
         }
         inf.true_rel_residual = rel;
         double* dst = x_dev ? x_even : h->io_b;

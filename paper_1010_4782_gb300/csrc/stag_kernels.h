@@ -70,6 +70,30 @@ void launch_fold_x(const Geom& g, double2* x, float4* xff, cudaStream_t s);
 // scal->red_out = |a - b|^2 (b may be nullptr: |a|^2)
 void launch_norm2_diff(const Geom& g, const double2* a, const double2* b, CgScalars* scal,
                        double* partials, cudaStream_t s);
+// ---- mixed-precision solver (blas_lo.cu)
+// r = b - Ax (Ax FP64 or float-float); scal->red_out = |r|^2
+void launch_residual(const Geom& g, const double2* b, const void* ax, bool ax_ff, double2* r,
+                     CgScalars* scal, double* partials, cudaStream_t s);
+// start of an inner run: delta, threshold (inner units), m^2, bounds of the replacement rule
+void launch_lo_reset(CgScalars* scal, double delta, double threshold, double m2, long long max_iter,
+                     long long rel_interval, double rel_delta, cudaStream_t s);
+// r_lo = inv_sigma * r64; d_lo = r_lo (first) or r_lo + beta d_lo; y = 0
+template <class V>
+void launch_lo_set_residual(const Geom& g, const double2* r64, V* r, V* d, float2* y, double inv_sigma,
+                            double beta, bool first, cudaStream_t s);
+template <class V>
+void launch_lo_update_xr(const Geom& g, float2* y, V* r, const V* d, const V* ad, CgScalars* scal,
+                         double* partials, cudaStream_t s);
+template <class V>
+void launch_lo_update_d(const Geom& g, const V* r, V* d, CgScalars* scal, cudaStream_t s);
+// out = scale * in, F64 SoA <-> low precision SoA
+template <class V>
+void launch_to_lo(const Geom& g, const double2* in, V* out, double scale, cudaStream_t s);
+template <class V>
+void launch_from_lo(const Geom& g, const V* in, double2* out, double scale, cudaStream_t s);
+// x += sigma * y (FP64); y = 0
+void launch_lo_fold_y(const Geom& g, double2* x, float2* y, double sigma, cudaStream_t s);
+
 // F64 SoA vector <-> FF SoA vector
 void launch_to_ff(const Geom& g, const double2* in, float4* out, cudaStream_t s);
 void launch_from_ff(const Geom& g, const float4* in, double2* out, cudaStream_t s);

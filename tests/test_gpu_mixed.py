@@ -1,0 +1,143 @@
+"""Mixed-precision reliable-update CG (the paper's stated next step, Sec. 5) and
+the low-precision operators it runs on, against the FP64 oracle.
+
+Operator tolerances (relative, norm-wise / element-wise against max |ref|):
+  * FP32 links, vectors and arithmetic: 2e-6 / 1e-5.  Each of the up to 96
+    products per component carries 2^-24 = 6e-8 rounding, and the odd
+    intermediate is rounded to FP32 once more.
+  * FP16-stored links and vectors (FP32 arithmetic): 2e-3 / 2e-2.  Storage
+    rounding is 2^-11 = 4.9e-4 relative per entry (links, input, intermediate,
+    output), averaged over the sums.
+Solves must meet the same bars as the FP64 solver: true residual <= 1e-10 and
+|x - x_oracle| / |x_oracle| <= 1e-8 against an oracle solution taken to 1e-13.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1010_4782_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = {binding.STAG_ARITH_F32: (2e-6, 1e-5), binding.STAG_ARITH_F16: (2e-3, 2e-2)}
+INNER_OF = {binding.STAG_ARITH_F32: binding.STAG_INNER_F32, binding.STAG_ARITH_F16: binding.STAG_INNER_F16}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1010_4782_gb300 import build
+
+    build.build()
+    binding.load()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _fields(dims, naik, seed):
+    if naik:
+        return inputs.asqtad_form_fields(dims, seeds=(seed, seed + 1, seed + 2))
+    return inputs.gauge_field(dims, seed), None
+
+
+def _handle(fat, lng, dims, mass, arith=binding.STAG_ARITH_FF, inner=binding.STAG_INNER_NONE, **kw):
+    opt = binding.stag_default_options()
+    opt.arith = arith
+    opt.inner = inner
+    for k, v in kw.items():
+        setattr(opt, k, v)
+    return binding.Handle(_dev(fat), dims, mass, naik_long=None if lng is None else _dev(lng), options=opt)
+
+
+@pytest.mark.parametrize("prec", [binding.STAG_ARITH_F32, binding.STAG_ARITH_F16])
+@pytest.mark.parametrize("naik", [False, True])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 12), (8, 8, 8, 16)])
+def test_low_precision_operator(dims, naik, prec):
+    mass = 0.05
+    fat, lng = _fields(dims, naik, 61)
+    ref = oracle.Operator(fat, lng, mass, dims).apply_A(v := inputs.gaussian_even_source(dims, 62))
+    with _handle(fat, lng, dims, mass, inner=INNER_OF[prec]) as h:
+        out = torch.empty_like(_dev(v))
+        binding.stag_apply_A_prec(h.h, prec, _dev(v), out)
+    got = out.cpu().numpy()
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    elem = np.abs(got - ref).max() / np.abs(ref).max()
+    tn, te = OP_TOL[prec]
+    assert rel <= tn and elem <= te, (rel, elem)
+
+
+def test_apply_A_prec_fp64_classes_match_apply_A():
+    dims = (6, 4, 2, 8)
+    fat, lng = _fields(dims, True, 63)
+    v = _dev(inputs.gaussian_even_source(dims, 64))
+    with _handle(fat, lng, dims, 0.1, arith=binding.STAG_ARITH_FF) as h:
+        a, b = torch.empty_like(v), torch.empty_like(v)
+        binding.stag_apply_A(h.h, v, a)
+        binding.stag_apply_A_prec(h.h, binding.STAG_ARITH_FF, v, b)
+        assert torch.equal(a, b)
+        c = torch.empty_like(v)
+        binding.stag_apply_A_prec(h.h, binding.STAG_ARITH_F64, v, c)
+        ref = oracle.Operator(fat, lng, 0.1, dims).apply_A(v.cpu().numpy())
+        assert np.linalg.norm(c.cpu().numpy() - ref) <= 1e-13 * np.linalg.norm(ref)
+        with pytest.raises(binding.StagError) as e:
+            binding.stag_apply_A_prec(h.h, binding.STAG_ARITH_F32, v, c)
+        assert e.value.code == binding.STAG_ERR_INVALID_ARG
+
+
+def _oracle_x(fat, lng, mass, dims, b):
+    op = oracle.Operator(fat, lng, mass, dims)
+    return op, oracle.solve(op.apply_A, b, tol=1e-13, max_iter=200000, max_restarts=20)["x"]
+
+
+CASES = [((4, 4, 4, 4), False, 0.1, 1),     # the config-1 system
+         ((8, 8, 8, 16), True, 0.05, 11),
+         ((10, 6, 4, 12), True, 0.031, 13),
+         ((8, 8, 8, 8), False, 0.02, 17)]
+
+
+@pytest.mark.parametrize("arith", [binding.STAG_ARITH_FF, binding.STAG_ARITH_F64])
+@pytest.mark.parametrize("inner", [binding.STAG_INNER_F32, binding.STAG_INNER_F16])
+@pytest.mark.parametrize("case", CASES)
+def test_mixed_solve(case, inner, arith):
+    dims, naik, mass, seed = case
+    tol = 1e-10
+    fat, lng = (inputs.gauge_field(dims, seed), None) if not naik else _fields(dims, True, seed)
+    b = inputs.gaussian_even_source(dims, 0)
+    op, x_ref = _oracle_x(fat, lng, mass, dims, b)
+    with _handle(fat, lng, dims, mass, arith=arith, inner=inner) as h:
+        x = torch.zeros_like(_dev(b))
+        code, info = binding.stag_cg_solve(h.h, _dev(b), x, tol, max_iter=20000)
+    assert code == binding.STAG_OK, info
+    assert info["true_rel_residual"] <= tol
+    assert info["reliable_updates"] >= 1
+    xs = x.cpu().numpy().reshape(-1)
+    r = b.reshape(-1) - op.apply_A(xs).reshape(-1)
+    assert np.linalg.norm(r) <= tol * np.linalg.norm(b) * 1.01
+    assert np.linalg.norm(xs - x_ref) / np.linalg.norm(x_ref) <= 1e-8
+
+
+def test_mixed_fp32_iteration_count_close_to_fp64():
+    dims, mass = (8, 8, 8, 16), 0.05
+    fat, lng = _fields(dims, True, 11)
+    b = _dev(inputs.gaussian_even_source(dims, 0))
+    its = {}
+    for inner in (binding.STAG_INNER_NONE, binding.STAG_INNER_F32):
+        with _handle(fat, lng, dims, mass, inner=inner) as h:
+            x = torch.zeros_like(b)
+            code, info = binding.stag_cg_solve(h.h, b, x, 1e-10)
+            assert code == binding.STAG_OK
+            its[inner] = info["iters"]
+    assert its[binding.STAG_INNER_F32] <= 1.3 * its[binding.STAG_INNER_NONE]
+
+
+def test_mixed_rejects_bad_options():
+    dims = (4, 4, 4, 4)
+    fat, _ = _fields(dims, False, 1)
+    with pytest.raises(binding.StagError):
+        _handle(fat, None, dims, 0.1, inner=binding.STAG_INNER_F32, reliable_delta=1.5)
+    with pytest.raises(binding.StagError):
+        _handle(fat, None, dims, 0.1, inner=7)

@@ -97,7 +97,8 @@ typedef struct {
     int32_t inner;          /* STAG_INNER_*, precision of the CG iteration (default NONE)      */
     int32_t reliable_interval; /* mixed precision: most iterations between residual
                                   replacements (default 100)                                  */
-    int32_t reserved;
+    int32_t autotune;       /* batched solves: time the candidate RHS-block and block shapes and
+                               keep the fastest (default 1); 0 = fixed shapes                  */
     double reliable_delta;  /* mixed precision: replace the residual once |r| < reliable_delta
                                times its maximum since the last replacement (default 0.1)     */
 } stag_options;
@@ -187,6 +188,56 @@ int64_t stag_device_bytes(const stag_handle* h);
 /* Number of CUDA kernels the handle has launched since it was created (each
  * replay of a captured graph counts every kernel in it; 0 for NULL). */
 int64_t stag_launch_count(const stag_handle* h);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent systems A_k x_k = b_k (k = 0 .. n_sys-1) solved together.
+ * No counterpart in the paper's single-system CG (Sec. 2, Fig. 1), whose method
+ * each system follows.  Systems whose links (fat and Naik pointers), extents
+ * and mass are equal share one packed field and run as right-hand sides of
+ * multi-RHS Dirac kernels (each link is loaded once for a block of right-hand
+ * sides); lattices of different sizes share every launch.  Each system runs the
+ * mixed-precision CG (FP32 iteration, FP64 scalars) with its own reliable
+ * updates in float-float arithmetic and a final true residual in native FP64.
+ * Blocks of check_interval iterations of all systems are one CUDA graph.  The
+ * right-hand sides per thread and threads per block of each group are chosen
+ * at create by timing the candidates (opt->autotune), cached per (extents,
+ * Naik, RHS count) for the process and in the file STAG_AUTOTUNE_CACHE names. */
+typedef struct stag_batch stag_batch;
+
+/* fat, naik: n_sys link arrays (the link layout above; naik may be NULL, or
+ * contain NULLs, for one-hop systems); dims: 4*n_sys extents; masses: n_sys.
+ * Link arrays are copied at create.  opt: NULL = defaults (only
+ * check_interval, reliable_interval, reliable_delta and autotune are used). */
+int stag_batch_create(stag_batch** out, int32_t n_sys, const double* const* fat, const double* const* naik,
+                      const int32_t* dims, const double* masses, const stag_options* opt);
+
+/* Order the batch's work after this cudaStream_t (NULL = legacy default stream). */
+int stag_batch_set_stream(stag_batch* b, void* cuda_stream);
+
+/* Solve every system to |b_k - A x_k| / |b_k| <= tol.  b[k], x[k]: [V_k/2][3]
+ * complex128 (host or device); x[k] is the initial guess on entry.  max_iter
+ * bounds each system's iterations (<= 0: unbounded).  infos (nullable): n_sys
+ * entries; time_ms is the wall time of the whole batch.  Returns STAG_OK when
+ * every system converged, else the first failing status. */
+int stag_batch_solve(stag_batch* b, const double* const* bvec, double* const* xvec, double tol, int32_t max_iter,
+                     stag_solve_info* infos);
+
+/* out[k] = A_k in[k] with the batch's FP32 multi-RHS kernels (the operator of
+ * the inner iteration; Sec. 2, Eq. (3)). */
+int stag_batch_apply_A(stag_batch* b, const double* const* in, double* const* out);
+
+/* The shapes the autotuner chose for system k's group and its measured D_oe time. */
+int stag_batch_tuning(const stag_batch* b, int32_t system, int32_t* rhs_per_thread, int32_t* threads_per_block,
+                      double* ms);
+
+/* Message of the batch's last failing call (b = NULL: of the last failing create). */
+const char* stag_batch_last_error(const stag_batch* b);
+
+/* Bytes of device memory the batch holds (0 for NULL). */
+int64_t stag_batch_device_bytes(const stag_batch* b);
+
+/* Release the batch.  NULL-safe. */
+int stag_batch_destroy(stag_batch* b);
 
 /* Largest V/2 that stag_apply_A_noalloc accepts. */
 #define STAG_NOALLOC_MAX_HALF_SITES 65536

@@ -55,6 +55,14 @@ EXPORTED = (
     "stag_device_bytes",
     "stag_launch_count",
     "stag_apply_A_noalloc",
+    "stag_batch_create",
+    "stag_batch_set_stream",
+    "stag_batch_solve",
+    "stag_batch_apply_A",
+    "stag_batch_tuning",
+    "stag_batch_last_error",
+    "stag_batch_device_bytes",
+    "stag_batch_destroy",
 )
 
 
@@ -67,7 +75,7 @@ class stag_options(ctypes.Structure):
         ("timing", ctypes.c_int32),
         ("inner", ctypes.c_int32),
         ("reliable_interval", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
         ("reliable_delta", ctypes.c_double),
     ]
 
@@ -133,8 +141,21 @@ def load(path: str | None = None):
     lib.stag_launch_count.argtypes = [H]
     lib.stag_launch_count.restype = ctypes.c_int64
     lib.stag_apply_A_noalloc.argtypes = [P, P, ctypes.POINTER(i32), d, P, P, P]
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.stag_batch_create.argtypes = [ctypes.POINTER(H), i32, PP, PP, ctypes.POINTER(i32),
+                                      ctypes.POINTER(d), ctypes.POINTER(stag_options)]
+    lib.stag_batch_set_stream.argtypes = [H, P]
+    lib.stag_batch_solve.argtypes = [H, PP, PP, d, i32, ctypes.POINTER(stag_solve_info)]
+    lib.stag_batch_apply_A.argtypes = [H, PP, PP]
+    lib.stag_batch_tuning.argtypes = [H, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(d)]
+    lib.stag_batch_last_error.argtypes = [H]
+    lib.stag_batch_last_error.restype = ctypes.c_char_p
+    lib.stag_batch_device_bytes.argtypes = [H]
+    lib.stag_batch_device_bytes.restype = ctypes.c_int64
+    lib.stag_batch_destroy.argtypes = [H]
     for name in EXPORTED:
-        if name not in ("stag_last_error", "stag_device_bytes", "stag_launch_count"):
+        if name not in ("stag_last_error", "stag_device_bytes", "stag_launch_count", "stag_batch_last_error",
+                        "stag_batch_device_bytes"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -246,6 +267,65 @@ def stag_apply_A_noalloc(links, naik_long, dims, mass, inp, out, stream=None):
     raw = getattr(stream, "cuda_stream", stream)
     _check(load().stag_apply_A_noalloc(_ptr(links), _ptr(naik_long), dd, float(mass), _ptr(inp), _ptr(out),
                                         ctypes.c_void_p(raw or 0)))
+
+
+def _ptr_array(arrs):
+    return (ctypes.c_void_p * len(arrs))(*[_ptr(a) for a in arrs])
+
+
+def stag_batch_create(fats, naiks, dims_list, masses, options: stag_options | None = None):
+    """fats, naiks (None entries allowed), dims_list: per-system lists; returns a batch handle."""
+    n = len(fats)
+    h = ctypes.c_void_p()
+    dd = (ctypes.c_int32 * (4 * n))(*[int(v) for dims in dims_list for v in dims])
+    mm = (ctypes.c_double * n)(*[float(m) for m in masses])
+    nk = _ptr_array(naiks) if naiks is not None else None
+    opt = ctypes.byref(options) if options is not None else None
+    code = load().stag_batch_create(ctypes.byref(h), n, _ptr_array(fats), nk, dd, mm, opt)
+    if code != STAG_OK:
+        raise StagError(code, stag_last_error(None))
+    return h
+
+
+def _bcheck(code, h):
+    if code != STAG_OK:
+        raise StagError(code, load().stag_batch_last_error(h).decode())
+
+
+def stag_batch_set_stream(h, stream):
+    raw = getattr(stream, "cuda_stream", stream)
+    _bcheck(load().stag_batch_set_stream(h, ctypes.c_void_p(raw or 0)), h)
+
+
+def stag_batch_solve(h, bs, xs, tol, max_iter=0):
+    """Returns (status, [info dict per system])."""
+    n = len(bs)
+    infos = (stag_solve_info * n)()
+    code = load().stag_batch_solve(h, _ptr_array(bs), _ptr_array(xs), float(tol), int(max_iter), infos)
+    if code not in (STAG_OK, STAG_ERR_NOT_CONVERGED, STAG_ERR_BREAKDOWN):
+        _bcheck(code, h)
+    return code, [i.as_dict() for i in infos]
+
+
+def stag_batch_apply_A(h, ins, outs):
+    _bcheck(load().stag_batch_apply_A(h, _ptr_array(ins), _ptr_array(outs)), h)
+
+
+def stag_batch_tuning(h, system):
+    rb = ctypes.c_int32()
+    bs = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _bcheck(load().stag_batch_tuning(h, int(system), ctypes.byref(rb), ctypes.byref(bs), ctypes.byref(ms)), h)
+    return rb.value, bs.value, ms.value
+
+
+def stag_batch_device_bytes(h) -> int:
+    return int(load().stag_batch_device_bytes(h))
+
+
+def stag_batch_destroy(h):
+    if h is not None:
+        load().stag_batch_destroy(h)
 
 
 class Handle:

@@ -500,6 +500,7 @@ int stag_default_options(stag_options* opt) {
     opt->inner = STAG_INNER_NONE;
     opt->reliable_interval = 100;
     opt->reliable_delta = 0.1;
+    opt->autotune = 1;
     return STAG_OK;
 }
 

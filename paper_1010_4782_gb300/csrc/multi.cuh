@@ -1,0 +1,50 @@
+// multi.cuh - types and launchers of the batched (many-system) kernels.
+#pragma once
+
+#include "stag_kernels.h"
+
+namespace stag {
+
+// One lattice (gauge field, mass) with nrhs right-hand sides; FP32 vectors are
+// stored right-hand-side innermost: v[(colour * vs + site) * rpad + rhs].
+struct MultiGroup {
+    Geom g;
+    const float2* fat;  // FP32 SoA links [2][4][9][vs], eta folded
+    const float2* lng;  // or nullptr
+    float2* d;          // search directions
+    float2* t;          // odd-parity intermediate D_oe d
+    float2* ad;         // A d
+    float2* r;          // iterated residual (scaled by 1/sigma per RHS)
+    float2* y;          // solution increment since the last replacement
+    double m2;
+    int nrhs;           // right-hand sides of this group
+    int rpad;           // storage stride (nrhs rounded up to the largest block of RHS)
+    int rhs0;           // global index of the group's first right-hand side (CG state)
+    int prhs0;          // padded index of its first slot (partial sums, counters)
+    int max_blocks;     // partial-sum stride per slot
+};
+
+struct MultiLaunch {
+    const MultiGroup* groups;  // device array
+    const int4* items;         // device array: (group, block in group, blocks in group, 0)
+    CgScalars* scal;           // one per right-hand side, global index
+    double* partials;          // [padded slots][max_blocks]
+    unsigned int* counters;    // [padded slots], indexed by the group's first slot
+    int out_parity;
+    int phase;                 // 0: t = D_oe d;  1: Ad = m^2 d - D_eo t
+};
+
+enum MultiKernel { MK_DSLASH_PLAIN = 0, MK_DSLASH_CG = 1, MK_UPDATE_XR = 2, MK_UPDATE_D = 3, MK_DSLASH_AXPY = 4 };
+
+// rb: right-hand sides per thread (1, 2, 4, 8; rpad / rb threads share a site, at most 32);
+// bs: threads per block (64, 128, 256)
+void launch_multi(MultiKernel k, const MultiLaunch& L, int nitems, int rb, int bs, cudaStream_t s);
+
+// single right-hand-side slot of a group's vectors
+void launch_slot_set_residual(const Geom& g, const double2* r64, float2* r, float2* d, float2* y, int rpad, int slot,
+                              double inv_sigma, double beta, bool first, cudaStream_t s);
+void launch_slot_fold_y(const Geom& g, double2* x, float2* y, int rpad, int slot, double sigma, cudaStream_t s);
+void launch_slot_put(const Geom& g, const double2* in, float2* out, int rpad, int slot, cudaStream_t s);
+void launch_slot_get(const Geom& g, const float2* in, double2* out, int rpad, int slot, cudaStream_t s);
+
+}  // namespace stag

@@ -1,0 +1,104 @@
+"""Pins of the parallel-transport network and flexible-CG oracle.
+
+Choices of weights that make the network reproduce the oracle's D (Eq. (5))
+and A = m^2 - D^2 (Eq. (3)) pin its transports, embedding and restriction;
+gauge covariance and linearity pin the rest; flexible CG reduces to Fig. 1's
+CG with the identity preconditioner and to one step with the exact inverse.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ptnet
+from paper_1010_4782_gb300 import inputs
+
+
+def _d_weights(c_out, c_in, o, i, sign=1.0):
+    w = np.zeros((9, c_out, c_in), dtype=np.complex128)
+    for mu in range(4):
+        w[1 + 2 * mu, o, i] = sign
+        w[2 + 2 * mu, o, i] = -sign
+    return w
+
+
+def test_one_layer_reproduces_D():
+    dims = (4, 6, 4, 8)
+    fat = inputs.random_links(dims, 3)
+    net = ptnet.PTNet(fat, dims, [_d_weights(1, 1, 0, 0)])
+    r = inputs.gaussian_even_source(dims, 1)
+    got = net.activations(r)[1][0]
+    op = oracle.Operator(fat, None, 0.1, dims)
+    ref = op.D(oracle.embed(r, dims, 0))
+    assert np.allclose(got, ref, rtol=0, atol=1e-13)
+
+
+def test_three_layers_reproduce_A():
+    """layer 1: (r, D r); layer 2: m^2 r - D (D r); layer 3: identity  =>  M = A on even sites."""
+    dims = (4, 4, 6, 4)
+    m = 0.3
+    fat = inputs.gauge_field(dims, 5)
+    w1 = np.zeros((9, 2, 1), dtype=np.complex128)
+    w1[0, 0, 0] = 1.0
+    w1 += _d_weights(2, 1, 1, 0)
+    w2 = np.zeros((9, 1, 2), dtype=np.complex128)
+    w2[0, 0, 0] = m ** 2
+    w2 += _d_weights(1, 2, 0, 1, sign=-1.0)
+    w3 = np.zeros((9, 1, 1), dtype=np.complex128)
+    w3[0, 0, 0] = 1.0
+    net = ptnet.PTNet(fat, dims, [w1, w2, w3])
+    r = inputs.gaussian_even_source(dims, 2)
+    ref = oracle.Operator(fat, None, m, dims).apply_A(r)
+    assert np.linalg.norm(net.apply(r) - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def _random_weights(seed, chans=(1, 8, 8, 1)):
+    rng = np.random.default_rng(seed)
+    return [0.3 * (rng.standard_normal((9, co, ci)) + 1j * rng.standard_normal((9, co, ci)))
+            for ci, co in zip(chans[:-1], chans[1:])]
+
+
+def test_network_gauge_covariant_and_linear():
+    dims = (4, 4, 4, 6)
+    fat = inputs.gauge_field(dims, 7)
+    ws = _random_weights(8)
+    g = inputs.gauge_transform(dims, 9)
+    fat_t = np.empty_like(fat)
+    for mu in range(4):
+        fat_t[..., mu, :, :] = g @ fat[..., mu, :, :] @ oracle.dagger(oracle.shift(g, mu, 1))
+    r1 = inputs.gaussian_even_source(dims, 10)
+    r2 = inputs.gaussian_even_source(dims, 11)
+    net = ptnet.PTNet(fat, dims, ws)
+    net_t = ptnet.PTNet(fat_t, dims, ws)
+    g_e = g.reshape(-1, 3, 3)[oracle.sites_of_parity(dims, 0)]
+    lhs = net_t.apply(oracle.matvec(g_e, r1))
+    rhs = oracle.matvec(g_e, net.apply(r1))
+    assert np.linalg.norm(lhs - rhs) <= 1e-13 * np.linalg.norm(rhs)
+    a, b = 0.7 - 0.2j, -1.3 + 0.5j
+    lin = net.apply(a * r1 + b * r2) - (a * net.apply(r1) + b * net.apply(r2))
+    assert np.linalg.norm(lin) <= 1e-13 * np.linalg.norm(net.apply(r1))
+
+
+def test_loss_definition():
+    dims = (2, 2, 2, 4)
+    fat = inputs.gauge_field(dims, 12)
+    net = ptnet.PTNet(fat, dims, _random_weights(13))
+    r = inputs.gaussian_even_source(dims, 14)
+    e = inputs.gaussian_even_source(dims, 15)
+    d = net.apply(r) - e
+    assert net.loss(r, e) == pytest.approx(np.vdot(d, d).real / np.vdot(e, e).real, rel=1e-14)
+
+
+def test_fcg_identity_is_cg_and_exact_inverse_is_one_step():
+    dims = (4, 4, 4, 4)
+    op = oracle.Operator(inputs.gauge_field(dims, 1), None, 0.2, dims)
+    b = inputs.gaussian_even_source(dims, 0).reshape(-1)
+    x_f, it_f = ptnet.fcg(op.apply_A, lambda r: r, b, tol=1e-10)
+    x_c, it_c, _, _ = oracle.cg_fig1(op.apply_A, b, np.zeros_like(b), 1e-10, 10000)
+    assert it_f == it_c
+    assert np.linalg.norm(x_f - x_c) <= 1e-9 * np.linalg.norm(x_c)
+    n = b.size
+    a = np.stack([op.apply_A(np.eye(1, n, k).reshape(-1, 3)).reshape(-1) for k in range(n)], axis=1)
+    ainv = np.linalg.inv(a)
+    x1, it1 = ptnet.fcg(op.apply_A, lambda r: ainv @ r, b, tol=1e-10)
+    assert it1 <= 1
+    assert np.linalg.norm(a @ x1 - b) <= 1e-10 * np.linalg.norm(b)

@@ -50,7 +50,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["single", "batched"], default="single")
+    p.add_argument("--workload", choices=["single", "batched", "learned"], default="single")
+    p.add_argument("--pairs", type=int, default=2000)
+    p.add_argument("--test-sources", type=int, default=64)
+    p.add_argument("--epochs", type=int, default=4)
     p.add_argument("--arith", choices=["ff", "f64"], default="ff")
     p.add_argument("--mass", type=float, default=MASS)
     p.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
@@ -523,6 +526,94 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ learned workload
+LEARNED_DIMS = (32, 32, 32, 64)
+
+
+def run_learned(args):
+    """Flexible CG with the parallel-transport network on a 32^3 x 64 asqtad-form field,
+    m = 0.0062: training pairs from plain-CG solves of Gaussian sources, training on the
+    GPU, then fresh test sources solved to 1e-10 with and without the network."""
+    import numpy as np
+    import torch
+
+    from paper_1010_4782_gb300 import binding, build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    binding.load()
+    dims = LEARNED_DIMS
+    fat, lng = inputs.asqtad_form_fields(dims, seeds=(31, 32, 33))
+    opt = binding.stag_default_options()
+    opt.arith = binding.STAG_ARITH_FF
+    h = binding.Handle(torch.from_numpy(fat).to(dev), dims, args.mass, naik_long=torch.from_numpy(lng).to(dev),
+                       options=opt)
+    del fat, lng
+    net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 5)
+    t0 = time.perf_counter()
+    npairs, k = 0, 0
+    while npairs < args.pairs:
+        src = [torch.from_numpy(inputs.gaussian_even_source(dims, 7000 + k)).to(dev)]
+        npairs = binding.stag_ptnet_add_pairs(net, src, stride=10, min_rel_residual=1e-6, max_pairs=args.pairs)
+        k += 1
+    t_pairs = time.perf_counter() - t0
+    loss0 = binding.stag_ptnet_dataset_loss(net)
+    t0 = time.perf_counter()
+    losses = binding.stag_ptnet_train(net, args.epochs, 16, 3e-3, seed=1)
+    t_train = time.perf_counter() - t0
+    loss1 = binding.stag_ptnet_dataset_loss(net)
+    res = {"fcg": [], "cg": []}
+    for j in range(args.test_sources):
+        b = torch.from_numpy(inputs.gaussian_even_source(dims, 90000 + j)).to(dev)
+        x = torch.zeros_like(b)
+        code, info = binding.stag_fcg_solve(h.h, net, b, x, TOL, MAX_ITER)
+        res["fcg"].append((code, info))
+        x2 = torch.zeros_like(b)
+        code2, info2 = binding.stag_cg_solve(h.h, b, x2, TOL, MAX_ITER)
+        res["cg"].append((code2, info2))
+    binding.stag_ptnet_destroy(net)
+    h.close()
+
+    def summary(rs):
+        its = [i["iters"] for _, i in rs]
+        ts = [i["time_ms"] / 1e3 for _, i in rs]
+        return {"solved": sum(1 for c, _ in rs if c == binding.STAG_OK), "iters_mean": float(np.mean(its)),
+                "time_s_mean": round(float(np.mean(ts)), 4),
+                "max_true_rel_residual": max(i["true_rel_residual"] for _, i in rs),
+                "fallbacks": sum(i["restarts"] for _, i in rs)}
+
+    fcg, cg = summary(res["fcg"]), summary(res["cg"])
+    line = {
+        "metric": METRIC + " [learned-preconditioner workload]",
+        "value": fcg["time_s_mean"],
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.test_sources,
+        "warmup": 0,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16 network, float-float CG",
+        "data": "synthetic (seeded SU(3) fields exp(0.3 i H), Gaussian sources)",
+        "config": {"workload": f"flexible CG + 3-layer PT network (1-8-8-1 complex channels), "
+                               f"{'x'.join(map(str, dims))} asqtad-form, m={args.mass}, tol {TOL}",
+                   "pairs": npairs, "sources_for_pairs": k, "epochs": args.epochs, "batch": 16,
+                   "test_sources": args.test_sources},
+        "pair_generation_s": round(t_pairs, 2),
+        "training_s": round(t_train, 2),
+        "loss_before": loss0,
+        "loss_after": loss1,
+        "epoch_losses": [float(v) for v in losses],
+        "fcg": fcg,
+        "plain_cg_ff": cg,
+        "iteration_gain": round(cg["iters_mean"] / fcg["iters_mean"], 3),
+        "time_ratio_fcg_over_cg": round(fcg["time_s_mean"] / cg["time_s_mean"], 3),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(fat, lng, b, dims, mass, iters, restarts):
     """Oracle: initial residual + one Fig. 1 iteration (two A applications) at full size."""
     import numpy as np
@@ -600,6 +691,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -54,6 +54,7 @@ enum {
     STAG_ARITH_F64 = 0, /* native FP64 fused multiply-add */
     STAG_ARITH_F32 = 2, /* FP32 links, vectors and arithmetic (stag_apply_A_prec only) */
     STAG_ARITH_F16 = 3, /* FP16-stored links and vectors, FP32 arithmetic (stag_apply_A_prec only) */
+    STAG_ARITH_BF16 = 4, /* BF16-stored activations, FP32 arithmetic (learned preconditioner only) */
     STAG_ARITH_FF = 1   /* float-float: each FP64 number held as an unevaluated sum of two
                            FP32 numbers (8 bytes, like FP64), products and sums formed with
                            error-free transformations (Dekker 1971; Knuth TAOCP vol. 2);
@@ -238,6 +239,67 @@ int64_t stag_batch_device_bytes(const stag_batch* b);
 
 /* Release the batch.  NULL-safe. */
 int stag_batch_destroy(stag_batch* b);
+
+/* ------------------------------------------------ learned preconditioner
+ * A gauge-covariant parallel-transport network M used as the preconditioner
+ * of flexible CG.  No counterpart in the paper, whose CG (Sec. 2, Fig. 1) is
+ * unpreconditioned; it is built on the same operator.  Three linear layers
+ * with 1 -> 8 -> 8 -> 1 complex channels on the whole lattice; each layer sums,
+ * over nine paths p (the identity and the one-hop transports from x + mu with
+ * U_mu(x) and from x - mu with U_mu(x - mu)^dag, eta-folded fat links, so that
+ * sum_mu T_{+mu} - T_{-mu} = D of Eq. (5)), complex weights W[p][out][in]
+ * times the transported inputs.  The residual enters on even sites (zero on
+ * odd sites) and the output is read on even sites.  Weights: layer-major
+ * [9][C_out][C_in], complex as interleaved doubles (stag_ptnet_num_weights
+ * complex numbers).  The network keeps a pointer to its handle (whose field
+ * and mass it uses); destroy it before the handle. */
+typedef struct stag_ptnet stag_ptnet;
+
+/* precision: STAG_ARITH_BF16 (activations stored as BF16, FP32 arithmetic) or
+ * STAG_ARITH_F32.  Weights start as 0.1 * identity plus seeded noise. */
+int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint64_t seed);
+int64_t stag_ptnet_num_weights(const stag_ptnet* n);
+int stag_ptnet_set_weights(stag_ptnet* n, const double* w, int64_t count);
+int stag_ptnet_get_weights(stag_ptnet* n, double* w, int64_t count);
+
+/* z_even = M(r_even) ([V/2][3] complex128, host or device). */
+int stag_ptnet_apply(stag_ptnet* n, const double* r_even, double* z_even);
+
+/* loss of one pair, the residual norm of the correction |A d|^2 / |A e|^2 with
+ * d = M(r) - e (A applied with the FP32 Dirac kernels), and its gradient
+ * dL/d conj(W) (complex, interleaved; nullable outputs). */
+int stag_ptnet_loss_grad(stag_ptnet* n, const double* r_even, const double* e_even, double* loss, double* grad);
+
+/* Training pairs from plain CG solves (the handle's solver, inner = NONE) of
+ * the given sources to 1e-10: after every `stride` iterations, while the
+ * iterated residual is above min_rel_residual * |b|, the residual r_k and, after
+ * convergence, e_k = x* - x_k are stored, both scaled by 1/|r_k|; at most
+ * max_pairs pairs in total.  *n_pairs: pairs stored so far. */
+int stag_ptnet_add_pairs(stag_ptnet* n, int32_t n_sources, const double* const* sources, int32_t stride,
+                         double min_rel_residual, int32_t max_pairs, int32_t* n_pairs);
+int stag_ptnet_num_pairs(const stag_ptnet* n);
+
+/* Adam (beta 0.9, 0.999) on the stored pairs: `epochs` passes in seeded random
+ * order, mini-batches of `batch` pairs, learning rate lr; epoch_loss (nullable):
+ * mean pair loss of each epoch. */
+int stag_ptnet_train(stag_ptnet* n, int32_t epochs, int32_t batch, double lr, uint64_t seed, double* epoch_loss);
+
+/* Mean loss over the stored pairs. */
+int stag_ptnet_dataset_loss(stag_ptnet* n, double* loss);
+
+const char* stag_ptnet_last_error(const stag_ptnet* n);
+int stag_ptnet_destroy(stag_ptnet* n);
+
+/* Flexible CG with z_k = M(r_k): alpha = (r, z) / (p, A p), x += alpha p,
+ * r -= alpha A p, beta = (z_new, r_new - r_old) / (r_old, z_old), p = z + beta p,
+ * with A in the handle's FP64-class arithmetic and FP64 vectors.  When the
+ * iterated residual falls below tol |b| the true residual is recomputed in
+ * native FP64 and judges convergence; when |r| drops less than 10 % in 60
+ * iterations, or (r, z) or (p, A p) is not positive, plain CG continues from the
+ * current x.  info->restarts counts these fallbacks; the arguments and return
+ * codes are those of stag_cg_solve. */
+int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* x_even, double tol,
+                   int32_t max_iter, stag_solve_info* info);
 
 /* Largest V/2 that stag_apply_A_noalloc accepts. */
 #define STAG_NOALLOC_MAX_HALF_SITES 65536

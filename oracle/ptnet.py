@@ -17,8 +17,9 @@ preconditioner of flexible CG.  Definitions:
   * the network: the residual r (even sites) is embedded on the full lattice
     (zero on odd sites), passed through the layers, and the last layer's
     single channel is restricted to even sites: M(r).
-  * loss of a pair (r, e), in the energy norm of A (the norm CG minimises):
-        d = M(r) - e,   L = <d, A d> / <e, A e>.
+  * loss of a pair (r, e): the residual norm of the correction, i.e. the
+    error d = M(r) - e in the norm |A .|:
+        L = |A d|^2 / |A e|^2.
   * flexible CG (Notay 2000): z_k = M(r_k), p_0 = z_0,
     alpha = (r_k, z_k) / (p_k, A p_k), x += alpha p, r -= alpha A p,
     beta = (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k), p = z_{k+1} + beta p.
@@ -77,10 +78,11 @@ class PTNet:
         return st.restrict(self.activations(r_even)[-1][0], self.dims, 0)
 
     def loss(self, r_even, e_even, apply_A):
-        """<d, A d> / <e, A e> with d = M(r) - e; apply_A acts on [V/2, 3] vectors."""
+        """|A d|^2 / |A e|^2 with d = M(r) - e; apply_A acts on [V/2, 3] vectors."""
         e = np.asarray(e_even, dtype=np.complex128).reshape(-1, 3)
-        d = self.apply(r_even) - e
-        return float(np.vdot(d, apply_A(d)).real / np.vdot(e, apply_A(e)).real)
+        ad = apply_A(self.apply(r_even) - e)
+        ae = apply_A(e)
+        return float(np.vdot(ad, ad).real / np.vdot(ae, ae).real)
 
 
 def fcg(apply_A, precond, b, x0=None, tol=1e-10, max_iter=10000):

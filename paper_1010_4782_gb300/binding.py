@@ -27,6 +27,7 @@ STAG_ARITH_F64 = 0
 STAG_ARITH_FF = 1
 STAG_ARITH_F32 = 2
 STAG_ARITH_F16 = 3
+STAG_ARITH_BF16 = 4
 
 STAG_INNER_NONE = 0
 STAG_INNER_F32 = 1
@@ -63,6 +64,19 @@ EXPORTED = (
     "stag_batch_last_error",
     "stag_batch_device_bytes",
     "stag_batch_destroy",
+    "stag_ptnet_create",
+    "stag_ptnet_num_weights",
+    "stag_ptnet_set_weights",
+    "stag_ptnet_get_weights",
+    "stag_ptnet_apply",
+    "stag_ptnet_loss_grad",
+    "stag_ptnet_add_pairs",
+    "stag_ptnet_num_pairs",
+    "stag_ptnet_train",
+    "stag_ptnet_dataset_loss",
+    "stag_ptnet_last_error",
+    "stag_ptnet_destroy",
+    "stag_fcg_solve",
 )
 
 
@@ -153,9 +167,24 @@ def load(path: str | None = None):
     lib.stag_batch_device_bytes.argtypes = [H]
     lib.stag_batch_device_bytes.restype = ctypes.c_int64
     lib.stag_batch_destroy.argtypes = [H]
+    lib.stag_ptnet_create.argtypes = [ctypes.POINTER(H), H, i32, ctypes.c_uint64]
+    lib.stag_ptnet_num_weights.argtypes = [H]
+    lib.stag_ptnet_num_weights.restype = ctypes.c_int64
+    lib.stag_ptnet_set_weights.argtypes = [H, P, ctypes.c_int64]
+    lib.stag_ptnet_get_weights.argtypes = [H, P, ctypes.c_int64]
+    lib.stag_ptnet_apply.argtypes = [H, P, P]
+    lib.stag_ptnet_loss_grad.argtypes = [H, P, P, ctypes.POINTER(d), P]
+    lib.stag_ptnet_add_pairs.argtypes = [H, i32, PP, i32, d, i32, ctypes.POINTER(i32)]
+    lib.stag_ptnet_num_pairs.argtypes = [H]
+    lib.stag_ptnet_train.argtypes = [H, i32, i32, d, ctypes.c_uint64, P]
+    lib.stag_ptnet_dataset_loss.argtypes = [H, ctypes.POINTER(d)]
+    lib.stag_ptnet_last_error.argtypes = [H]
+    lib.stag_ptnet_last_error.restype = ctypes.c_char_p
+    lib.stag_ptnet_destroy.argtypes = [H]
+    lib.stag_fcg_solve.argtypes = [H, H, P, P, d, i32, ctypes.POINTER(stag_solve_info)]
     for name in EXPORTED:
         if name not in ("stag_last_error", "stag_device_bytes", "stag_launch_count", "stag_batch_last_error",
-                        "stag_batch_device_bytes"):
+                        "stag_batch_device_bytes", "stag_ptnet_num_weights", "stag_ptnet_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -326,6 +355,78 @@ def stag_batch_device_bytes(h) -> int:
 def stag_batch_destroy(h):
     if h is not None:
         load().stag_batch_destroy(h)
+
+
+def _pcheck(code, net, h=None):
+    if code != STAG_OK:
+        msg = load().stag_ptnet_last_error(net).decode()
+        if h is not None:
+            msg += " / " + stag_last_error(h)
+        raise StagError(code, msg)
+
+
+def stag_ptnet_create(h, precision=STAG_ARITH_BF16, seed=0):
+    n = ctypes.c_void_p()
+    code = load().stag_ptnet_create(ctypes.byref(n), h, int(precision), int(seed))
+    if code != STAG_OK:
+        raise StagError(code, stag_last_error(h))
+    return n
+
+
+def stag_ptnet_weights(net):
+    nw = int(load().stag_ptnet_num_weights(net))
+    w = np.zeros(nw, dtype=np.complex128)
+    _pcheck(load().stag_ptnet_get_weights(net, w.ctypes.data, nw), net)
+    return w
+
+
+def stag_ptnet_set_weights(net, w):
+    w = np.ascontiguousarray(w, dtype=np.complex128)
+    _pcheck(load().stag_ptnet_set_weights(net, w.ctypes.data, w.size), net)
+
+
+def stag_ptnet_apply(net, r, z):
+    _pcheck(load().stag_ptnet_apply(net, _ptr(r), _ptr(z)), net)
+
+
+def stag_ptnet_loss_grad(net, r, e):
+    nw = int(load().stag_ptnet_num_weights(net))
+    loss = ctypes.c_double()
+    g = np.zeros(nw, dtype=np.complex128)
+    _pcheck(load().stag_ptnet_loss_grad(net, _ptr(r), _ptr(e), ctypes.byref(loss), g.ctypes.data), net)
+    return loss.value, g
+
+
+def stag_ptnet_add_pairs(net, sources, stride, min_rel_residual=1e-6, max_pairs=2000):
+    npairs = ctypes.c_int32()
+    _pcheck(load().stag_ptnet_add_pairs(net, len(sources), _ptr_array(sources), int(stride), float(min_rel_residual),
+                                        int(max_pairs), ctypes.byref(npairs)), net)
+    return npairs.value
+
+
+def stag_ptnet_train(net, epochs, batch, lr, seed=0):
+    losses = np.zeros(max(1, epochs), dtype=np.float64)
+    _pcheck(load().stag_ptnet_train(net, int(epochs), int(batch), float(lr), int(seed), losses.ctypes.data), net)
+    return losses[:epochs]
+
+
+def stag_ptnet_dataset_loss(net):
+    v = ctypes.c_double()
+    _pcheck(load().stag_ptnet_dataset_loss(net, ctypes.byref(v)), net)
+    return v.value
+
+
+def stag_ptnet_destroy(net):
+    if net is not None:
+        load().stag_ptnet_destroy(net)
+
+
+def stag_fcg_solve(h, net, b, x, tol, max_iter=0):
+    info = stag_solve_info()
+    code = load().stag_fcg_solve(h, net, _ptr(b), _ptr(x), float(tol), int(max_iter), ctypes.byref(info))
+    if code not in (STAG_OK, STAG_ERR_NOT_CONVERGED):
+        _check(code, h)
+    return code, info.as_dict()
 
 
 class Handle:

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/stag.h"
+#include "handle.h"
 #include "stag_kernels.h"
 
 using namespace stag;
@@ -28,58 +29,7 @@ struct Fail {
     int code;
 };
 
-struct KernelStat {
-    double ms = 0.0;
-    long long launches = 0;
-};
-
 }  // namespace
-
-struct stag_handle {
-    Geom g{};
-    int device = 0;
-    double mass = 0.0;
-    bool naik = false;
-    stag_options opt{};
-    cudaStream_t user_stream = nullptr;
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev_in = nullptr;
-    // links
-    double2* fat64 = nullptr;
-    double2* lng64 = nullptr;
-    float4* fatff = nullptr;
-    float4* lngff = nullptr;
-    // vectors: 16 bytes per complex, [3][vs]
-    double2 *x = nullptr, *r = nullptr, *ad = nullptr, *b = nullptr;
-    void* d = nullptr;   // CG direction (F64 or FF)
-    void* t = nullptr;   // odd-parity intermediate (F64 or FF)
-    void* u = nullptr;   // scratch even vector (F64 or FF)
-    float4* xff = nullptr;   // FF: solution increment since the last fold into x
-    // mixed precision: low-precision links and inner vectors
-    float2* fat32 = nullptr;
-    float2* lng32 = nullptr;
-    __half2* fat16 = nullptr;
-    __half2* lng16 = nullptr;
-    void* lo_d = nullptr;    // [3][vs] float2 (F32) or __half2 (F16)
-    void* lo_t = nullptr;
-    void* lo_ad = nullptr;
-    void* lo_r = nullptr;
-    float2* lo_y = nullptr;  // solution increment since the last replacement, FP32
-    double* io_a = nullptr;  // ABI-layout staging [vh][3] complex
-    double* io_b = nullptr;
-    // reductions
-    double* partials = nullptr;
-    CgScalars* scal = nullptr;
-    CgScalars* scal_host = nullptr;  // pinned
-    // graphs
-    cudaGraphExec_t graph = nullptr;
-    // timing
-    std::vector<cudaEvent_t> events;
-    KernelStat stats[STAG_KERNEL_COUNT];
-    long long device_bytes = 0;
-    long long launches = 0;  // kernels launched by this handle (graph replays counted per kernel)
-    std::string err = "no error";
-};
 
 namespace {
 
@@ -291,6 +241,7 @@ void run_fig1(stag_handle* h) {
             launch_check(h, "CG iteration");
         }
         read_state(h);
+        if (h->block_hook) h->block_hook();
         if (timing) {
             const long long active = h->scal_host->iter - iter_before;
             for (long long k = 0; k < active && k < K; ++k) {
@@ -479,11 +430,108 @@ void solve_mixed(stag_handle* h, double bnorm2, double tol, long long max_it, st
     inf.iter_rel_residual = rel;
 }
 
+// Plain CG (Fig. 1) with the true-residual check and restarts, on vectors
+// already packed into h->b and h->x.
+void solve_plain(stag_handle* h, double bnorm2, double tol, long long max_it, stag_solve_info& inf, int& status,
+                 double& rel) {
+    const Geom& g = h->g;
+    const double threshold = tol * tol * bnorm2;
+    const double m2 = h->mass * h->mass;
+    const bool ff = use_ff(h);
+    apply_A_f64(h, h->x, h->ad);  // A x for r = b - A x
+    long long iters = 0;
+    int restarts = 0;
+    while (true) {
+        launch_cg_reset(h->scal, threshold, m2, max_it - iters, h->s);
+        if (ff)
+            launch_cg_init_ff(g, h->b, h->ad, reinterpret_cast<float4*>(h->r), static_cast<float4*>(h->d), h->xff,
+                              h->scal, h->partials, h->s);
+        else
+            launch_cg_init(g, h->b, h->ad, h->r, static_cast<double2*>(h->d), h->scal, h->partials, h->s);
+        h->launches += 2;
+        launch_check(h, "CG init");
+        run_fig1(h);
+        iters += h->scal_host->iter;
+        inf.iter_rel_residual = std::sqrt(h->scal_host->delta_new / bnorm2);
+        const bool breakdown = h->scal_host->status != 0;
+        // true residual with native FP64 arithmetic
+        apply_A_f64(h, h->x, h->ad);
+        launch_norm2_diff(g, h->b, h->ad, h->scal, h->partials, h->s);
+        h->launches += 1;
+        launch_check(h, "true residual");
+        rel = std::sqrt(read_red_out(h) / bnorm2);
+        if (breakdown) {
+            status = STAG_ERR_BREAKDOWN;
+            h->err = "CG breakdown: d^dag A d <= 0 or non-finite";
+            break;
+        }
+        if (rel <= tol) break;
+        if (iters >= max_it || restarts >= h->opt.max_restarts) {
+            status = STAG_ERR_NOT_CONVERGED;
+            h->err = "not converged: true residual " + std::to_string(rel) + " after " + std::to_string(iters) +
+                     " iterations";
+            break;
+        }
+        ++restarts;
+    }
+    inf.iters = (int32_t)iters;
+    inf.restarts = restarts;
+}
+
 }  // namespace
 
 namespace stag {
 // Error message of a handle-free call, read with stag_last_error(NULL).
 void set_noalloc_error(const std::string& msg) { g_create_error = msg; }
+
+void handle_apply_A_f64(stag_handle* h, const double2* in, double2* out) {
+    try {
+        apply_A_f64(h, in, out);
+    } catch (const Fail& f) {
+        throw HandleError{f.code};
+    }
+}
+
+int handle_solve_packed(stag_handle* h, double bnorm2, double tol, long long max_it, stag_solve_info& info) {
+    int status = STAG_OK;
+    if (max_it <= 0) max_it = 3LL * h->g.vh;
+    double rel = 0.0;
+    try {
+        if (h->opt.inner != STAG_INNER_NONE)
+            solve_mixed(h, bnorm2, tol, max_it, info, status, rel);
+        else
+            solve_plain(h, bnorm2, tol, max_it, info, status, rel);
+    } catch (const Fail& f) {
+        throw HandleError{f.code};
+    }
+    info.true_rel_residual = rel;
+    info.status = status;
+    return status;
+}
+
+void handle_begin(stag_handle* h) {
+    try {
+        begin_call(h);
+    } catch (const Fail& f) {
+        throw HandleError{f.code};
+    }
+}
+
+void handle_end(stag_handle* h) {
+    try {
+        end_call(h);
+    } catch (const Fail& f) {
+        throw HandleError{f.code};
+    }
+}
+
+bool handle_is_device_ptr(stag_handle* h, const void* p) {
+    try {
+        return is_device_ptr(h, p);
+    } catch (const Fail& f) {
+        throw HandleError{f.code};
+    }
+}
 }  // namespace stag
 
 // ====================================================================== ABI
@@ -807,52 +855,10 @@ int stag_cg_solve(stag_handle* h, const double* b_even, double* x_even, double t
         if (bnorm2 == 0.0) {
             cuda_check(h, cudaMemsetAsync(h->x, 0, vec_bytes(g), h->s), "zero x");
         } else {
-            const double threshold = tol * tol * bnorm2;
-            const double m2 = h->mass * h->mass;
-            const bool ff = use_ff(h);
-            if (h->opt.inner != STAG_INNER_NONE) {
+            if (h->opt.inner != STAG_INNER_NONE)
                 solve_mixed(h, bnorm2, tol, max_it, inf, status, rel);
-            } else {
-                apply_A_f64(h, h->x, h->ad);  // A x for r = b - A x
-                long long iters = 0;
-                int restarts = 0;
-                while (true) {
-                    launch_cg_reset(h->scal, threshold, m2, max_it - iters, h->s);
-                    if (ff)
-                        launch_cg_init_ff(g, h->b, h->ad, reinterpret_cast<float4*>(h->r), static_cast<float4*>(h->d),
-                                          h->xff, h->scal, h->partials, h->s);
-                    else
-                        launch_cg_init(g, h->b, h->ad, h->r, static_cast<double2*>(h->d), h->scal, h->partials,
-                                       h->s);
-                    h->launches += 2;
-                    launch_check(h, "CG init");
-                    run_fig1(h);
-                    iters += h->scal_host->iter;
-                    inf.iter_rel_residual = std::sqrt(h->scal_host->delta_new / bnorm2);
-                    const bool breakdown = h->scal_host->status != 0;
-                    // true residual with native FP64 arithmetic
-                    apply_A_f64(h, h->x, h->ad);
-                    launch_norm2_diff(g, h->b, h->ad, h->scal, h->partials, h->s);
-                    h->launches += 1;
-                    launch_check(h, "true residual");
-                    rel = std::sqrt(read_red_out(h) / bnorm2);
-                    if (breakdown) {
-                        status = STAG_ERR_BREAKDOWN;
-                        h->err = "CG breakdown: d^dag A d <= 0 or non-finite";
-                        break;
-                    }
-                    if (rel <= tol) break;
-                    if (iters >= max_it || restarts >= h->opt.max_restarts) {
-                        status = STAG_ERR_NOT_CONVERGED;
-                        h->err = "not converged: true residual " + std::to_string(rel) + " after " +
-                                 std::to_string(iters) + " iterations";
-                        break;
-                    }
-                    ++restarts;
-                }
-                inf.iters = (int32_t)iters;
-                inf.restarts = restarts;
-            }
+            else
+                solve_plain(h, bnorm2, tol, max_it, inf, status, rel);
         }
         inf.true_rel_residual = rel;
         double* dst = x_dev ? x_even : h->io_b;

@@ -1,0 +1,1261 @@
+// pt.cu - learned preconditioner: a gauge-covariant parallel-transport network,
+// its training on the GPU with the library's own forward / adjoint /
+// weight-gradient kernels, and flexible CG that uses it.
+//
+// The paper's CG (Sec. 2, Fig. 1) has no preconditioner; this is an added form
+// built on the same operator.  Network (the oracle in oracle/ptnet.py states
+// the same definitions):
+//   paths p = 0..8: identity, and p = 1 + 2 mu + s transporting from x + mu
+//   (s = 0: U_mu(x) psi(x+mu)) or x - mu (s = 1: U_mu(x-mu)^dag psi(x-mu)) with the
+//   operator's eta-folded fat links, so that sum_mu (T_{+mu} - T_{-mu}) = D;
+//   layer: psi_l(x, o) = sum_p sum_i W_l[p][o][i] (T_p psi_{l-1, i})(x);
+//   three layers with 1 -> 8 -> 8 -> 1 complex channels on the whole lattice;
+//   input: the residual on even sites (zero on odd sites); output: the last
+//   channel on even sites.  Linear and gauge covariant.
+// Training pairs (r_k, e_k = x* - x_k) are snapshots of plain-CG solves of
+// caller-supplied sources, scaled by 1/|r_k|; loss: the residual norm of the
+// correction, L = |A d|^2 / |A e|^2 with d = M r - e (the least-squares
+// polynomial-preconditioning objective: it weights the modes of A by lambda^2,
+// so the network fits lambda M(lambda) ~ 1 on the bulk of the spectrum), A
+// applied with the FP32 Dirac kernels; Adam on the real and imaginary parts of
+// the weights.  Activations are stored
+// as BF16 (or FP32, for gradient checks) and every sum runs in FP32.
+//
+// Gradients (Wirtinger, G = dL/d conj(W)):
+//   output seed  g_3 = A (A d) / |A e|^2 on even sites, 0 on odd sites;
+//   data         g_{l-1}(x, i) = sum_p sum_o conj(W_l[p][o][i]) (T_p^dag g_{l,o})(x),
+//                T_{+mu}^dag = T_{-mu}, T_{-mu}^dag = T_{+mu};
+//   weights      G_l[p][o][i] = sum_x sum_c conj((T_p psi_{l-1,i})(x)_c) g_{l,o}(x)_c.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <random>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/stag.h"
+#include "ff.cuh"
+#include "handle.h"
+#include "stag_kernels.h"
+
+namespace stag {
+
+constexpr int kPaths = 9;
+constexpr int kHidden = 8;
+constexpr int kLayers = 3;
+constexpr int kChan[kLayers + 1] = {1, kHidden, kHidden, 1};
+constexpr int kWgradBlocks = 608;  // x-blocks of the weight-gradient grid (4 per SM)
+
+__device__ __forceinline__ float2 ldc(const float2* p) { return *p; }
+__device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+__device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+
+// whole-lattice field: [channel][colour][parity][vs]
+__device__ __forceinline__ size_t fidx(int ch, int c, int P, int i, size_t vs) {
+    return ((size_t)(ch * 3 + c) * 2 + P) * vs + i;
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulf_conj(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ int pt_neighbour(const Geom& g, int x, int y, int z, int t, int mu, bool up) {
+    switch (mu) {
+        case 0: x = up ? wrap_up(x, 1, g.lx) : wrap_dn(x, 1, g.lx); break;
+        case 1: y = up ? wrap_up(y, 1, g.ly) : wrap_dn(y, 1, g.ly); break;
+        case 2: z = up ? wrap_up(z, 1, g.lz) : wrap_dn(z, 1, g.lz); break;
+        default: t = up ? wrap_up(t, 1, g.lt) : wrap_dn(t, 1, g.lt); break;
+    }
+    return site_index(x, y, z, t, g);
+}
+
+// Source site (parity Pn, index nb) and link of transport direction d
+// (0: from x + mu with U_mu(x); 1: from x - mu with U_mu(x - mu)^dag).
+struct Hop {
+    int Pn, nb;
+    const float2* u;
+};
+
+__device__ __forceinline__ Hop pt_hop(const Geom& g, const float2* links, int P, int i, int x, int y, int z, int t,
+                                      int mu, int d) {
+    Hop h;
+    h.Pn = 1 - P;
+    const size_t vs = (size_t)g.vs;
+    if (d == 0) {
+        h.nb = pt_neighbour(g, x, y, z, t, mu, true);
+        h.u = links + ((size_t)(P * 4 + mu) * 9) * vs + i;
+    } else {
+        h.nb = pt_neighbour(g, x, y, z, t, mu, false);
+        h.u = links + ((size_t)((1 - P) * 4 + mu) * 9) * vs + h.nb;
+    }
+    return h;
+}
+
+// t = U v (d = 0) or U^dag v (d = 1)
+__device__ __forceinline__ void pt_apply(const float2 (&U)[9], int d, const float2 (&v)[3], float2 (&t)[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 u = d == 0 ? U[3 * r + c] : U[3 * c + r];
+            const float2 m = d == 0 ? cmulf(u, v[c]) : cmulf_conj(u, v[c]);
+            a.x += m.x;
+            a.y += m.y;
+        }
+        t[r] = a;
+    }
+}
+
+// One layer (ADJ = false) or its adjoint (ADJ = true; CIN / COUT are then the
+// forward layer's output / input channel counts, w its forward weights).
+template <int CIN, int COUT, class TI, class TO, bool ADJ>
+__global__ void __launch_bounds__(256) pt_layer_kernel(Geom g, const float2* __restrict__ links,
+                                                       const float2* __restrict__ w, const TI* __restrict__ in,
+                                                       TO* __restrict__ out) {
+    __shared__ float2 sw[kPaths * CIN * COUT];
+    for (int k = threadIdx.x; k < kPaths * CIN * COUT; k += blockDim.x) sw[k] = w[k];
+    __syncthreads();
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= 2 * g.vh) return;
+    const int P = n >= g.vh ? 1 : 0;
+    const int i = n - P * g.vh;
+    const size_t vs = (size_t)g.vs;
+    int x, y, z, t;
+    site_coords(i, P, g, x, y, z, t);
+    float2 acc[COUT][3];
+#pragma unroll
+    for (int o = 0; o < COUT; ++o)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[o][c] = make_float2(0.f, 0.f);
+    for (int p = 0; p < kPaths; ++p) {
+        int Pn = P, nb = i, d = 0;
+        float2 U[9];
+        if (p > 0) {
+            const int mu = (p - 1) >> 1, s = (p - 1) & 1;
+            d = ADJ ? 1 - s : s;
+            const Hop hp = pt_hop(g, links, P, i, x, y, z, t, mu, d);
+            Pn = hp.Pn;
+            nb = hp.nb;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+        }
+#pragma unroll
+        for (int ci = 0; ci < CIN; ++ci) {
+            float2 v[3], tv[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[c] = ldc(in + fidx(ci, c, Pn, nb, vs));
+            if (p > 0) {
+                pt_apply(U, d, v, tv);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tv[c] = v[c];
+            }
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) {
+                const float2 wv = ADJ ? make_float2(sw[(p * CIN + ci) * COUT + o].x, -sw[(p * CIN + ci) * COUT + o].y)
+                                      : sw[(p * COUT + o) * CIN + ci];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 m = cmulf(wv, tv[c]);
+                    acc[o][c].x += m.x;
+                    acc[o][c].y += m.y;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < COUT; ++o)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stc(out + fidx(o, c, P, i, vs), acc[o][c]);
+}
+
+// partials[blk][p][o][i] = sum over the block's sites of
+// sum_c conj((T_p psi_i)(x)_c) g_o(x)_c, o in [o0, o0 + OC), path p = blockIdx.y.
+template <int CIN, int OC, class T>
+__global__ void __launch_bounds__(256) pt_wgrad_kernel(Geom g, const float2* __restrict__ links,
+                                                       const T* __restrict__ psi, const T* __restrict__ gout,
+                                                       int cout, float2* __restrict__ partials) {
+    const int p = blockIdx.y;
+    const int o0 = blockIdx.z * OC;
+    const size_t vs = (size_t)g.vs;
+    float2 acc[OC][CIN];
+#pragma unroll
+    for (int oo = 0; oo < OC; ++oo)
+#pragma unroll
+        for (int ci = 0; ci < CIN; ++ci) acc[oo][ci] = make_float2(0.f, 0.f);
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < 2 * g.vh; n += gridDim.x * blockDim.x) {
+        const int P = n >= g.vh ? 1 : 0;
+        const int i = n - P * g.vh;
+        int x, y, z, t;
+        site_coords(i, P, g, x, y, z, t);
+        int Pn = P, nb = i, d = 0;
+        float2 U[9];
+        if (p > 0) {
+            const int mu = (p - 1) >> 1;
+            d = (p - 1) & 1;
+            const Hop hp = pt_hop(g, links, P, i, x, y, z, t, mu, d);
+            Pn = hp.Pn;
+            nb = hp.nb;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+        }
+        float2 gv[OC][3];
+#pragma unroll
+        for (int oo = 0; oo < OC; ++oo)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gv[oo][c] = ldc(gout + fidx(o0 + oo, c, P, i, vs));
+#pragma unroll
+        for (int ci = 0; ci < CIN; ++ci) {
+            float2 v[3], tv[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[c] = ldc(psi + fidx(ci, c, Pn, nb, vs));
+            if (p > 0) {
+                pt_apply(U, d, v, tv);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tv[c] = v[c];
+            }
+#pragma unroll
+            for (int oo = 0; oo < OC; ++oo)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 m = cmulf_conj(tv[c], gv[oo][c]);
+                    acc[oo][ci].x += m.x;
+                    acc[oo][ci].y += m.y;
+                }
+        }
+    }
+    __shared__ float2 sred[256 / 32][OC * CIN];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int oo = 0; oo < OC; ++oo)
+#pragma unroll
+        for (int ci = 0; ci < CIN; ++ci) {
+            float2 v = acc[oo][ci];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+            }
+            if (lane == 0) sred[wp][oo * CIN + ci] = v;
+        }
+    __syncthreads();
+    for (int k = threadIdx.x; k < OC * CIN; k += blockDim.x) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int q = 0; q < (int)(blockDim.x / 32); ++q) {
+            s.x += sred[q][k].x;
+            s.y += sred[q][k].y;
+        }
+        const int oo = k / CIN, ci = k % CIN;
+        partials[(((size_t)blockIdx.x * kPaths + p) * cout + o0 + oo) * CIN + ci] = s;
+    }
+}
+
+// grad[p][o][i] += sum over blocks of partials (block order)
+__global__ void pt_wgrad_sum_kernel(const float2* __restrict__ partials, int nblk, int nw, float2* grad) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nw) return;
+    float2 s = make_float2(0.f, 0.f);
+    for (int b = 0; b < nblk; ++b) {
+        s.x += partials[(size_t)b * nw + k].x;
+        s.y += partials[(size_t)b * nw + k].y;
+    }
+    grad[k].x += s.x;
+    grad[k].y += s.y;
+}
+
+// act0 = embed(scale * r): even sites from an even-site vector, odd sites zero.
+template <class TS, class T>
+__global__ void __launch_bounds__(kBlock) pt_embed_kernel(Geom g, const TS* __restrict__ src, double scale,
+                                                          T* __restrict__ act0) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float2 v;
+        if constexpr (std::is_same<TS, double2>::value) {
+            const double2 d = src[c * vs + i];
+            v = make_float2((float)(d.x * scale), (float)(d.y * scale));
+        } else {
+            v = ldc(src + c * vs + i);
+        }
+        stc(act0 + fidx(0, c, 0, i, vs), v);
+        stc(act0 + fidx(0, c, 1, i, vs), make_float2(0.f, 0.f));
+    }
+}
+
+// out (FP64 even SoA) = scale * act3 on even sites
+template <class T>
+__global__ void __launch_bounds__(kBlock) pt_extract_kernel(Geom g, const T* __restrict__ act3, double scale,
+                                                            double2* __restrict__ out) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 v = ldc(act3 + fidx(0, c, 0, i, vs));
+        out[c * vs + i] = make_double2(scale * (double)v.x, scale * (double)v.y);
+    }
+}
+
+// d = act3 - e on even sites, as an FP32 SoA vector [3][vs]
+template <class T>
+__global__ void __launch_bounds__(kBlock) pt_diff_kernel(Geom g, const T* __restrict__ act3, const T* __restrict__ e,
+                                                         float2* __restrict__ d) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 o = ldc(act3 + fidx(0, c, 0, i, vs));
+        const float2 t = ldc(e + c * vs + i);
+        d[c * vs + i] = make_float2(o.x - t.x, o.y - t.y);
+    }
+}
+
+// g3 = v * inv on even sites (0 on odd)
+template <class T>
+__global__ void __launch_bounds__(kBlock) pt_seed_kernel(Geom g, const float2* __restrict__ v, float inv,
+                                                         T* __restrict__ g3) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 a = v[c * vs + i];
+        stc(g3 + fidx(0, c, 0, i, vs), make_float2(a.x * inv, a.y * inv));
+        stc(g3 + fidx(0, c, 1, i, vs), make_float2(0.f, 0.f));
+    }
+}
+
+// FP32 copy [3][vs] of a slot
+template <class T>
+__global__ void __launch_bounds__(kBlock) pt_slot_f32_kernel(Geom g, const T* __restrict__ slot, float2* __restrict__ out) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c * vs + i] = ldc(slot + c * vs + i);
+}
+
+// per-block partials of Re<a, b> for FP32 [3][vs] vectors (FP64 sums)
+__global__ void __launch_bounds__(kBlock) pt_dot_f32_kernel(Geom g, const float2* __restrict__ a,
+                                                            const float2* __restrict__ b, double* __restrict__ partials) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    double acc = 0.0;
+    if (i < g.vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 x = a[c * vs + i], y = b[c * vs + i];
+            acc += (double)x.x * y.x + (double)x.y * y.y;
+        }
+    }
+    __shared__ double sm[kBlock / 32];
+    const double s = block_sum<kBlock>(acc, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// |v|^2 of an even-site vector (T, [3][vs]) -> per-block partials (FP64)
+template <class T>
+__global__ void __launch_bounds__(kBlock) pt_norm2_kernel(Geom g, const T* __restrict__ v, double* partials) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    double acc = 0.0;
+    if (i < g.vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 a = ldc(v + c * vs + i);
+            acc += (double)a.x * a.x + (double)a.y * a.y;
+        }
+    }
+    __shared__ double sm[kBlock / 32];
+    const double s = block_sum<kBlock>(acc, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// slot (T, even [3][vs]) = scale * v, v an FP64 or float-float SoA vector
+template <class TS, class T>
+__global__ void __launch_bounds__(kBlock) pt_store_slot_kernel(Geom g, const TS* __restrict__ v, double scale,
+                                                               T* __restrict__ slot) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double2 d;
+        if constexpr (std::is_same<TS, float4>::value)
+            d = ff_to_complex(v[c * vs + i]);
+        else
+            d = v[c * vs + i];
+        stc(slot + c * vs + i, make_float2((float)(d.x * scale), (float)(d.y * scale)));
+    }
+}
+
+// slot = scale * (a - b), FP64 inputs
+template <class T>
+__global__ void __launch_bounds__(kBlock) pt_store_diff_kernel(Geom g, const double2* __restrict__ a,
+                                                               const double2* __restrict__ b, double scale,
+                                                               T* __restrict__ slot) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double2 x = a[c * vs + i], y = b[c * vs + i];
+        stc(slot + c * vs + i, make_float2((float)((x.x - y.x) * scale), (float)((x.y - y.y) * scale)));
+    }
+}
+
+// Adam on the real and imaginary parts: grad is sum_batch dL/dconj(W); dL/d(Re, Im) = 2 (Re, Im) / batch
+__global__ void pt_adam_kernel(float* w, const float* grad, float* m, float* v, int n, float gscale, float lr,
+                               float b1, float b2, float c1, float c2, float eps) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float gk = grad[k] * gscale;
+    const float mk = b1 * m[k] + (1.f - b1) * gk;
+    const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    w[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+}
+
+// FP32 copy of the eta-folded FP64 links
+__global__ void pt_links_kernel(const double2* __restrict__ in, float2* __restrict__ out, size_t n) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = make_float2((float)in[k].x, (float)in[k].y);
+}
+
+// --------------------------------------------------- flexible CG vectors
+// per-block partials of Re<a, b>, Re<a, c>, <b, b> (FP64)
+__global__ void __launch_bounds__(kBlock) fcg_dots_kernel(Geom g, const double2* __restrict__ a,
+                                                          const double2* __restrict__ b, const double2* __restrict__ c,
+                                                          double* __restrict__ partials, int nblk) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    double ab = 0.0, ac = 0.0, bb = 0.0;
+    if (i < g.vh) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double2 x = a[k * vs + i], y = b[k * vs + i];
+            ab = fma(x.x, y.x, fma(x.y, y.y, ab));
+            bb = fma(y.x, y.x, fma(y.y, y.y, bb));
+            if (c) {
+                const double2 zz = c[k * vs + i];
+                ac = fma(x.x, zz.x, fma(x.y, zz.y, ac));
+            }
+        }
+    }
+    __shared__ double sm[kBlock / 32];
+    const double s0 = block_sum<kBlock>(ab, sm);
+    __syncthreads();
+    const double s1 = block_sum<kBlock>(ac, sm);
+    __syncthreads();
+    const double s2 = block_sum<kBlock>(bb, sm);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s0;
+        partials[nblk + blockIdx.x] = s1;
+        partials[2 * nblk + blockIdx.x] = s2;
+    }
+}
+
+// r_old = r; x += alpha p; r -= alpha q
+__global__ void __launch_bounds__(kBlock) fcg_update_kernel(Geom g, double2* x, double2* r, double2* r_old,
+                                                            const double2* __restrict__ p,
+                                                            const double2* __restrict__ q, double alpha) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const size_t j = k * vs + i;
+        const double2 pp = p[j], qq = q[j], rr = r[j];
+        double2 xx = x[j];
+        r_old[j] = rr;
+        xx.x = fma(alpha, pp.x, xx.x);
+        xx.y = fma(alpha, pp.y, xx.y);
+        x[j] = xx;
+        r[j] = make_double2(fma(-alpha, qq.x, rr.x), fma(-alpha, qq.y, rr.y));
+    }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(kBlock) fcg_dir_kernel(Geom g, double2* p, const double2* __restrict__ z,
+                                                         double beta) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const size_t j = k * vs + i;
+        const double2 pp = p[j], zz = z[j];
+        p[j] = make_double2(fma(beta, pp.x, zz.x), fma(beta, pp.y, zz.y));
+    }
+}
+
+// r = b - q
+__global__ void __launch_bounds__(kBlock) fcg_sub_kernel(Geom g, double2* r, const double2* __restrict__ b,
+                                                         const double2* __restrict__ q) {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const size_t j = k * vs + i;
+        r[j] = make_double2(b[j].x - q[j].x, b[j].y - q[j].y);
+    }
+}
+
+}  // namespace stag
+
+using namespace stag;
+
+// =========================================================== the network
+struct stag_ptnet {
+    stag_handle* h = nullptr;
+    Geom g{};
+    int prec = STAG_ARITH_BF16;  // activation storage: STAG_ARITH_BF16 or STAG_ARITH_F32
+    size_t elem = 4;             // bytes per stored complex
+    float2* links = nullptr;     // FP32 eta-folded fat links (transports and A)
+    float2* lng = nullptr;       // FP32 eta-folded Naik links (A), or nullptr
+    float2 *va = nullptr, *vt = nullptr, *vad = nullptr;  // FP32 [3][vs] vectors for A d
+    std::vector<float2> w_host;  // weights, layer-major [9][C_out][C_in]
+    float2* w = nullptr;         // device weights (FP32 master)
+    float2* grad = nullptr;
+    float *adam_m = nullptr, *adam_v = nullptr;
+    long long adam_t = 0;
+    void* act[kLayers + 1] = {};  // activations (whole lattice)
+    void* gact[kLayers + 1] = {}; // gradients of activations
+    float2* wpart = nullptr;      // weight-gradient partials
+    double* red = nullptr;        // reduction partials
+    std::vector<double> red_host;
+    // training pairs: r and e slots (even sites, [3][vs]) and <e, A e>
+    std::vector<void*> pairs_r, pairs_e;
+    std::vector<double> pairs_eae;
+    void* scratch_r = nullptr;  // slots for stag_ptnet_loss_grad
+    void* scratch_e = nullptr;
+    // flexible CG vectors (FP64 SoA)
+    double2 *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr, *fro = nullptr;
+    long long device_bytes = 0;
+    std::string err = "no error";
+};
+
+namespace {
+
+struct PFail {
+    int code;
+};
+
+int layer_offset(int l) {  // complex weights before layer l (0-based)
+    int off = 0;
+    for (int k = 0; k < l; ++k) off += kPaths * kChan[k + 1] * kChan[k];
+    return off;
+}
+int n_weights() { return layer_offset(kLayers); }
+
+void pfail(stag_ptnet* n, int code, const std::string& msg) {
+    if (n) n->err = msg;
+    throw PFail{code};
+}
+
+void pcheck(stag_ptnet* n, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    pfail(n, e == cudaErrorMemoryAllocation ? STAG_ERR_OOM : STAG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* palloc(stag_ptnet* n, size_t bytes, const char* what) {
+    void* p = nullptr;
+    pcheck(n, cudaMalloc(&p, bytes), what);
+    n->device_bytes += (long long)bytes;
+    pcheck(n, cudaMemsetAsync(p, 0, bytes, n->h->s), what);
+    return p;
+}
+
+cudaStream_t S(stag_ptnet* n) { return n->h->s; }
+size_t field_bytes(const stag_ptnet* n, int ch) { return (size_t)ch * 3 * 2 * n->g.vs * n->elem; }
+size_t slot_bytes(const stag_ptnet* n) { return (size_t)3 * n->g.vs * n->elem; }
+int site_blocks(const Geom& g) { return blocks_for(2 * g.vh); }
+
+template <class T>
+void layer_fwd(stag_ptnet* n, int l, const T* in, T* out) {
+    const Geom& g = n->g;
+    const float2* w = n->w + layer_offset(l);
+    const int nb = site_blocks(g);
+    if (l == 0)
+        pt_layer_kernel<1, kHidden, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
+    else if (l == 1)
+        pt_layer_kernel<kHidden, kHidden, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
+    else
+        pt_layer_kernel<kHidden, 1, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
+}
+
+// gradient of layer l's input from the gradient of its output
+template <class T>
+void layer_adj(stag_ptnet* n, int l, const T* gout, T* gin) {
+    const Geom& g = n->g;
+    const float2* w = n->w + layer_offset(l);
+    const int nb = site_blocks(g);
+    if (l == 2)
+        pt_layer_kernel<1, kHidden, T, T, true><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin);
+    else if (l == 1)
+        pt_layer_kernel<kHidden, kHidden, T, T, true><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin);
+}
+
+template <class T>
+void layer_wgrad(stag_ptnet* n, int l, const T* psi, const T* gout) {
+    const Geom& g = n->g;
+    const int cin = kChan[l], cout = kChan[l + 1];
+    const int nw = kPaths * cout * cin;
+    if (l == 0) {
+        dim3 grid(kWgradBlocks, kPaths, 1);
+        pt_wgrad_kernel<1, kHidden, T><<<grid, 256, 0, S(n)>>>(g, n->links, psi, gout, cout, n->wpart);
+    } else if (l == 1) {
+        dim3 grid(kWgradBlocks, kPaths, kHidden / 4);
+        pt_wgrad_kernel<kHidden, 4, T><<<grid, 256, 0, S(n)>>>(g, n->links, psi, gout, cout, n->wpart);
+    } else {
+        dim3 grid(kWgradBlocks, kPaths, 1);
+        pt_wgrad_kernel<kHidden, 1, T><<<grid, 256, 0, S(n)>>>(g, n->links, psi, gout, cout, n->wpart);
+    }
+    pt_wgrad_sum_kernel<<<blocks_for(nw), kBlock, 0, S(n)>>>(n->wpart, kWgradBlocks, nw, n->grad + layer_offset(l));
+}
+
+double read_partials(stag_ptnet* n, int count) {
+    n->red_host.resize(count);
+    pcheck(n, cudaMemcpyAsync(n->red_host.data(), n->red, count * sizeof(double), cudaMemcpyDeviceToHost, S(n)),
+           "read reduction");
+    pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+    double s = 0.0;
+    for (int k = 0; k < count; ++k) s += n->red_host[k];
+    return s;
+}
+
+// vad = A va with the FP32 Dirac kernels (uses vt)
+void apply_A_f32(stag_ptnet* n) {
+    const Geom& g = n->g;
+    const double m2 = n->h->mass * n->h->mass;
+    launch_dslash_f32(g, 1, n->links, n->lng, n->va, n->vt, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, S(n));
+    launch_dslash_f32(g, 0, n->links, n->lng, n->vt, n->vad, EPI_AXPY, n->va, m2, nullptr, nullptr, S(n));
+}
+
+// |A e|^2 of a slot
+template <class T>
+double slot_energy(stag_ptnet* n, const void* slot) {
+    const Geom& g = n->g;
+    pt_slot_f32_kernel<T><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, static_cast<const T*>(slot), n->va);
+    apply_A_f32(n);
+    pt_dot_f32_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->vad, n->vad, n->red);
+    return read_partials(n, blocks_for(g.vh));
+}
+
+template <class T>
+double slot_norm2(stag_ptnet* n, const void* slot) {
+    pt_norm2_kernel<T><<<blocks_for(n->g.vh), kBlock, 0, S(n)>>>(n->g, static_cast<const T*>(slot), n->red);
+    return read_partials(n, blocks_for(n->g.vh));
+}
+
+// forward through all layers from act[0]
+template <class T>
+void forward(stag_ptnet* n) {
+    for (int l = 0; l < kLayers; ++l) layer_fwd<T>(n, l, static_cast<const T*>(n->act[l]), static_cast<T*>(n->act[l + 1]));
+}
+
+// forward pass and loss |A d|^2 / |A e|^2 of one pair (eae = |A e|^2); with
+// seed, leaves the output gradient A (A d) / |A e|^2 in gact[3]
+template <class T>
+double forward_energy(stag_ptnet* n, const void* r, const void* e, double eae, bool seed = false) {
+    const Geom& g = n->g;
+    pt_embed_kernel<T, T><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, static_cast<const T*>(r), 1.0, static_cast<T*>(n->act[0]));
+    forward<T>(n);
+    pt_diff_kernel<T><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, static_cast<const T*>(n->act[3]), static_cast<const T*>(e), n->va);
+    apply_A_f32(n);
+    pt_dot_f32_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->vad, n->vad, n->red);
+    if (seed) {
+        pcheck(n, cudaMemcpyAsync(n->va, n->vad, (size_t)3 * g.vs * sizeof(float2), cudaMemcpyDeviceToDevice, S(n)), "copy");
+        apply_A_f32(n);
+        pt_seed_kernel<T><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->vad, (float)(1.0 / eae), static_cast<T*>(n->gact[3]));
+    }
+    pcheck(n, cudaGetLastError(), "forward");
+    return read_partials(n, blocks_for(g.vh)) / eae;
+}
+
+// loss and accumulated weight gradients of one pair (slots r, e; <e, A e>); returns the loss
+template <class T>
+double sample_step(stag_ptnet* n, const void* r, const void* e, double eae) {
+    const double loss = forward_energy<T>(n, r, e, eae, true);
+    for (int l = kLayers - 1; l >= 0; --l) {
+        layer_wgrad<T>(n, l, static_cast<const T*>(n->act[l]), static_cast<const T*>(n->gact[l + 1]));
+        if (l > 0) layer_adj<T>(n, l, static_cast<const T*>(n->gact[l + 1]), static_cast<T*>(n->gact[l]));
+    }
+    pcheck(n, cudaGetLastError(), "training step");
+    return loss;
+}
+
+// z = M(r) for FP64 vectors (scaled by 1/|r| on the way in, back on the way out)
+template <class T>
+void apply_net(stag_ptnet* n, const double2* r, double rnorm, double2* z) {
+    const Geom& g = n->g;
+    const double s = rnorm > 0.0 ? 1.0 / rnorm : 1.0;
+    pt_embed_kernel<double2, T><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, r, s, static_cast<T*>(n->act[0]));
+    forward<T>(n);
+    pt_extract_kernel<T><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, static_cast<const T*>(n->act[3]), rnorm > 0.0 ? rnorm : 1.0, z);
+}
+
+void upload_weights(stag_ptnet* n) {
+    pcheck(n, cudaMemcpyAsync(n->w, n->w_host.data(), n->w_host.size() * sizeof(float2), cudaMemcpyHostToDevice, S(n)),
+           "upload weights");
+}
+
+void download_weights(stag_ptnet* n) {
+    pcheck(n, cudaMemcpyAsync(n->w_host.data(), n->w, n->w_host.size() * sizeof(float2), cudaMemcpyDeviceToHost, S(n)),
+           "download weights");
+    pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+}
+
+void destroy_net(stag_ptnet* n) {
+    if (!n) return;
+    if (n->h && n->h->s) cudaStreamSynchronize(n->h->s);
+    for (void* p : {(void*)n->links, (void*)n->lng, (void*)n->va, (void*)n->vt, (void*)n->vad, (void*)n->w, (void*)n->grad, (void*)n->adam_m, (void*)n->adam_v,
+                    (void*)n->wpart, (void*)n->red, n->scratch_r, n->scratch_e, (void*)n->fr, (void*)n->fz,
+                    (void*)n->fp, (void*)n->fq, (void*)n->fro})
+        if (p) cudaFree(p);
+    for (int l = 0; l <= kLayers; ++l) {
+        if (n->act[l]) cudaFree(n->act[l]);
+        if (n->gact[l]) cudaFree(n->gact[l]);
+    }
+    for (void* p : n->pairs_r) cudaFree(p);
+    for (void* p : n->pairs_e) cudaFree(p);
+    delete n;
+}
+
+bool is_bf16(const stag_ptnet* n) { return n->prec == STAG_ARITH_BF16; }
+
+// FP64-class A p into q (FP64): float-float when the handle has it, else native FP64
+void apply_A_q(stag_ptnet* n, const double2* p, double2* q) {
+    stag_handle* h = n->h;
+    const Geom& g = h->g;
+    if (h->fatff) {
+        float4* u = static_cast<float4*>(h->u);
+        float4* t = static_cast<float4*>(h->t);
+        float4* o = reinterpret_cast<float4*>(h->ad);
+        const LinkSet L{h->fat64, h->lng64, h->fatff, h->lngff};
+        launch_to_ff(g, p, u, h->s);
+        launch_dslash_ff(g, 1, L, u, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
+        launch_dslash_ff(g, 0, L, t, o, EPI_AXPY, u, h->mass * h->mass, nullptr, nullptr, h->s);
+        launch_from_ff(g, o, q, h->s);
+        h->launches += 4;
+    } else {
+        handle_apply_A_f64(h, p, q);
+    }
+}
+
+// (Re<a,b>, Re<a,c>, |b|^2)
+void dots(stag_ptnet* n, const double2* a, const double2* b, const double2* c, double out[3]) {
+    const Geom& g = n->g;
+    const int nb = blocks_for(g.vh);
+    fcg_dots_kernel<<<nb, kBlock, 0, S(n)>>>(g, a, b, c, n->red, nb);
+    pcheck(n, cudaGetLastError(), "dots");
+    n->red_host.resize(3 * nb);
+    pcheck(n, cudaMemcpyAsync(n->red_host.data(), n->red, 3 * nb * sizeof(double), cudaMemcpyDeviceToHost, S(n)),
+           "read dots");
+    pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int b2 = 0; b2 < nb; ++b2) s += n->red_host[k * nb + b2];
+        out[k] = s;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint64_t seed) {
+    if (out) *out = nullptr;
+    if (!out || !h) return STAG_ERR_INVALID_ARG;
+    stag_ptnet* n = nullptr;
+    try {
+        if (precision != STAG_ARITH_BF16 && precision != STAG_ARITH_F32) {
+            h->err = "ptnet precision must be STAG_ARITH_BF16 or STAG_ARITH_F32";
+            return STAG_ERR_INVALID_ARG;
+        }
+        n = new stag_ptnet();
+        n->h = h;
+        n->g = h->g;
+        n->prec = precision;
+        n->elem = precision == STAG_ARITH_BF16 ? sizeof(__nv_bfloat162) : sizeof(float2);
+        handle_begin(h);
+        const size_t nl = (size_t)2 * 4 * 9 * n->g.vs;
+        n->links = static_cast<float2*>(palloc(n, nl * sizeof(float2), "allocate links"));
+        pt_links_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->fat64, n->links, nl);
+        if (h->lng64) {
+            n->lng = static_cast<float2*>(palloc(n, nl * sizeof(float2), "allocate links"));
+            pt_links_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->lng64, n->lng, nl);
+        }
+        const size_t fv = (size_t)3 * n->g.vs * sizeof(float2);
+        n->va = static_cast<float2*>(palloc(n, fv, "allocate vectors"));
+        n->vt = static_cast<float2*>(palloc(n, fv, "allocate vectors"));
+        n->vad = static_cast<float2*>(palloc(n, fv, "allocate vectors"));
+        const int nw = n_weights();
+        n->w = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate weights"));
+        n->grad = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate gradients"));
+        n->adam_m = static_cast<float*>(palloc(n, 2 * nw * sizeof(float), "allocate optimiser"));
+        n->adam_v = static_cast<float*>(palloc(n, 2 * nw * sizeof(float), "allocate optimiser"));
+        n->wpart = static_cast<float2*>(palloc(n, (size_t)kWgradBlocks * nw * sizeof(float2), "allocate partials"));
+        n->red = static_cast<double*>(palloc(n, 3 * (size_t)blocks_for(2 * n->g.vs) * sizeof(double), "allocate partials"));
+        for (int l = 0; l <= kLayers; ++l) {
+            n->act[l] = palloc(n, field_bytes(n, kChan[l]), "allocate activations");
+            n->gact[l] = palloc(n, field_bytes(n, kChan[l]), "allocate activations");
+        }
+        n->scratch_r = palloc(n, slot_bytes(n), "allocate slots");
+        n->scratch_e = palloc(n, slot_bytes(n), "allocate slots");
+        const size_t vb = (size_t)3 * n->g.vs * sizeof(double2);
+        n->fr = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
+        n->fz = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
+        n->fp = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
+        n->fq = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
+        n->fro = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
+        // initial weights: M = s * identity through channel 0, plus small seeded noise
+        n->w_host.assign(nw, make_float2(0.f, 0.f));
+        std::mt19937_64 rng(seed);
+        std::normal_distribution<float> nd(0.f, 1.f);
+        for (int l = 0; l < kLayers; ++l) {
+            const int cin = kChan[l], cout = kChan[l + 1];
+            const float sc = 0.02f / std::sqrt((float)(kPaths * cin));
+            for (int k = 0; k < kPaths * cin * cout; ++k)
+                n->w_host[layer_offset(l) + k] = make_float2(sc * nd(rng), sc * nd(rng));
+            n->w_host[layer_offset(l) + 0].x += (l == kLayers - 1) ? 0.1f : 1.0f;  // identity path, channel 0 -> 0
+        }
+        upload_weights(n);
+        pcheck(n, cudaGetLastError(), "ptnet create");
+        handle_end(h);
+        *out = n;
+        return STAG_OK;
+    } catch (const PFail& f) {
+        destroy_net(n);
+        return f.code;
+    } catch (const HandleError& f) {
+        destroy_net(n);
+        return f.code;
+    } catch (...) {
+        destroy_net(n);
+        return STAG_ERR_CUDA;
+    }
+}
+
+int64_t stag_ptnet_num_weights(const stag_ptnet* n) { return n ? n_weights() : 0; }
+
+int stag_ptnet_set_weights(stag_ptnet* n, const double* w, int64_t count) {
+    if (!n || !w || count != n_weights()) return STAG_ERR_INVALID_ARG;
+    try {
+        for (int k = 0; k < n_weights(); ++k) n->w_host[k] = make_float2((float)w[2 * k], (float)w[2 * k + 1]);
+        upload_weights(n);
+        pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+        return STAG_OK;
+    } catch (const PFail& f) {
+        return f.code;
+    }
+}
+
+int stag_ptnet_get_weights(stag_ptnet* n, double* w, int64_t count) {
+    if (!n || !w || count != n_weights()) return STAG_ERR_INVALID_ARG;
+    try {
+        download_weights(n);
+        for (int k = 0; k < n_weights(); ++k) {
+            w[2 * k] = n->w_host[k].x;
+            w[2 * k + 1] = n->w_host[k].y;
+        }
+        return STAG_OK;
+    } catch (const PFail& f) {
+        return f.code;
+    }
+}
+
+int stag_ptnet_apply(stag_ptnet* n, const double* r_even, double* z_even) {
+    if (!n || !r_even || !z_even) return STAG_ERR_INVALID_ARG;
+    stag_handle* h = n->h;
+    try {
+        handle_begin(h);
+        const Geom& g = n->g;
+        const bool out_dev = handle_is_device_ptr(h, z_even);
+        const double* src = r_even;
+        if (!handle_is_device_ptr(h, r_even)) {
+            pcheck(n, cudaMemcpyAsync(h->io_a, r_even, (size_t)3 * g.vh * sizeof(double2), cudaMemcpyHostToDevice, S(n)), "copy r");
+            src = h->io_a;
+        }
+        launch_pack_vec(g, src, n->fr, S(n));
+        double d3[3];
+        dots(n, n->fr, n->fr, nullptr, d3);
+        const double rn = std::sqrt(d3[0]);
+        if (is_bf16(n))
+            apply_net<__nv_bfloat162>(n, n->fr, rn, n->fz);
+        else
+            apply_net<float2>(n, n->fr, rn, n->fz);
+        launch_unpack_vec(g, n->fz, out_dev ? z_even : h->io_b, S(n));
+        if (!out_dev)
+            pcheck(n, cudaMemcpyAsync(z_even, h->io_b, (size_t)3 * g.vh * sizeof(double2), cudaMemcpyDeviceToHost, S(n)), "copy z");
+        pcheck(n, cudaGetLastError(), "ptnet apply");
+        handle_end(h);
+        return STAG_OK;
+    } catch (const PFail& f) {
+        return f.code;
+    } catch (const HandleError& f) {
+        return f.code;
+    }
+}
+
+int stag_ptnet_loss_grad(stag_ptnet* n, const double* r_even, const double* e_even, double* loss, double* grad) {
+    if (!n || !r_even || !e_even) return STAG_ERR_INVALID_ARG;
+    stag_handle* h = n->h;
+    try {
+        handle_begin(h);
+        const Geom& g = n->g;
+        for (int k = 0; k < 2; ++k) {
+            const double* v = k == 0 ? r_even : e_even;
+            if (!handle_is_device_ptr(h, v)) {
+                pcheck(n, cudaMemcpyAsync(h->io_a, v, (size_t)3 * g.vh * sizeof(double2), cudaMemcpyHostToDevice, S(n)), "copy");
+                v = h->io_a;
+            }
+            launch_pack_vec(g, v, n->fr, S(n));
+            void* slot = k == 0 ? n->scratch_r : n->scratch_e;
+            if (is_bf16(n))
+                pt_store_slot_kernel<double2, __nv_bfloat162><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->fr, 1.0, static_cast<__nv_bfloat162*>(slot));
+            else
+                pt_store_slot_kernel<double2, float2><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->fr, 1.0, static_cast<float2*>(slot));
+        }
+        pcheck(n, cudaMemsetAsync(n->grad, 0, n_weights() * sizeof(float2), S(n)), "zero gradients");
+        double L;
+        if (is_bf16(n)) {
+            const double eae = slot_energy<__nv_bfloat162>(n, n->scratch_e);
+            L = sample_step<__nv_bfloat162>(n, n->scratch_r, n->scratch_e, eae);
+        } else {
+            const double eae = slot_energy<float2>(n, n->scratch_e);
+            L = sample_step<float2>(n, n->scratch_r, n->scratch_e, eae);
+        }
+        if (loss) *loss = L;
+        if (grad) {
+            std::vector<float2> gh(n_weights());
+            pcheck(n, cudaMemcpyAsync(gh.data(), n->grad, gh.size() * sizeof(float2), cudaMemcpyDeviceToHost, S(n)), "read gradients");
+            pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+            for (int k = 0; k < n_weights(); ++k) {
+                grad[2 * k] = gh[k].x;
+                grad[2 * k + 1] = gh[k].y;
+            }
+        }
+        handle_end(h);
+        return STAG_OK;
+    } catch (const PFail& f) {
+        return f.code;
+    } catch (const HandleError& f) {
+        return f.code;
+    }
+}
+
+int stag_ptnet_add_pairs(stag_ptnet* n, int32_t n_sources, const double* const* sources, int32_t stride,
+                         double min_rel_residual, int32_t max_pairs, int32_t* n_pairs) {
+    if (!n || !sources || n_sources < 1 || stride < 1 || max_pairs < 0) return STAG_ERR_INVALID_ARG;
+    stag_handle* h = n->h;
+    if (h->opt.inner != STAG_INNER_NONE) {
+        h->err = "training pairs come from the plain CG solver (inner = NONE)";
+        return STAG_ERR_INVALID_ARG;
+    }
+    const stag_options saved = h->opt;
+    int code = STAG_OK;
+    std::vector<double2*> xsnap;
+    try {
+        handle_begin(h);
+        const Geom& g = n->g;
+        const size_t vb = (size_t)3 * g.vs * sizeof(double2);
+        // blocks of `stride` iterations: one snapshot per block
+        if (h->graph) {
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        h->opt.check_interval = stride;
+        for (int sidx = 0; sidx < n_sources && (int)n->pairs_r.size() < max_pairs; ++sidx) {
+            const double* src = sources[sidx];
+            if (!handle_is_device_ptr(h, src)) {
+                pcheck(n, cudaMemcpyAsync(h->io_a, src, (size_t)3 * g.vh * sizeof(double2), cudaMemcpyHostToDevice, S(n)), "copy source");
+                src = h->io_a;
+            }
+            launch_pack_vec(g, src, h->b, S(n));
+            pcheck(n, cudaMemsetAsync(h->x, 0, vb, S(n)), "zero x");
+            launch_norm2_diff(g, h->b, nullptr, h->scal, h->partials, S(n));
+            pcheck(n, cudaMemcpyAsync(h->scal_host, h->scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, S(n)), "read");
+            pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+            const double bnorm2 = h->scal_host->red_out;
+            if (!(bnorm2 > 0.0)) continue;
+            std::vector<std::pair<void*, double>> rs;  // (r slot, 1/|r|) of this solve
+            const bool ff = h->fatff != nullptr && h->opt.arith == STAG_ARITH_FF;
+            h->block_hook = [&]() {
+                const double rel2 = h->scal_host->delta_new / bnorm2;
+                if (h->scal_host->done || rel2 < min_rel_residual * min_rel_residual) return;
+                if ((int)(n->pairs_r.size() + rs.size()) >= max_pairs) return;
+                const double inv = 1.0 / std::sqrt(h->scal_host->delta_new);
+                void* slot = palloc(n, slot_bytes(n), "allocate pair");
+                if (is_bf16(n)) {
+                    if (ff)
+                        pt_store_slot_kernel<float4, __nv_bfloat162><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, reinterpret_cast<const float4*>(h->r), inv, static_cast<__nv_bfloat162*>(slot));
+                    else
+                        pt_store_slot_kernel<double2, __nv_bfloat162><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, h->r, inv, static_cast<__nv_bfloat162*>(slot));
+                } else {
+                    if (ff)
+                        pt_store_slot_kernel<float4, float2><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, reinterpret_cast<const float4*>(h->r), inv, static_cast<float2*>(slot));
+                    else
+                        pt_store_slot_kernel<double2, float2><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, h->r, inv, static_cast<float2*>(slot));
+                }
+                double2* xs = static_cast<double2*>(palloc(n, vb, "allocate snapshot"));
+                pcheck(n, cudaMemcpyAsync(xs, h->x, vb, cudaMemcpyDeviceToDevice, S(n)), "snapshot x");
+                xsnap.push_back(xs);
+                rs.push_back({slot, inv});
+            };
+            stag_solve_info info{};
+            const int st = handle_solve_packed(h, bnorm2, 1e-10, 0, info);
+            h->block_hook = nullptr;
+            if (st != STAG_OK) pfail(n, st, "training-pair solve did not converge");
+            // e_k = (x* - x_k) / |r_k|
+            for (size_t k = 0; k < rs.size(); ++k) {
+                void* slot = palloc(n, slot_bytes(n), "allocate pair");
+                if (is_bf16(n))
+                    pt_store_diff_kernel<__nv_bfloat162><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, h->x, xsnap[k], rs[k].second, static_cast<__nv_bfloat162*>(slot));
+                else
+                    pt_store_diff_kernel<float2><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, h->x, xsnap[k], rs[k].second, static_cast<float2*>(slot));
+                n->pairs_r.push_back(rs[k].first);
+                n->pairs_e.push_back(slot);
+                n->pairs_eae.push_back(is_bf16(n) ? slot_energy<__nv_bfloat162>(n, slot) : slot_energy<float2>(n, slot));
+            }
+            for (double2* p : xsnap) cudaFree(p);
+            for (double2* p : xsnap) n->device_bytes -= (long long)vb;
+            xsnap.clear();
+        }
+        pcheck(n, cudaGetLastError(), "training pairs");
+        handle_end(h);
+    } catch (const PFail& f) {
+        code = f.code;
+    } catch (const HandleError& f) {
+        code = f.code;
+    }
+    h->block_hook = nullptr;
+    for (double2* p : xsnap) cudaFree(p);
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->opt = saved;
+    if (n_pairs) *n_pairs = (int32_t)n->pairs_r.size();
+    return code;
+}
+
+int stag_ptnet_train(stag_ptnet* n, int32_t epochs, int32_t batch, double lr, uint64_t seed, double* epoch_loss) {
+    if (!n || epochs < 0 || batch < 1 || !(lr > 0.0)) return STAG_ERR_INVALID_ARG;
+    if (n->pairs_r.empty()) {
+        n->err = "no training pairs";
+        return STAG_ERR_INVALID_ARG;
+    }
+    try {
+        handle_begin(n->h);
+        const int np = (int)n->pairs_r.size();
+        const int nw = n_weights();
+        std::vector<int> order(np);
+        std::iota(order.begin(), order.end(), 0);
+        std::mt19937_64 rng(seed);
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        for (int ep = 0; ep < epochs; ++ep) {
+            std::shuffle(order.begin(), order.end(), rng);
+            double total = 0.0;
+            for (int s0 = 0; s0 < np; s0 += batch) {
+                const int s1 = std::min(np, s0 + batch);
+                pcheck(n, cudaMemsetAsync(n->grad, 0, nw * sizeof(float2), S(n)), "zero gradients");
+                for (int s = s0; s < s1; ++s) {
+                    const int k = order[s];
+                    total += is_bf16(n) ? sample_step<__nv_bfloat162>(n, n->pairs_r[k], n->pairs_e[k], n->pairs_eae[k])
+                                        : sample_step<float2>(n, n->pairs_r[k], n->pairs_e[k], n->pairs_eae[k]);
+                }
+                n->adam_t += 1;
+                const float c1 = 1.f - std::pow(b1, (float)n->adam_t), c2 = 1.f - std::pow(b2, (float)n->adam_t);
+                pt_adam_kernel<<<blocks_for(2 * nw), kBlock, 0, S(n)>>>(reinterpret_cast<float*>(n->w),
+                                                                        reinterpret_cast<const float*>(n->grad),
+                                                                        n->adam_m, n->adam_v, 2 * nw,
+                                                                        2.f / (float)(s1 - s0), (float)lr, b1, b2,
+                                                                        c1, c2, eps);
+            }
+            if (epoch_loss) epoch_loss[ep] = total / np;
+        }
+        pcheck(n, cudaGetLastError(), "training");
+        download_weights(n);
+        handle_end(n->h);
+        return STAG_OK;
+    } catch (const PFail& f) {
+        return f.code;
+    } catch (const HandleError& f) {
+        return f.code;
+    }
+}
+
+int stag_ptnet_dataset_loss(stag_ptnet* n, double* loss) {
+    if (!n || !loss) return STAG_ERR_INVALID_ARG;
+    if (n->pairs_r.empty()) return STAG_ERR_INVALID_ARG;
+    try {
+        handle_begin(n->h);
+        double total = 0.0;
+        for (size_t k = 0; k < n->pairs_r.size(); ++k)
+            total += is_bf16(n) ? forward_energy<__nv_bfloat162>(n, n->pairs_r[k], n->pairs_e[k], n->pairs_eae[k])
+                                : forward_energy<float2>(n, n->pairs_r[k], n->pairs_e[k], n->pairs_eae[k]);
+        *loss = total / n->pairs_r.size();
+        handle_end(n->h);
+        return STAG_OK;
+    } catch (const PFail& f) {
+        return f.code;
+    } catch (const HandleError& f) {
+        return f.code;
+    }
+}
+
+int stag_ptnet_num_pairs(const stag_ptnet* n) { return n ? (int)n->pairs_r.size() : 0; }
+
+const char* stag_ptnet_last_error(const stag_ptnet* n) { return n ? n->err.c_str() : "NULL network"; }
+
+int stag_ptnet_destroy(stag_ptnet* n) {
+    destroy_net(n);
+    return STAG_OK;
+}
+
+int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* x_even, double tol, int32_t max_iter,
+                   stag_solve_info* info) {
+    if (!h || !n || n->h != h || !b_even || !x_even || b_even == x_even) return STAG_ERR_INVALID_ARG;
+    if (!(tol > 0.0) || !std::isfinite(tol)) return STAG_ERR_INVALID_ARG;
+    stag_solve_info inf{};
+    int status = STAG_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    try {
+        handle_begin(h);
+        const Geom& g = h->g;
+        const size_t ab = (size_t)3 * g.vh * sizeof(double2);
+        const bool x_dev = handle_is_device_ptr(h, x_even);
+        const double* bs = b_even;
+        if (!handle_is_device_ptr(h, bs)) {
+            pcheck(n, cudaMemcpyAsync(h->io_a, bs, ab, cudaMemcpyHostToDevice, S(n)), "copy b");
+            bs = h->io_a;
+        }
+        launch_pack_vec(g, bs, h->b, S(n));
+        const double* xs = x_even;
+        if (!x_dev) {
+            pcheck(n, cudaMemcpyAsync(h->io_b, xs, ab, cudaMemcpyHostToDevice, S(n)), "copy x");
+            xs = h->io_b;
+        }
+        launch_pack_vec(g, xs, h->x, S(n));
+        double d3[3];
+        dots(n, h->b, h->b, nullptr, d3);
+        const double bnorm2 = d3[0];
+        if (!std::isfinite(bnorm2)) pfail(n, STAG_ERR_INVALID_ARG, "source has non-finite entries");
+        const long long max_it = max_iter > 0 ? max_iter : 3LL * g.vh;
+        long long iters = 0;
+        int fallbacks = 0;
+        double rel = 0.0;
+        auto precond = [&](const double2* r, double rnorm, double2* z) {
+            if (is_bf16(n))
+                apply_net<__nv_bfloat162>(n, r, rnorm, z);
+            else
+                apply_net<float2>(n, r, rnorm, z);
+        };
+        auto true_residual = [&]() {
+            handle_apply_A_f64(h, h->x, n->fq);
+            fcg_sub_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->fr, h->b, n->fq);
+            dots(n, n->fr, n->fr, nullptr, d3);
+            return std::sqrt(d3[0] / bnorm2);
+        };
+        if (bnorm2 == 0.0) {
+            pcheck(n, cudaMemsetAsync(h->x, 0, (size_t)3 * g.vs * sizeof(double2), S(n)), "zero x");
+        } else {
+            bool use_plain = false;
+            while (true) {
+                // r = b - A x (FP64), z = M r, p = z
+                rel = true_residual();
+                if (rel <= tol) break;
+                if (iters >= max_it) {
+                    status = STAG_ERR_NOT_CONVERGED;
+                    break;
+                }
+                if (use_plain) {
+                    // plain FP64-class CG from the current x, judged by its own FP64 residual
+                    stag_solve_info pi{};
+                    status = handle_solve_packed(h, bnorm2, tol, max_it - iters, pi);
+                    iters += pi.iters;
+                    rel = pi.true_rel_residual;
+                    break;
+                }
+                double rr = d3[0];
+                precond(n->fr, std::sqrt(rr), n->fz);
+                pcheck(n, cudaMemcpyAsync(n->fp, n->fz, (size_t)3 * g.vs * sizeof(double2), cudaMemcpyDeviceToDevice, S(n)), "p = z");
+                dots(n, n->fr, n->fz, nullptr, d3);
+                double rz = d3[0];
+                std::vector<double> hist;
+                bool stalled = !(rz > 0.0);
+                while (!stalled && iters < max_it && rr > tol * tol * bnorm2) {
+                    apply_A_q(n, n->fp, n->fq);
+                    dots(n, n->fp, n->fq, nullptr, d3);
+                    const double pq = d3[0];
+                    if (!(pq > 0.0)) {
+                        stalled = true;
+                        break;
+                    }
+                    const double alpha = rz / pq;
+                    fcg_update_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, h->x, n->fr, n->fro, n->fp, n->fq, alpha);
+                    dots(n, n->fr, n->fr, nullptr, d3);
+                    rr = d3[0];
+                    ++iters;
+                    hist.push_back(rr);
+                    // stall: less than a 10 % drop of |r| over the last 60 iterations
+                    if (hist.size() > 60 && std::sqrt(rr) > 0.9 * std::sqrt(hist[hist.size() - 61])) {
+                        stalled = true;
+                        break;
+                    }
+                    precond(n->fr, std::sqrt(rr), n->fz);
+                    dots(n, n->fz, n->fr, n->fro, d3);  // (z, r_new), (z, r_old)
+                    const double beta = (d3[0] - d3[1]) / rz;
+                    rz = d3[0];
+                    if (!(rz > 0.0)) {
+                        stalled = true;
+                        break;
+                    }
+                    fcg_dir_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->fp, n->fz, beta);
+                }
+                if (stalled) {
+                    use_plain = true;
+                    ++fallbacks;
+                }
+            }
+            inf.iter_rel_residual = rel;
+        }
+        inf.iters = (int32_t)iters;
+        inf.restarts = fallbacks;
+        inf.true_rel_residual = rel;
+        if (status == STAG_ERR_NOT_CONVERGED) h->err = "flexible CG: not converged";
+        launch_unpack_vec(g, h->x, x_dev ? x_even : h->io_b, S(n));
+        if (!x_dev) pcheck(n, cudaMemcpyAsync(x_even, h->io_b, ab, cudaMemcpyDeviceToHost, S(n)), "copy x");
+        pcheck(n, cudaGetLastError(), "flexible CG");
+        handle_end(h);
+    } catch (const PFail& f) {
+        status = f.code;
+        h->err = n->err;
+    } catch (const HandleError& f) {
+        status = f.code;
+    }
+    inf.status = status;
+    inf.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return status;
+}
+
+}  // extern "C"

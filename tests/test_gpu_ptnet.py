@@ -1,0 +1,198 @@
+"""Learned preconditioner on the GPU against the oracle (oracle/ptnet.py).
+
+Tolerances: FP32 activations - forward 2e-6 (three layers of FP32 sums),
+loss 1e-5 and gradients vs FP64 central differences of the
+oracle's loss 1e-3 relative to the largest checked component; BF16
+activations - forward 2e-2 (2^-8 storage rounding per layer).
+Flexible CG meets the solver bars: true residual <= 1e-10, x within 1e-8 of the
+oracle solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import ptnet
+from paper_1010_4782_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+CHANS = (1, 8, 8, 1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1010_4782_gb300 import build
+
+    build.build()
+    binding.load()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _split(wflat):
+    out, off = [], 0
+    for ci, co in zip(CHANS[:-1], CHANS[1:]):
+        n = 9 * co * ci
+        out.append(wflat[off:off + n].reshape(9, co, ci))
+        off += n
+    return out
+
+
+def _random_flat(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    n = sum(9 * co * ci for ci, co in zip(CHANS[:-1], CHANS[1:]))
+    return scale * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+
+
+def _handle(fat, lng, dims, mass, arith=binding.STAG_ARITH_FF):
+    opt = binding.stag_default_options()
+    opt.arith = arith
+    return binding.Handle(_dev(fat), dims, mass, naik_long=None if lng is None else _dev(lng), options=opt)
+
+
+@pytest.mark.parametrize("prec,tol", [(binding.STAG_ARITH_F32, 2e-6), (binding.STAG_ARITH_BF16, 2e-2)])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8)])
+def test_forward_parity(dims, prec, tol):
+    fat = inputs.gauge_field(dims, 81)
+    w = _random_flat(82)
+    r = inputs.gaussian_even_source(dims, 83)
+    ref = ptnet.PTNet(fat, dims, _split(w)).apply(r)
+    with _handle(fat, None, dims, 0.1) as h:
+        net = binding.stag_ptnet_create(h.h, prec, 1)
+        try:
+            binding.stag_ptnet_set_weights(net, w)
+            z = torch.empty_like(_dev(r))
+            binding.stag_ptnet_apply(net, _dev(r), z)
+        finally:
+            binding.stag_ptnet_destroy(net)
+    got = z.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+
+
+def test_network_weights_reproducing_A():
+    """Layer 1: (r, D r); layer 2: m^2 r - D(D r); layer 3: identity => the network is A."""
+    dims, m = (4, 6, 4, 8), 0.3
+    fat, lng = inputs.asqtad_form_fields(dims, seeds=(84, 85, 86))
+    w1 = np.zeros((9, 8, 1), complex)
+    w2 = np.zeros((9, 8, 8), complex)
+    w3 = np.zeros((9, 1, 8), complex)
+    w1[0, 0, 0] = 1
+    w2[0, 0, 0] = m ** 2
+    w3[0, 0, 0] = 1
+    for mu in range(4):
+        w1[1 + 2 * mu, 1, 0], w1[2 + 2 * mu, 1, 0] = 1, -1
+        w2[1 + 2 * mu, 0, 1], w2[2 + 2 * mu, 0, 1] = -1, 1
+    w = np.concatenate([w1.ravel(), w2.ravel(), w3.ravel()])
+    v = inputs.gaussian_even_source(dims, 87)
+    with _handle(fat, None, dims, m) as h:   # one-hop operator
+        net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_F32, 1)
+        try:
+            binding.stag_ptnet_set_weights(net, w)
+            z = torch.empty_like(_dev(v))
+            binding.stag_ptnet_apply(net, _dev(v), z)
+            a = torch.empty_like(z)
+            binding.stag_apply_A(h.h, _dev(v), a)
+        finally:
+            binding.stag_ptnet_destroy(net)
+    assert torch.linalg.vector_norm(z - a) <= 2e-6 * torch.linalg.vector_norm(a)
+
+
+def test_gradient_matches_oracle_finite_differences():
+    dims = (4, 4, 4, 4)
+    fat = inputs.gauge_field(dims, 91)
+    w = _random_flat(92, 0.2)
+    r = inputs.gaussian_even_source(dims, 93)
+    e = inputs.gaussian_even_source(dims, 94)
+    with _handle(fat, None, dims, 0.1) as h:
+        net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_F32, 1)
+        try:
+            binding.stag_ptnet_set_weights(net, w)
+            loss, grad = binding.stag_ptnet_loss_grad(net, _dev(r), _dev(e))
+        finally:
+            binding.stag_ptnet_destroy(net)
+    onet = ptnet.PTNet(fat, dims, _split(w))
+    A = oracle.Operator(fat, None, 0.1, dims).apply_A
+    assert loss == pytest.approx(onet.loss(r, e, A), rel=1e-5)
+    rng = np.random.default_rng(95)
+    idx = np.concatenate([rng.choice(72, 6, replace=False), 72 + rng.choice(576, 10, replace=False),
+                          648 + rng.choice(72, 6, replace=False)])
+    fd, gpu = [], []
+    for k in idx:
+        for part in (1.0, 1j):
+            hstep = 1e-6
+            wp, wm = w.copy(), w.copy()
+            wp[k] += hstep * part
+            wm[k] -= hstep * part
+            lp = ptnet.PTNet(fat, dims, _split(wp)).loss(r, e, A)
+            lm = ptnet.PTNet(fat, dims, _split(wm)).loss(r, e, A)
+            fd.append((lp - lm) / (2 * hstep))
+            gpu.append(2 * (grad[k].real if part == 1.0 else grad[k].imag))
+    fd, gpu = np.array(fd), np.array(gpu)
+    assert np.abs(fd - gpu).max() <= 1e-3 * np.abs(fd).max()
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """8^4 asqtad-form field, m = 0.05: pairs from plain-CG solves, BF16 network trained on them."""
+    dims, m = (8, 8, 8, 8), 0.05
+    fat, lng = inputs.asqtad_form_fields(dims, seeds=(101, 102, 103))
+    h = _handle(fat, lng, dims, m)
+    net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 7)
+    sources = [_dev(inputs.gaussian_even_source(dims, 200 + k)) for k in range(4)]
+    npairs = binding.stag_ptnet_add_pairs(net, sources, stride=4, min_rel_residual=1e-6, max_pairs=400)
+    before = binding.stag_ptnet_dataset_loss(net)
+    losses = binding.stag_ptnet_train(net, epochs=8, batch=8, lr=3e-3, seed=1)
+    after = binding.stag_ptnet_dataset_loss(net)
+    yield dict(dims=dims, m=m, fat=fat, lng=lng, h=h, net=net, npairs=npairs, before=before, after=after,
+               losses=losses)
+    binding.stag_ptnet_destroy(net)
+    h.close()
+
+
+def test_training_reduces_loss(trained):
+    assert trained["npairs"] >= 100
+    assert trained["after"] < 0.8 * trained["before"], (trained["before"], trained["after"], trained["losses"])
+    assert np.all(np.isfinite(trained["losses"]))
+
+
+def test_fcg_with_trained_network_gains_over_plain_cg(trained):
+    dims, m, h, net = trained["dims"], trained["m"], trained["h"], trained["net"]
+    op = oracle.Operator(trained["fat"], trained["lng"], m, dims)
+    it_fcg, it_cg = [], []
+    for k in range(3):
+        b = inputs.gaussian_even_source(dims, 500 + k)   # fresh sources
+        x = torch.zeros_like(_dev(b))
+        code, info = binding.stag_fcg_solve(h.h, net, _dev(b), x, 1e-10, max_iter=20000)
+        assert code == binding.STAG_OK, info
+        assert info["true_rel_residual"] <= 1e-10
+        xs = x.cpu().numpy().reshape(-1)
+        ref = oracle.solve(op.apply_A, b, tol=1e-13, max_iter=200000, max_restarts=20)["x"]
+        assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-8
+        it_fcg.append((info["iters"], info["restarts"]))
+        x2 = torch.zeros_like(x)
+        code, info2 = binding.stag_cg_solve(h.h, _dev(b), x2, 1e-10)
+        it_cg.append(info2["iters"])
+    assert all(rs == 0 for _, rs in it_fcg), it_fcg  # no fallback to plain CG
+    # at least 10 % fewer iterations than CG without the network
+    assert sum(i for i, _ in it_fcg) < 0.9 * sum(it_cg), (it_fcg, it_cg)
+
+
+def test_fcg_falls_back_to_plain_cg(trained):
+    """A network with zero weights gives z = 0: flexible CG hands over to plain CG, which converges."""
+    dims, m = (4, 4, 4, 4), 0.1
+    fat = inputs.gauge_field(dims, 1)
+    with _handle(fat, None, dims, m) as h:
+        net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 1)
+        try:
+            binding.stag_ptnet_set_weights(net, np.zeros(720, complex))
+            b = _dev(inputs.gaussian_even_source(dims, 0))
+            x = torch.zeros_like(b)
+            code, info = binding.stag_fcg_solve(h.h, net, b, x, 1e-10)
+        finally:
+            binding.stag_ptnet_destroy(net)
+    assert code == binding.STAG_OK and info["restarts"] >= 1 and info["true_rel_residual"] <= 1e-10

@@ -78,9 +78,9 @@ def test_network_gauge_covariant_and_linear():
     assert np.linalg.norm(lin) <= 1e-13 * np.linalg.norm(net.apply(r1))
 
 
-def test_energy_loss_vanishes_at_the_exact_inverse_and_is_positive():
-    """The energy-norm loss is >= 0, and 0 when M r = e = A^-1 r (weights reproducing A^-1
-    are not available, so the exact pair is compared against a perturbed one)."""
+def test_loss_definition():
+    """The loss is >= 0, zero for a pair whose target is the network's own output, and
+    |A (M r - e)|^2 / |A e|^2."""
     dims = (2, 2, 2, 4)
     fat = inputs.gauge_field(dims, 12)
     op = oracle.Operator(fat, None, 0.5, dims)
@@ -90,9 +90,9 @@ def test_energy_loss_vanishes_at_the_exact_inverse_and_is_positive():
     assert net.loss(r, e, op.apply_A) > 0.0
     # a pair whose target is exactly the network's output has zero loss
     assert net.loss(r, net.apply(r), op.apply_A) == pytest.approx(0.0, abs=1e-28)
-    # and the loss is the energy norm of the difference over that of e
-    d = net.apply(r) - e
-    ref = np.vdot(d, op.apply_A(d)).real / np.vdot(e, op.apply_A(e)).real
+    ad = op.apply_A(net.apply(r) - e)
+    ae = op.apply_A(e)
+    ref = np.vdot(ad, ad).real / np.vdot(ae, ae).real
     assert net.loss(r, e, op.apply_A) == pytest.approx(ref, rel=1e-14)
 
 

@@ -54,6 +54,9 @@ def parse_args():
     p.add_argument("--pairs", type=int, default=2000)
     p.add_argument("--test-sources", type=int, default=64)
     p.add_argument("--epochs", type=int, default=4)
+    p.add_argument("--stride", type=int, default=2)
+    p.add_argument("--min-rel", type=float, default=0.05)
+    p.add_argument("--lr", type=float, default=1e-3)
     p.add_argument("--arith", choices=["ff", "f64"], default="ff")
     p.add_argument("--mass", type=float, default=MASS)
     p.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
@@ -556,20 +559,28 @@ def run_learned(args):
     npairs, k = 0, 0
     while npairs < args.pairs:
         src = [torch.from_numpy(inputs.gaussian_even_source(dims, 7000 + k)).to(dev)]
-        npairs = binding.stag_ptnet_add_pairs(net, src, stride=10, min_rel_residual=1e-6, max_pairs=args.pairs)
+        npairs = binding.stag_ptnet_add_pairs(net, src, stride=args.stride, min_rel_residual=args.min_rel,
+                                              max_pairs=args.pairs)
         k += 1
     t_pairs = time.perf_counter() - t0
     loss0 = binding.stag_ptnet_dataset_loss(net)
     t0 = time.perf_counter()
-    losses = binding.stag_ptnet_train(net, args.epochs, 16, 3e-3, seed=1)
+    t_fcg0 = None
+    # the network before training (its polynomial start) on the first test source
+    b0 = torch.from_numpy(inputs.gaussian_even_source(dims, 90000)).to(dev)
+    x0 = torch.zeros_like(b0)
+    _, info_init = binding.stag_fcg_solve(h.h, net, b0, x0, TOL, MAX_ITER)
+    losses = binding.stag_ptnet_train(net, args.epochs, 16, args.lr, seed=1)
     t_train = time.perf_counter() - t0
     loss1 = binding.stag_ptnet_dataset_loss(net)
-    res = {"fcg": [], "cg": []}
+    res = {"fcg": [], "fcg_fp32": [], "cg": []}
     for j in range(args.test_sources):
         b = torch.from_numpy(inputs.gaussian_even_source(dims, 90000 + j)).to(dev)
-        x = torch.zeros_like(b)
-        code, info = binding.stag_fcg_solve(h.h, net, b, x, TOL, MAX_ITER)
-        res["fcg"].append((code, info))
+        for key, prec in (("fcg", binding.STAG_ARITH_BF16), ("fcg_fp32", binding.STAG_ARITH_F32)):
+            binding.stag_ptnet_set_inference_precision(net, prec)
+            x = torch.zeros_like(b)
+            code, info = binding.stag_fcg_solve(h.h, net, b, x, TOL, MAX_ITER)
+            res[key].append((code, info))
         x2 = torch.zeros_like(b)
         code2, info2 = binding.stag_cg_solve(h.h, b, x2, TOL, MAX_ITER)
         res["cg"].append((code2, info2))
@@ -582,9 +593,10 @@ def run_learned(args):
         return {"solved": sum(1 for c, _ in rs if c == binding.STAG_OK), "iters_mean": float(np.mean(its)),
                 "time_s_mean": round(float(np.mean(ts)), 4),
                 "max_true_rel_residual": max(i["true_rel_residual"] for _, i in rs),
-                "fallbacks": sum(i["restarts"] for _, i in rs)}
+                "restarts": sum(i["restarts"] for _, i in rs),
+                "fallbacks": sum(i.get("fallbacks", 0) for _, i in rs)}
 
-    fcg, cg = summary(res["fcg"]), summary(res["cg"])
+    fcg, fcg32, cg = summary(res["fcg"]), summary(res["fcg_fp32"]), summary(res["cg"])
     line = {
         "metric": METRIC + " [learned-preconditioner workload]",
         "value": fcg["time_s_mean"],
@@ -600,14 +612,21 @@ def run_learned(args):
         "config": {"workload": f"flexible CG + 3-layer PT network (1-8-8-1 complex channels), "
                                f"{'x'.join(map(str, dims))} asqtad-form, m={args.mass}, tol {TOL}",
                    "pairs": npairs, "sources_for_pairs": k, "epochs": args.epochs, "batch": 16,
+                   "pair_stride": args.stride, "pairs_while_rel_residual_above": args.min_rel,
                    "test_sources": args.test_sources},
         "pair_generation_s": round(t_pairs, 2),
         "training_s": round(t_train, 2),
+        "untrained_start_first_source": {"iters": info_init["iters"], "restarts": info_init["restarts"],
+                                         "fallbacks": info_init["fallbacks"]},
+        "learning_rate": args.lr,
         "loss_before": loss0,
         "loss_after": loss1,
         "epoch_losses": [float(v) for v in losses],
         "fcg": fcg,
+        "fcg_fp32_inference": fcg32,
         "plain_cg_ff": cg,
+        "iteration_gain_fp32_inference": round(cg["iters_mean"] / fcg32["iters_mean"], 3),
+        "time_ratio_fp32_inference_over_cg": round(fcg32["time_s_mean"] / cg["time_s_mean"], 3),
         "iteration_gain": round(cg["iters_mean"] / fcg["iters_mean"], 3),
         "time_ratio_fcg_over_cg": round(fcg["time_s_mean"] / cg["time_s_mean"], 3),
     }

@@ -112,6 +112,8 @@ typedef struct {
     double true_rel_residual; /* |b - A x| / |b|, A applied in native FP64                 */
     double iter_rel_residual; /* sqrt(delta_new) / |b| of the last Fig. 1 iterate          */
     double time_ms;           /* wall time of the solve inside the call                     */
+    int32_t fallbacks;        /* flexible CG: hand-overs to plain CG                        */
+    int32_t reserved;
 } stag_solve_info;
 
 /* Fill *opt with the defaults.  Returns STAG_ERR_INVALID_ARG if opt is NULL. */
@@ -256,7 +258,10 @@ int stag_batch_destroy(stag_batch* b);
 typedef struct stag_ptnet stag_ptnet;
 
 /* precision: STAG_ARITH_BF16 (activations stored as BF16, FP32 arithmetic) or
- * STAG_ARITH_F32.  Weights start as 0.1 * identity plus seeded noise. */
+ * STAG_ARITH_F32.  The weights start as the least-squares degree-1 polynomial
+ * preconditioner alpha + beta A_fat (alpha = 4/L, beta = -10/(3 L^2), L = 1.25
+ * times the Rayleigh quotient after 100 power iterations; A_fat: m^2 - D^2 with
+ * the one-hop links the transports use) plus small noise seeded by `seed`. */
 int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint64_t seed);
 int64_t stag_ptnet_num_weights(const stag_ptnet* n);
 int stag_ptnet_set_weights(stag_ptnet* n, const double* w, int64_t count);
@@ -290,14 +295,21 @@ int stag_ptnet_dataset_loss(stag_ptnet* n, double* loss);
 const char* stag_ptnet_last_error(const stag_ptnet* n);
 int stag_ptnet_destroy(stag_ptnet* n);
 
+/* Storage of the activations when the network is applied (stag_ptnet_apply,
+ * stag_fcg_solve): STAG_ARITH_BF16 or STAG_ARITH_F32 (default: the precision
+ * given at create).  Training and the stored pairs keep the create precision. */
+int stag_ptnet_set_inference_precision(stag_ptnet* n, int32_t precision);
+
 /* Flexible CG with z_k = M(r_k): alpha = (r, z) / (p, A p), x += alpha p,
  * r -= alpha A p, beta = (z_new, r_new - r_old) / (r_old, z_old), p = z + beta p,
  * with A in the handle's FP64-class arithmetic and FP64 vectors.  When the
  * iterated residual falls below tol |b| the true residual is recomputed in
- * native FP64 and judges convergence; when |r| drops less than 10 % in 60
- * iterations, or (r, z) or (p, A p) is not positive, plain CG continues from the
- * current x.  info->restarts counts these fallbacks; the arguments and return
- * codes are those of stag_cg_solve. */
+ * native FP64 and judges convergence.  When the smallest |r| so far has not
+ * dropped by 10 % within 100 iterations: if this cycle reduced the true
+ * residual more than 100-fold, flexible CG restarts from the true residual
+ * (info->restarts), otherwise plain CG continues from the current x
+ * (info->fallbacks); (r, z) <= 0 or (p, A p) <= 0 also hand over to plain CG.
+ * The arguments and return codes are those of stag_cg_solve. */
 int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* x_even, double tol,
                    int32_t max_iter, stag_solve_info* info);
 

@@ -76,6 +76,7 @@ EXPORTED = (
     "stag_ptnet_dataset_loss",
     "stag_ptnet_last_error",
     "stag_ptnet_destroy",
+    "stag_ptnet_set_inference_precision",
     "stag_fcg_solve",
 )
 
@@ -103,10 +104,12 @@ class stag_solve_info(ctypes.Structure):
         ("true_rel_residual", ctypes.c_double),
         ("iter_rel_residual", ctypes.c_double),
         ("time_ms", ctypes.c_double),
+        ("fallbacks", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class StagError(RuntimeError):
@@ -181,6 +184,7 @@ def load(path: str | None = None):
     lib.stag_ptnet_last_error.argtypes = [H]
     lib.stag_ptnet_last_error.restype = ctypes.c_char_p
     lib.stag_ptnet_destroy.argtypes = [H]
+    lib.stag_ptnet_set_inference_precision.argtypes = [H, i32]
     lib.stag_fcg_solve.argtypes = [H, H, P, P, d, i32, ctypes.POINTER(stag_solve_info)]
     for name in EXPORTED:
         if name not in ("stag_last_error", "stag_device_bytes", "stag_launch_count", "stag_batch_last_error",
@@ -414,6 +418,10 @@ def stag_ptnet_dataset_loss(net):
     v = ctypes.c_double()
     _pcheck(load().stag_ptnet_dataset_loss(net, ctypes.byref(v)), net)
     return v.value
+
+
+def stag_ptnet_set_inference_precision(net, precision):
+    _pcheck(load().stag_ptnet_set_inference_precision(net, int(precision)), net)
 
 
 def stag_ptnet_destroy(net):

@@ -31,6 +31,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <random>
@@ -432,6 +434,35 @@ __global__ void pt_adam_kernel(float* w, const float* grad, float* m, float* v, 
     w[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
 }
 
+// v = a fixed pseudo-random vector (start of the power iteration)
+__global__ void pt_fill_kernel(Geom g, float2* v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        unsigned int h = (unsigned int)(c * vs + i) * 2654435761u + 12345u;
+        h ^= h >> 15;
+        h *= 2246822519u;
+        h ^= h >> 13;
+        const float a = (float)(h & 0xffff) / 65536.f - 0.5f;
+        const float b = (float)(h >> 16) / 65536.f - 0.5f;
+        v[c * vs + i] = make_float2(a, b);
+    }
+}
+
+// v = s * w
+__global__ void pt_scale_kernel(Geom g, float2* v, const float2* w, float s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 a = w[c * vs + i];
+        v[c * vs + i] = make_float2(s * a.x, s * a.y);
+    }
+}
+
 // FP32 copy of the eta-folded FP64 links
 __global__ void pt_links_kernel(const double2* __restrict__ in, float2* __restrict__ out, size_t n) {
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -526,7 +557,8 @@ using namespace stag;
 struct stag_ptnet {
     stag_handle* h = nullptr;
     Geom g{};
-    int prec = STAG_ARITH_BF16;  // activation storage: STAG_ARITH_BF16 or STAG_ARITH_F32
+    int prec = STAG_ARITH_BF16;  // activation storage of training and pairs: STAG_ARITH_BF16 or STAG_ARITH_F32
+    int inf_prec = STAG_ARITH_BF16;  // activation storage when the network is applied
     size_t elem = 4;             // bytes per stored complex
     float2* links = nullptr;     // FP32 eta-folded fat links (transports and A)
     float2* lng = nullptr;       // FP32 eta-folded Naik links (A), or nullptr
@@ -584,7 +616,7 @@ void* palloc(stag_ptnet* n, size_t bytes, const char* what) {
 }
 
 cudaStream_t S(stag_ptnet* n) { return n->h->s; }
-size_t field_bytes(const stag_ptnet* n, int ch) { return (size_t)ch * 3 * 2 * n->g.vs * n->elem; }
+size_t field_bytes(const stag_ptnet* n, int ch) { return (size_t)ch * 3 * 2 * n->g.vs * sizeof(float2); }
 size_t slot_bytes(const stag_ptnet* n) { return (size_t)3 * n->g.vs * n->elem; }
 int site_blocks(const Geom& g) { return blocks_for(2 * g.vh); }
 
@@ -740,6 +772,7 @@ void destroy_net(stag_ptnet* n) {
 }
 
 bool is_bf16(const stag_ptnet* n) { return n->prec == STAG_ARITH_BF16; }
+bool infer_bf16(const stag_ptnet* n) { return n->inf_prec == STAG_ARITH_BF16; }
 
 // FP64-class A p into q (FP64): float-float when the handle has it, else native FP64
 void apply_A_q(stag_ptnet* n, const double2* p, double2* q) {
@@ -794,6 +827,7 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         n->h = h;
         n->g = h->g;
         n->prec = precision;
+        n->inf_prec = precision;
         n->elem = precision == STAG_ARITH_BF16 ? sizeof(__nv_bfloat162) : sizeof(float2);
         handle_begin(h);
         const size_t nl = (size_t)2 * 4 * 9 * n->g.vs;
@@ -826,16 +860,51 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         n->fp = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
         n->fq = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
         n->fro = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
-        // initial weights: M = s * identity through channel 0, plus small seeded noise
+        // initial weights: the least-squares degree-1 polynomial preconditioner
+        // alpha + beta A_fat (A_fat: the one-hop part the transports can express),
+        // minimising the integral of (1 - lambda p(lambda))^2 over [0, Lmax]:
+        // alpha = 4 / Lmax, beta = -10 / (3 Lmax^2); Lmax = 1.25 times the Rayleigh
+        // quotient after 100 power iterations of the FP32 operator (the quotient
+        // approaches the largest eigenvalue from below, slowly when the top of the
+        // spectrum is dense; lambda p(lambda) stays positive up to 1.2 Lmax).
+        // Plus small seeded noise.
+        pt_fill_kernel<<<blocks_for(n->g.vh), kBlock, 0, S(n)>>>(n->g, n->va);
+        double lam = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            apply_A_f32(n);
+            pt_dot_f32_kernel<<<blocks_for(n->g.vh), kBlock, 0, S(n)>>>(n->g, n->va, n->vad, n->red);
+            const double num = read_partials(n, blocks_for(n->g.vh));
+            pt_dot_f32_kernel<<<blocks_for(n->g.vh), kBlock, 0, S(n)>>>(n->g, n->va, n->va, n->red);
+            const double den = read_partials(n, blocks_for(n->g.vh));
+            pt_dot_f32_kernel<<<blocks_for(n->g.vh), kBlock, 0, S(n)>>>(n->g, n->vad, n->vad, n->red);
+            const double nrm = std::sqrt(read_partials(n, blocks_for(n->g.vh)));
+            if (den > 0.0) lam = num / den;
+            if (!(nrm > 0.0)) break;
+            pt_scale_kernel<<<blocks_for(n->g.vh), kBlock, 0, S(n)>>>(n->g, n->va, n->vad, (float)(1.0 / nrm));
+        }
+        const double lmax = 1.25 * std::max(lam, 1e-6);
+        const double alpha = 4.0 / lmax, beta = -10.0 / (3.0 * lmax * lmax);
+        const double m2 = h->mass * h->mass;
         n->w_host.assign(nw, make_float2(0.f, 0.f));
         std::mt19937_64 rng(seed);
         std::normal_distribution<float> nd(0.f, 1.f);
         for (int l = 0; l < kLayers; ++l) {
             const int cin = kChan[l], cout = kChan[l + 1];
-            const float sc = 0.02f / std::sqrt((float)(kPaths * cin));
+            const float sc = 1e-4f / std::sqrt((float)(kPaths * cin));  // symmetry breaking only
             for (int k = 0; k < kPaths * cin * cout; ++k)
                 n->w_host[layer_offset(l) + k] = make_float2(sc * nd(rng), sc * nd(rng));
-            n->w_host[layer_offset(l) + 0].x += (l == kLayers - 1) ? 0.1f : 1.0f;  // identity path, channel 0 -> 0
+        }
+        auto W = [&](int l, int p, int o, int i) -> float2& {
+            return n->w_host[layer_offset(l) + (p * kChan[l + 1] + o) * kChan[l] + i];
+        };
+        W(0, 0, 0, 0).x += 1.f;                       // channel 0: r
+        W(1, 0, 0, 0).x += (float)(alpha + beta * m2); // (alpha + beta m^2) r
+        W(2, 0, 0, 0).x += 1.f;                       // output: channel 0
+        for (int mu = 0; mu < 4; ++mu) {
+            W(0, 1 + 2 * mu, 1, 0).x += 1.f;           // channel 1: D r
+            W(0, 2 + 2 * mu, 1, 0).x -= 1.f;
+            W(1, 1 + 2 * mu, 0, 1).x -= (float)beta;   // - beta D (D r)
+            W(1, 2 + 2 * mu, 0, 1).x += (float)beta;
         }
         upload_weights(n);
         pcheck(n, cudaGetLastError(), "ptnet create");
@@ -898,7 +967,7 @@ int stag_ptnet_apply(stag_ptnet* n, const double* r_even, double* z_even) {
         double d3[3];
         dots(n, n->fr, n->fr, nullptr, d3);
         const double rn = std::sqrt(d3[0]);
-        if (is_bf16(n))
+        if (infer_bf16(n))
             apply_net<__nv_bfloat162>(n, n->fr, rn, n->fz);
         else
             apply_net<float2>(n, n->fr, rn, n->fz);
@@ -1122,6 +1191,12 @@ int stag_ptnet_dataset_loss(stag_ptnet* n, double* loss) {
     }
 }
 
+int stag_ptnet_set_inference_precision(stag_ptnet* n, int32_t precision) {
+    if (!n || (precision != STAG_ARITH_BF16 && precision != STAG_ARITH_F32)) return STAG_ERR_INVALID_ARG;
+    n->inf_prec = precision;
+    return STAG_OK;
+}
+
 int stag_ptnet_num_pairs(const stag_ptnet* n) { return n ? (int)n->pairs_r.size() : 0; }
 
 const char* stag_ptnet_last_error(const stag_ptnet* n) { return n ? n->err.c_str() : "NULL network"; }
@@ -1161,10 +1236,10 @@ int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* 
         if (!std::isfinite(bnorm2)) pfail(n, STAG_ERR_INVALID_ARG, "source has non-finite entries");
         const long long max_it = max_iter > 0 ? max_iter : 3LL * g.vh;
         long long iters = 0;
-        int fallbacks = 0;
+        int fallbacks = 0, restarts = 0;
         double rel = 0.0;
         auto precond = [&](const double2* r, double rnorm, double2* z) {
-            if (is_bf16(n))
+            if (infer_bf16(n))
                 apply_net<__nv_bfloat162>(n, r, rnorm, z);
             else
                 apply_net<float2>(n, r, rnorm, z);
@@ -1179,9 +1254,11 @@ int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* 
             pcheck(n, cudaMemsetAsync(h->x, 0, (size_t)3 * g.vs * sizeof(double2), S(n)), "zero x");
         } else {
             bool use_plain = false;
+            double cycle_start_rel = 0.0;
             while (true) {
                 // r = b - A x (FP64), z = M r, p = z
                 rel = true_residual();
+                cycle_start_rel = rel;
                 if (rel <= tol) break;
                 if (iters >= max_it) {
                     status = STAG_ERR_NOT_CONVERGED;
@@ -1200,14 +1277,19 @@ int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* 
                 pcheck(n, cudaMemcpyAsync(n->fp, n->fz, (size_t)3 * g.vs * sizeof(double2), cudaMemcpyDeviceToDevice, S(n)), "p = z");
                 dots(n, n->fr, n->fz, nullptr, d3);
                 double rz = d3[0];
-                std::vector<double> hist;
+                // stall: the best |r| so far has not dropped by 10 % within 100 iterations
+                double best = rr, mark = rr;
+                long long mark_it = iters;
+                const char* why = nullptr;
                 bool stalled = !(rz > 0.0);
+                if (stalled) why = "(r, z) <= 0";
                 while (!stalled && iters < max_it && rr > tol * tol * bnorm2) {
                     apply_A_q(n, n->fp, n->fq);
                     dots(n, n->fp, n->fq, nullptr, d3);
                     const double pq = d3[0];
                     if (!(pq > 0.0)) {
                         stalled = true;
+                        why = "(p, A p) <= 0";
                         break;
                     }
                     const double alpha = rz / pq;
@@ -1215,10 +1297,13 @@ int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* 
                     dots(n, n->fr, n->fr, nullptr, d3);
                     rr = d3[0];
                     ++iters;
-                    hist.push_back(rr);
-                    // stall: less than a 10 % drop of |r| over the last 60 iterations
-                    if (hist.size() > 60 && std::sqrt(rr) > 0.9 * std::sqrt(hist[hist.size() - 61])) {
+                    best = std::min(best, rr);
+                    if (best < 0.81 * mark) {
+                        mark = best;
+                        mark_it = iters;
+                    } else if (iters - mark_it > 100) {
                         stalled = true;
+                        why = "no 10 % drop of the best residual in 100 iterations";
                         break;
                     }
                     precond(n->fr, std::sqrt(rr), n->fz);
@@ -1227,19 +1312,31 @@ int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* 
                     rz = d3[0];
                     if (!(rz > 0.0)) {
                         stalled = true;
+                        why = "(r, z) <= 0";
                         break;
                     }
                     fcg_dir_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->fp, n->fz, beta);
                 }
                 if (stalled) {
-                    use_plain = true;
-                    ++fallbacks;
+                    // a cycle that cut the residual 100-fold restarts flexible CG; otherwise plain CG
+                    const bool progress = std::sqrt(rr / bnorm2) < 0.01 * cycle_start_rel &&
+                                          std::strcmp(why, "(r, z) <= 0") != 0 && std::strcmp(why, "(p, A p) <= 0") != 0;
+                    if (std::getenv("STAG_DEBUG"))
+                        std::fprintf(stderr, "stag_fcg_solve: %s after %lld iterations: %s (|r|/|b| = %.3e)\n",
+                                     progress ? "restart" : "fallback to plain CG", iters, why, std::sqrt(rr / bnorm2));
+                    if (progress) {
+                        ++restarts;
+                    } else {
+                        use_plain = true;
+                        ++fallbacks;
+                    }
                 }
             }
             inf.iter_rel_residual = rel;
         }
         inf.iters = (int32_t)iters;
-        inf.restarts = fallbacks;
+        inf.restarts = restarts;
+        inf.fallbacks = fallbacks;
         inf.true_rel_residual = rel;
         if (status == STAG_ERR_NOT_CONVERGED) h->err = "flexible CG: not converged";
         launch_unpack_vec(g, h->x, x_dev ? x_even : h->io_b, S(n));

@@ -136,32 +136,54 @@ def test_gradient_matches_oracle_finite_differences():
     assert np.abs(fd - gpu).max() <= 1e-3 * np.abs(fd).max()
 
 
+def _poor_start():
+    """0.1 * identity through channel 0 - a deliberately poor starting point."""
+    w = _random_flat(111, 0.002)
+    w1, w2, w3 = _split(w.copy())
+    w1[0, 0, 0] += 1
+    w2[0, 0, 0] += 1
+    w3[0, 0, 0] += 0.1
+    return np.concatenate([w1.ravel(), w2.ravel(), w3.ravel()])
+
+
 @pytest.fixture(scope="module")
 def trained():
-    """8^4 asqtad-form field, m = 0.05: pairs from plain-CG solves, BF16 network trained on them."""
+    """8^4 asqtad-form field, m = 0.05: pairs from plain-CG solves; one BF16 network from
+    the library's polynomial start, one from a poor start, both trained on the pairs."""
     dims, m = (8, 8, 8, 8), 0.05
     fat, lng = inputs.asqtad_form_fields(dims, seeds=(101, 102, 103))
     h = _handle(fat, lng, dims, m)
-    net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 7)
     sources = [_dev(inputs.gaussian_even_source(dims, 200 + k)) for k in range(4)]
-    npairs = binding.stag_ptnet_add_pairs(net, sources, stride=4, min_rel_residual=1e-6, max_pairs=400)
-    before = binding.stag_ptnet_dataset_loss(net)
-    losses = binding.stag_ptnet_train(net, epochs=8, batch=8, lr=3e-3, seed=1)
-    after = binding.stag_ptnet_dataset_loss(net)
-    yield dict(dims=dims, m=m, fat=fat, lng=lng, h=h, net=net, npairs=npairs, before=before, after=after,
-               losses=losses)
-    binding.stag_ptnet_destroy(net)
+    out = dict(dims=dims, m=m, fat=fat, lng=lng, h=h)
+    for name, weights in (("poly", None), ("poor", _poor_start())):
+        net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 7)
+        if weights is not None:
+            binding.stag_ptnet_set_weights(net, weights)
+        npairs = binding.stag_ptnet_add_pairs(net, sources, stride=2, min_rel_residual=0.05, max_pairs=400)
+        before = binding.stag_ptnet_dataset_loss(net)
+        losses = binding.stag_ptnet_train(net, epochs=6, batch=8, lr=3e-3, seed=1)
+        after = binding.stag_ptnet_dataset_loss(net)
+        out[name] = dict(net=net, npairs=npairs, before=before, after=after, losses=losses)
+    yield out
+    for name in ("poly", "poor"):
+        binding.stag_ptnet_destroy(out[name]["net"])
     h.close()
 
 
-def test_training_reduces_loss(trained):
-    assert trained["npairs"] >= 100
-    assert trained["after"] < 0.8 * trained["before"], (trained["before"], trained["after"], trained["losses"])
-    assert np.all(np.isfinite(trained["losses"]))
+def test_training_reduces_loss_from_a_poor_start(trained):
+    t = trained["poor"]
+    assert t["npairs"] >= 100
+    assert t["after"] < 0.8 * t["before"], (t["before"], t["after"], t["losses"])
+    assert np.all(np.isfinite(t["losses"]))
+
+
+def test_training_keeps_the_polynomial_start(trained):
+    t = trained["poly"]
+    assert t["after"] <= 1.001 * t["before"], (t["before"], t["after"], t["losses"])
 
 
 def test_fcg_with_trained_network_gains_over_plain_cg(trained):
-    dims, m, h, net = trained["dims"], trained["m"], trained["h"], trained["net"]
+    dims, m, h, net = trained["dims"], trained["m"], trained["h"], trained["poly"]["net"]
     op = oracle.Operator(trained["fat"], trained["lng"], m, dims)
     it_fcg, it_cg = [], []
     for k in range(3):
@@ -173,13 +195,13 @@ def test_fcg_with_trained_network_gains_over_plain_cg(trained):
         xs = x.cpu().numpy().reshape(-1)
         ref = oracle.solve(op.apply_A, b, tol=1e-13, max_iter=200000, max_restarts=20)["x"]
         assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-8
-        it_fcg.append((info["iters"], info["restarts"]))
+        it_fcg.append((info["iters"], info["fallbacks"]))
         x2 = torch.zeros_like(x)
         code, info2 = binding.stag_cg_solve(h.h, _dev(b), x2, 1e-10)
         it_cg.append(info2["iters"])
     assert all(rs == 0 for _, rs in it_fcg), it_fcg  # no fallback to plain CG
-    # at least 10 % fewer iterations than CG without the network
-    assert sum(i for i, _ in it_fcg) < 0.9 * sum(it_cg), (it_fcg, it_cg)
+    # at least 20 % fewer iterations than CG without the network
+    assert sum(i for i, _ in it_fcg) < 0.8 * sum(it_cg), (it_fcg, it_cg)
 
 
 def test_fcg_falls_back_to_plain_cg(trained):
@@ -195,4 +217,4 @@ def test_fcg_falls_back_to_plain_cg(trained):
             code, info = binding.stag_fcg_solve(h.h, net, b, x, 1e-10)
         finally:
             binding.stag_ptnet_destroy(net)
-    assert code == binding.STAG_OK and info["restarts"] >= 1 and info["true_rel_residual"] <= 1e-10
+    assert code == binding.STAG_OK and info["fallbacks"] >= 1 and info["true_rel_residual"] <= 1e-10

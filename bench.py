@@ -50,7 +50,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["single", "batched", "learned"], default="single")
+    p.add_argument("--workload", choices=["single", "batched", "learned", "decomposed"], default="single")
     p.add_argument("--pairs", type=int, default=2000)
     p.add_argument("--test-sources", type=int, default=64)
     p.add_argument("--epochs", type=int, default=4)
@@ -633,6 +633,75 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------- decomposed workload
+# Sec. 4, Table 2: per-node times of the multi-GPU CG on 28^3 x 96 (FP64, one-hop
+# operator, GTX 295 per node, 20 Gb InfiniBand), in ms.
+PAPER_TABLE2 = {4: {"dirac": 4.7, "collect": 0.9, "d2h": 2.9, "exchange": 2.3, "h2d": 3.4},
+                8: {"dirac": 2.45, "collect": 0.5, "d2h": 2.1, "exchange": 1.8, "h2d": 1.7}}
+
+
+def run_decomposed(args):
+    """The paper's decomposition emulated on one GPU: 28^3 x 96, one-hop FP64 operator,
+    4 and 8 slabs along t; per-rank time of each step of one A application with the
+    faces staged through the host (the paper's path) or copied device to device."""
+    import numpy as np
+    import torch
+
+    from paper_1010_4782_gb300 import binding, build, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    binding.load()
+    dims = tuple(args.dims)
+    opt = binding.stag_default_options()
+    opt.arith = binding.STAG_ARITH_F64
+    h = binding.Handle(torch.from_numpy(inputs.gauge_field(dims, 1)).to(dev), dims, args.mass, options=opt)
+    v = torch.from_numpy(inputs.gaussian_even_source(dims, 3)).to(dev)
+    out = torch.empty_like(v)
+    reps = 10
+    results = {}
+    for P in (4, 8):
+        dd = binding.stag_dd_create(h.h, P)
+        try:
+            for mode, name in ((binding.STAG_DD_HOST, "host_staged"), (binding.STAG_DD_DEVICE, "device_direct")):
+                binding.stag_dd_apply_A(dd, h.h, v, out, mode)  # warm-up
+                acc = dict.fromkeys(binding.DD_PHASES, 0.0)
+                for _ in range(reps):
+                    ph = binding.stag_dd_apply_A(dd, h.h, v, out, mode)
+                    for k in acc:
+                        acc[k] += ph[k]
+                per_rank = {k: round(acc[k] / reps / P, 4) for k in acc}
+                per_rank["total"] = round(sum(per_rank.values()), 4)
+                results[f"{P}_ranks_{name}"] = per_rank
+            x = torch.zeros_like(v)
+            code, info, ph = binding.stag_dd_cg_solve(dd, h.h, v, x, TOL, MAX_ITER, binding.STAG_DD_HOST)
+            results[f"{P}_ranks_cg_host_staged"] = {
+                "status": code, "iters": info["iters"], "true_rel_residual": info["true_rel_residual"],
+                "time_s": round(info["time_ms"] / 1e3, 3),
+                "per_iteration_per_rank_ms": {k: round(ph[k] / max(1, info["iters"]) / P, 4) for k in ph}}
+        finally:
+            binding.stag_dd_destroy(dd)
+    ref = torch.empty_like(v)
+    binding.stag_apply_A(h.h, v, ref)
+    h.close()
+    line = {
+        "metric": METRIC + " [emulated decomposition, Table 2]",
+        "value": results["4_ranks_host_staged"]["total"],
+        "unit": "ms per A application per rank",
+        "n_gpus": world,
+        "higher_is_better": False,
+        "dtype": "f64",
+        "data": "synthetic (seeded SU(3) field exp(0.3 i H), Gaussian vector)",
+        "config": {"workload": f"{'x'.join(map(str, dims))} one-hop FP64, slabs along t, m={args.mass}",
+                   "note": "all ranks on one GPU: per-rank = total over ranks / ranks"},
+        "results": results,
+        "paper_table2_per_node_ms": PAPER_TABLE2,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(fat, lng, b, dims, mass, iters, restarts):
     """Oracle: initial residual + one Fig. 1 iteration (two A applications) at full size."""
     import numpy as np
@@ -712,6 +781,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "decomposed":
+        run_decomposed(args)
     else:
         run_ours(args)
 

@@ -313,6 +313,35 @@ int stag_ptnet_set_inference_precision(stag_ptnet* n, int32_t precision);
 int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* x_even, double tol,
                    int32_t max_iter, stag_solve_info* info);
 
+/* ------------------------------------- emulated domain decomposition
+ * The multi-GPU decomposition of Sec. 4 emulated on one GPU: the lattice is cut
+ * into n_ranks slabs along t (Lt / n_ranks even and at least the hop reach, 1
+ * or 3), each stored with ghost t-slices, and before every half-Dslash each
+ * rank's boundary faces are packed ("boundary data collect"), exchanged and
+ * unpacked into its neighbours' ghost slices.  STAG_DD_HOST stages the faces
+ * through pinned host memory with host copies between the ranks' buffers (the
+ * paper's GPU -> host -> MPI -> host -> GPU path); STAG_DD_DEVICE copies them
+ * device to device (the direct path Sec. 5 proposes).  Native FP64 arithmetic.
+ * phase_ms (nullable, 6 entries, summed over all ranks and calls of the solve):
+ * [0] Dirac kernels, [1] face pack + unpack, [2] device -> host, [3] exchange
+ * between ranks (host copies, or device copies in STAG_DD_DEVICE), [4] host ->
+ * device, [5] global sums of the dot products.  The object keeps a pointer to
+ * its handle; destroy it first. */
+enum { STAG_DD_HOST = 0, STAG_DD_DEVICE = 1 };
+typedef struct stag_dd stag_dd;
+int stag_dd_create(stag_dd** out, stag_handle* h, int32_t n_ranks);
+/* out_even = A in_even through the decomposition (bit-identical to stag_apply_A
+ * with STAG_ARITH_F64). */
+int stag_dd_apply_A(stag_dd* dd, const double* in_even, double* out_even, int32_t mode, double* phase_ms);
+/* Fig. 1 CG with the decomposed operator; every dot product is a per-rank
+ * partial sum gathered to the host and summed over the ranks; the true residual
+ * is recomputed at the end (no restart).  Arguments and codes as stag_cg_solve. */
+int stag_dd_cg_solve(stag_dd* dd, const double* b_even, double* x_even, double tol, int32_t max_iter,
+                     int32_t mode, stag_solve_info* info, double* phase_ms);
+/* Bytes of faces exchanged since create. */
+int64_t stag_dd_bytes_exchanged(const stag_dd* dd);
+int stag_dd_destroy(stag_dd* dd);
+
 /* Largest V/2 that stag_apply_A_noalloc accepts. */
 #define STAG_NOALLOC_MAX_HALF_SITES 65536
 

@@ -33,6 +33,10 @@ STAG_INNER_NONE = 0
 STAG_INNER_F32 = 1
 STAG_INNER_F16 = 2
 
+STAG_DD_HOST = 0
+STAG_DD_DEVICE = 1
+DD_PHASES = ("dirac", "collect", "d2h", "exchange", "h2d", "global_sum")
+
 STAG_KERNEL_DSLASH_OE = 0
 STAG_KERNEL_DSLASH_EO = 1
 STAG_KERNEL_UPDATE_XR = 2
@@ -78,6 +82,11 @@ EXPORTED = (
     "stag_ptnet_destroy",
     "stag_ptnet_set_inference_precision",
     "stag_fcg_solve",
+    "stag_dd_create",
+    "stag_dd_apply_A",
+    "stag_dd_cg_solve",
+    "stag_dd_bytes_exchanged",
+    "stag_dd_destroy",
 )
 
 
@@ -186,9 +195,16 @@ def load(path: str | None = None):
     lib.stag_ptnet_destroy.argtypes = [H]
     lib.stag_ptnet_set_inference_precision.argtypes = [H, i32]
     lib.stag_fcg_solve.argtypes = [H, H, P, P, d, i32, ctypes.POINTER(stag_solve_info)]
+    lib.stag_dd_create.argtypes = [ctypes.POINTER(H), H, i32]
+    lib.stag_dd_apply_A.argtypes = [H, P, P, i32, P]
+    lib.stag_dd_cg_solve.argtypes = [H, P, P, d, i32, i32, ctypes.POINTER(stag_solve_info), P]
+    lib.stag_dd_bytes_exchanged.argtypes = [H]
+    lib.stag_dd_bytes_exchanged.restype = ctypes.c_int64
+    lib.stag_dd_destroy.argtypes = [H]
     for name in EXPORTED:
         if name not in ("stag_last_error", "stag_device_bytes", "stag_launch_count", "stag_batch_last_error",
-                        "stag_batch_device_bytes", "stag_ptnet_num_weights", "stag_ptnet_last_error"):
+                        "stag_batch_device_bytes", "stag_ptnet_num_weights", "stag_ptnet_last_error",
+                        "stag_dd_bytes_exchanged"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -435,6 +451,33 @@ def stag_fcg_solve(h, net, b, x, tol, max_iter=0):
     if code not in (STAG_OK, STAG_ERR_NOT_CONVERGED):
         _check(code, h)
     return code, info.as_dict()
+
+
+def stag_dd_create(h, n_ranks):
+    dd = ctypes.c_void_p()
+    _check(load().stag_dd_create(ctypes.byref(dd), h, int(n_ranks)), h)
+    return dd
+
+
+def stag_dd_apply_A(dd, h, inp, out, mode=STAG_DD_HOST):
+    ph = np.zeros(6, dtype=np.float64)
+    _check(load().stag_dd_apply_A(dd, _ptr(inp), _ptr(out), int(mode), ph.ctypes.data), h)
+    return dict(zip(DD_PHASES, ph.tolist()))
+
+
+def stag_dd_cg_solve(dd, h, b, x, tol, max_iter=0, mode=STAG_DD_HOST):
+    info = stag_solve_info()
+    ph = np.zeros(6, dtype=np.float64)
+    code = load().stag_dd_cg_solve(dd, _ptr(b), _ptr(x), float(tol), int(max_iter), int(mode), ctypes.byref(info),
+                                   ph.ctypes.data)
+    if code not in (STAG_OK, STAG_ERR_NOT_CONVERGED):
+        _check(code, h)
+    return code, info.as_dict(), dict(zip(DD_PHASES, ph.tolist()))
+
+
+def stag_dd_destroy(dd):
+    if dd is not None:
+        load().stag_dd_destroy(dd)
 
 
 class Handle:

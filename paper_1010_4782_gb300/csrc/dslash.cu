@@ -166,6 +166,7 @@ struct DslashParams {
     float2 m2_ff;              // m^2 as float-float (EPI_AXPY, FF)
     CgScalars* scal;
     double* partials;
+    int i0, i1;                // output sites [i0, i1) of parity P
 };
 
 template <class A>
@@ -206,11 +207,11 @@ __global__ void __launch_bounds__(kBlock, 4) dslash_kernel(const DslashParams<A>
         if (p.scal->done) return;
     }
     const Geom& g = p.g;
-    const int i = blockIdx.x * kBlock + threadIdx.x;
+    const int i = p.i0 + blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;
     typename A::Acc acc;
     A::zero(acc);
-    const bool active = i < g.vh;
+    const bool active = i < p.i1;
     if (active) {
         int x, y, z, t;
         site_coords(i, p.P, g, x, y, z, t);
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kBlock, 4) dslash_kernel(const DslashParams<A>
 
 template <class A, int EPI>
 static void launch_one(const DslashParams<A>& p, bool naik, cudaStream_t s) {
-    const int blocks = blocks_for(p.g.vh);
+    const int blocks = blocks_for(p.i1 - p.i0);
     if (naik)
         dslash_kernel<A, true, EPI><<<blocks, kBlock, 0, s>>>(p);
     else
@@ -289,7 +290,15 @@ void launch_dslash_f64(const Geom& g, int out_parity, const LinkSet& L, const do
                        double2* out, Epilogue epi, const double2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s) {
     DslashParams<ArithF64> p{g, out_parity, L.fat64, L.lng64, in, out, src, m2,
-                             make_float2(0.f, 0.f), scal, partials};
+                             make_float2(0.f, 0.f), scal, partials, 0, g.vh};
+    launch_any(p, L.lng64 != nullptr, epi, s);
+}
+
+void launch_dslash_f64_range(const Geom& g, int out_parity, const LinkSet& L, const double2* in, double2* out,
+                             Epilogue epi, const double2* src, double m2, int i0, int i1, cudaStream_t s) {
+    if (i1 <= i0) return;
+    DslashParams<ArithF64> p{g, out_parity, L.fat64, L.lng64, in, out, src, m2,
+                             make_float2(0.f, 0.f), nullptr, nullptr, i0, i1};
     launch_any(p, L.lng64 != nullptr, epi, s);
 }
 
@@ -297,21 +306,23 @@ void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const flo
                       float4* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
                       double* partials, cudaStream_t s) {
     DslashParams<ArithFF> p{g, out_parity, L.fatff, L.lngff, in, out, src, m2,
-                            host_ff_from_double(m2), scal, partials};
+                            host_ff_from_double(m2), scal, partials, 0, g.vh};
     launch_any(p, L.lngff != nullptr, epi, s);
 }
 
 void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const float2* lng,
                        const float2* in, float2* out, Epilogue epi, const float2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s) {
-    DslashParams<ArithF32> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials};
+    DslashParams<ArithF32> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials, 0,
+                             g.vh};
     launch_any(p, lng != nullptr, epi, s);
 }
 
 void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng,
                        const __half2* in, __half2* out, Epilogue epi, const __half2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s) {
-    DslashParams<ArithH16> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials};
+    DslashParams<ArithH16> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials, 0,
+                             g.vh};
     launch_any(p, lng != nullptr, epi, s);
 }
 

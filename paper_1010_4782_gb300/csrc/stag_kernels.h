@@ -35,6 +35,9 @@ void launch_unpack_vec(const Geom& g, const double2* soa, double* aos, cudaStrea
 void launch_dslash_f64(const Geom& g, int out_parity, const LinkSet& L, const double2* in,
                        double2* out, Epilogue epi, const double2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s);
+// FP64 half-Dslash over output sites [i0, i1) only (no reduction epilogue)
+void launch_dslash_f64_range(const Geom& g, int out_parity, const LinkSet& L, const double2* in, double2* out,
+                             Epilogue epi, const double2* src, double m2, int i0, int i1, cudaStream_t s);
 void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const float4* in,
                       float4* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
                       double* partials, cudaStream_t s);

@@ -20,6 +20,15 @@ preconditioner of flexible CG.  Definitions:
   * loss of a pair (r, e): the residual norm of the correction, i.e. the
     error d = M(r) - e in the norm |A .|:
         L = |A d|^2 / |A e|^2.
+  * self-adjoint tie: with E the embedding of even-site vectors and L_l the
+    layers, M = E^dag L_3 L_2 L_1 E is Hermitian when L_3 = L_1^dag and
+    L_2 = L_2^dag.  The adjoint of a layer has the weights
+    W^dag[p][i][o] = conj(W[rev(p)][o][i]), rev(p) the path in the opposite
+    direction (T_{+mu}^dag = T_{-mu}), so the tie is
+        W_3[p][0][i] = conj(W_1[rev(p)][i][0]),
+        W_2[p][o][i] = conj(W_2[rev(p)][i][o]);
+    `tie` projects arbitrary weights onto these relations (the mean of each
+    weight and its partner's conjugate).
   * flexible CG (Notay 2000): z_k = M(r_k), p_0 = z_0,
     alpha = (r_k, z_k) / (p_k, A p_k), x += alpha p, r -= alpha A p,
     beta = (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k), p = z_{k+1} + beta p.
@@ -36,6 +45,28 @@ N_PATHS = 9
 def path_of(p):
     """(mu, s) of path p >= 1: transport from x + mu (s = 0) or x - mu (s = 1)."""
     return (p - 1) // 2, (p - 1) % 2
+
+
+def rev(p):
+    """The path opposite to p (p = 0 is its own)."""
+    if p == 0:
+        return 0
+    mu, s = path_of(p)
+    return 1 + 2 * mu + (1 - s)
+
+
+def adjoint_weights(w):
+    """Weights of the adjoint of a layer with weights w [9, C_out, C_in]: [9, C_in, C_out]."""
+    w = np.asarray(w, dtype=np.complex128)
+    return np.stack([np.conj(w[rev(p)]).T for p in range(N_PATHS)])
+
+
+def tie(weights):
+    """Project [W_1, W_2, W_3] onto the self-adjoint form W_3 = W_1^dag, W_2 = W_2^dag."""
+    w1, w2, w3 = (np.asarray(w, dtype=np.complex128) for w in weights)
+    w1t = 0.5 * (w1 + adjoint_weights(w3))
+    w2t = 0.5 * (w2 + adjoint_weights(w2))
+    return [w1t, w2t, adjoint_weights(w1t)]
 
 
 def transport(u_folded, psi, p):

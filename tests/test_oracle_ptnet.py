@@ -78,6 +78,52 @@ def test_network_gauge_covariant_and_linear():
     assert np.linalg.norm(lin) <= 1e-13 * np.linalg.norm(net.apply(r1))
 
 
+def _vdot(a, b):
+    return np.vdot(np.asarray(a).reshape(-1), np.asarray(b).reshape(-1))
+
+
+def test_tied_network_is_hermitian_and_untied_is_not():
+    dims = (4, 4, 6, 4)
+    fat = inputs.asqtad_form_fields(dims, seeds=(21, 22, 23))[0]
+    u = inputs.gaussian_even_source(dims, 24)
+    v = inputs.gaussian_even_source(dims, 25)
+    ws = _random_weights(26)
+    tied = ptnet.tie(ws)
+    net = ptnet.PTNet(fat, dims, tied)
+    lhs, rhs = _vdot(u, net.apply(v)), _vdot(net.apply(u), v)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    raw = ptnet.PTNet(fat, dims, ws)
+    lhs, rhs = _vdot(u, raw.apply(v)), _vdot(raw.apply(u), v)
+    assert abs(lhs - rhs) > 1e-3 * abs(lhs)
+    # a projection: tying tied weights changes nothing
+    again = ptnet.tie(tied)
+    assert all(np.array_equal(a, b) for a, b in zip(again, tied))
+    # rev pairs +mu with -mu
+    assert [ptnet.rev(p) for p in range(9)] == [0, 2, 1, 4, 3, 6, 5, 8, 7]
+
+
+def test_tied_degree_one_polynomial_is_a_plus_b_times_A_minus_m2():
+    """W_1 = (identity; D), W_2 = diag(a, b) on the identity path, tied:
+    M = E^dag (a + b D^dag D) E = a + b (A - m^2) on even sites, by Eq. (3) and D^dag = -D."""
+    dims = (4, 6, 4, 4)
+    m, a, b = 0.2, 0.7, -0.3
+    fat = inputs.gauge_field(dims, 27)
+    w1 = np.zeros((9, 2, 1), dtype=np.complex128)
+    w1[0, 0, 0] = 1.0
+    w1 += _d_weights(2, 1, 1, 0)
+    w2 = np.zeros((9, 2, 2), dtype=np.complex128)
+    w2[0, 0, 0] = a
+    w2[0, 1, 1] = b
+    w3 = ptnet.adjoint_weights(w1)
+    tied = ptnet.tie([w1, w2, w3])
+    assert all(np.allclose(x, y, rtol=0, atol=1e-15) for x, y in zip(tied, [w1, w2, w3]))
+    net = ptnet.PTNet(fat, dims, [w1, w2, w3])
+    r = inputs.gaussian_even_source(dims, 28)
+    ar = oracle.Operator(fat, None, m, dims).apply_A(r)
+    ref = a * r + b * (ar - m * m * r)
+    assert np.linalg.norm(net.apply(r) - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
 def test_loss_definition():
     """The loss is >= 0, zero for a pair whose target is the network's own output, and
     |A (M r - e)|^2 / |A e|^2."""

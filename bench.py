@@ -61,6 +61,10 @@ def parse_args():
     p.add_argument("--mass", type=float, default=MASS)
     p.add_argument("--dims", type=int, nargs=4, default=list(DIMS))
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-sequential", action="store_true",
+                   help="batched workload: skip the one-at-a-time comparison solves")
+    p.add_argument("--main-only", action="store_true",
+                   help="batched workload: only the 16 right-hand sides on the 32^3 x 64 field")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-forms", "--no-f64", dest="no_forms", action="store_true")
     return p.parse_args()
@@ -330,7 +334,8 @@ def run_ours(args):
         variants = [("fp64_plain", binding.STAG_ARITH_F64, binding.STAG_INNER_NONE),
                     ("ff_plain", binding.STAG_ARITH_FF, binding.STAG_INNER_NONE),
                     ("mixed_fp32", binding.STAG_ARITH_FF, binding.STAG_INNER_F32),
-                    ("mixed_fp16", binding.STAG_ARITH_FF, binding.STAG_INNER_F16)]
+                    ("mixed_fp16", binding.STAG_ARITH_FF, binding.STAG_INNER_F16),
+                    ("mixed_bf16", binding.STAG_ARITH_FF, binding.STAG_INNER_BF16)]
         forms = {}
         one_hop = torch.from_numpy(inputs.gauge_field(dims, 1)).to(dev)
         for op_name, f_in, l_in in (("asqtad", fat_d, lng_d), ("one_hop", one_hop, None)):
@@ -431,7 +436,7 @@ def run_batched(args):
         masses.append(MASS)
         bs.append(torch.from_numpy(inputs.gaussian_even_source(BATCH_MAIN, 1000 * rank + k)).to(dev))
     ms_lat = np.linspace(0.01, 0.05, len(BATCH_LATTICES))
-    for j, d in enumerate(BATCH_LATTICES):
+    for j, d in enumerate([] if args.main_only else BATCH_LATTICES):
         fats.append(torch.from_numpy(inputs.gauge_field(d, 500 + j)).to(dev))
         lngs.append(None)
         dims.append(d)
@@ -487,8 +492,11 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
         return time.perf_counter() - t0, its
 
-    seq32, it32 = sequential(binding.STAG_ARITH_FF, binding.STAG_INNER_F32)
-    seq64, it64 = sequential(binding.STAG_ARITH_F64, binding.STAG_INNER_NONE)
+    if args.no_sequential:
+        seq32 = it32 = seq64 = it64 = None
+    else:
+        seq32, it32 = sequential(binding.STAG_ARITH_FF, binding.STAG_INNER_F32)
+        seq64, it64 = sequential(binding.STAG_ARITH_F64, binding.STAG_INNER_NONE)
     rb, bsz, ms = tuning
     vh = accounting.half_sites(BATCH_MAIN)
     bytes_launch = vh * (16 * 72 + BATCH_NRHS * (24 + 24))  # FP32 links once + 16 RHS in and out
@@ -507,8 +515,10 @@ def run_batched(args):
         "vs_baseline": None,
         "dtype": "f32 (FP64-class reliable updates)",
         "data": "synthetic (seeded SU(3) fields exp(0.3 i H), Gaussian sources)",
-        "config": {"workload": f"batched: {BATCH_NRHS} RHS on 32x32x32x64 asqtad-form (m={MASS}) + "
-                               "24 one-hop lattices (8x 8^4, 8x 16^4, 8x 24^3x48; m 0.01..0.05), tol 1e-10",
+        "config": {"workload": f"batched: {BATCH_NRHS} RHS on 32x32x32x64 asqtad-form (m={MASS})"
+                               + ("" if args.main_only else
+                                  " + 24 one-hop lattices (8x 8^4, 8x 16^4, 8x 24^3x48; m 0.01..0.05)")
+                               + ", tol 1e-10",
                    "step": "stag_batch_create + stag_batch_solve + stag_batch_destroy"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
@@ -519,10 +529,10 @@ def run_batched(args):
         "systems": n,
         "iters_main_group": [i["iters"] for i in infos[:BATCH_NRHS]],
         "max_true_rel_residual": max(i["true_rel_residual"] for i in infos),
-        "sequential_mixed_fp32_s": round(seq32, 3),
-        "sequential_fp64_plain_s": round(seq64, 3),
-        "speedup_vs_sequential_mixed_fp32": round(seq32 / value, 3),
-        "speedup_vs_sequential_fp64_plain": round(seq64 / value, 3),
+        "sequential_mixed_fp32_s": seq32 and round(seq32, 3),
+        "sequential_fp64_plain_s": seq64 and round(seq64, 3),
+        "speedup_vs_sequential_mixed_fp32": seq32 and round(seq32 / value, 3),
+        "speedup_vs_sequential_fp64_plain": seq64 and round(seq64 / value, 3),
         "iters_total": {"batched": sum(i["iters"] for i in infos), "sequential_fp32": it32,
                         "sequential_fp64": it64},
     }

@@ -54,7 +54,8 @@ enum {
     STAG_ARITH_F64 = 0, /* native FP64 fused multiply-add */
     STAG_ARITH_F32 = 2, /* FP32 links, vectors and arithmetic (stag_apply_A_prec only) */
     STAG_ARITH_F16 = 3, /* FP16-stored links and vectors, FP32 arithmetic (stag_apply_A_prec only) */
-    STAG_ARITH_BF16 = 4, /* BF16-stored activations, FP32 arithmetic (learned preconditioner only) */
+    STAG_ARITH_BF16 = 4, /* BF16-stored links and vectors (or network activations), FP32
+                            arithmetic (stag_apply_A_prec and the learned preconditioner) */
     STAG_ARITH_FF = 1   /* float-float: each FP64 number held as an unevaluated sum of two
                            FP32 numbers (8 bytes, like FP64), products and sums formed with
                            error-free transformations (Dekker 1971; Knuth TAOCP vol. 2);
@@ -62,10 +63,10 @@ enum {
 };
 
 /* Inner precision of the CG iteration.  NONE: the whole iteration in the
- * FP64-class arithmetic selected by `arith` (plain CG, Fig. 1).  F32 / F16:
+ * FP64-class arithmetic selected by `arith` (plain CG, Fig. 1).  F32 / F16 / BF16:
  * mixed-precision CG (the paper's stated next step, Sec. 5) - the iteration runs
- * on FP32 vectors and links (F32) or on FP16-stored vectors and links with FP32
- * arithmetic (F16), and the iterated residual is replaced by the true residual
+ * on FP32 vectors and links (F32) or on FP16- or BF16-stored vectors and links
+ * with FP32 arithmetic (F16, BF16), and the iterated residual is replaced by the true residual
  * b - A x, computed in the FP64-class arithmetic, whenever it has dropped by
  * reliable_delta since the last replacement or after reliable_interval
  * iterations (reliable updates, Sleijpen & van der Vorst 1996).  x, b and the
@@ -73,7 +74,8 @@ enum {
 enum {
     STAG_INNER_NONE = 0,
     STAG_INNER_F32 = 1,
-    STAG_INNER_F16 = 2
+    STAG_INNER_F16 = 2,
+    STAG_INNER_BF16 = 3
 };
 
 /* Kernel ids for stag_kernel_stats. */
@@ -153,8 +155,8 @@ int stag_apply_A(stag_handle* h, const double* in_even, double* out_even);
 
 /* As stag_apply_A (Sec. 2, Eq. (3)) in a chosen arithmetic: STAG_ARITH_F64
  * (always available), STAG_ARITH_FF (handle created with arith = FF),
- * STAG_ARITH_F32 / STAG_ARITH_F16 (handle created with inner = F32 / F16: the
- * operator the mixed-precision iteration uses; FP16 vectors are scaled to unit
+ * STAG_ARITH_F32 / STAG_ARITH_F16 / STAG_ARITH_BF16 (handle created with inner =
+ * F32 / F16 / BF16: the operator the mixed-precision iteration uses; FP16 vectors are scaled to unit
  * rms entries on the way in and back on the way out).  Returns
  * STAG_ERR_INVALID_ARG when the handle holds no links of that precision. */
 int stag_apply_A_prec(stag_handle* h, int32_t arith, const double* in_even, double* out_even);

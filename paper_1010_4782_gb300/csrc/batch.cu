@@ -151,7 +151,7 @@ void pack_group_field(stag_batch* b, Group& G, const double* src, double2* s64, 
         }
         p = static_cast<const double*>(stage);
     }
-    launch_pack_links(G.g, p, s64, sff, s32, nullptr, b->s);
+    launch_pack_links(G.g, p, s64, sff, s32, nullptr, nullptr, b->s);
     cudaError_t e = cudaGetLastError();
     if (stage) {
         const cudaError_t e2 = cudaStreamSynchronize(b->s);
@@ -173,10 +173,10 @@ MultiLaunch make_launch(stag_batch* b, int parity, int phase, int first_item) {
     return L;
 }
 
-constexpr int kMaxGroupBlocks = 4096;  // blocks per group and launch; partial-sum capacity
+constexpr int kMaxGroupBlocks = 16384;  // blocks per group and launch; partial-sum capacity
 
 // Blocks of a group for a shape: one per tile of sites, at most kMaxGroupBlocks
-// (blocks then stride over the tiles).
+// (blocks then take contiguous runs of tiles).
 int group_blocks(const Group& G, int rb, int bs) {
     const int spb = bs / (G.rpad / rb);
     const int ntiles = (G.g.vh + spb - 1) / spb;

@@ -1,8 +1,8 @@
 // blas_lo.cu - vector steps of the mixed-precision CG with reliable updates.
 //
 // The paper names mixed precision as the next step for its CG (Sec. 5).  The
-// inner iteration is Fig. 1 run on low-precision vectors (FP32, or FP16
-// storage with FP32 arithmetic) with the low-precision Dirac kernels; FP64
+// inner iteration is Fig. 1 run on low-precision vectors (FP32, or FP16 or
+// BF16 storage with FP32 arithmetic) with the low-precision Dirac kernels; FP64
 // holds the solution x, the source b and the replaced residual.  Following the
 // reliable-update scheme (Sleijpen & van der Vorst 1996), the iterated
 // residual is replaced by the true residual b - A x, computed in FP64-class
@@ -27,6 +27,8 @@ __device__ __forceinline__ float2 ldv(const float2* p) { return *p; }
 __device__ __forceinline__ float2 ldv(const __half2* p) { return __half22float2(*p); }
 __device__ __forceinline__ void stv(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void stv(__half2* p, float2 v) { *p = __float22half2_rn(v); }
+__device__ __forceinline__ float2 ldv(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+__device__ __forceinline__ void stv(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
 
 // r64 = b - Ax (Ax in FP64 or float-float); scal->red_out = |r64|^2
 template <class AXT>
@@ -279,5 +281,13 @@ template void launch_lo_update_xr<__half2>(const Geom&, float2*, __half2*, const
                                            CgScalars*, double*, cudaStream_t);
 template void launch_lo_update_d<float2>(const Geom&, const float2*, float2*, CgScalars*, cudaStream_t);
 template void launch_lo_update_d<__half2>(const Geom&, const __half2*, __half2*, CgScalars*, cudaStream_t);
+
+template void launch_to_lo<__nv_bfloat162>(const Geom&, const double2*, __nv_bfloat162*, double, cudaStream_t);
+template void launch_from_lo<__nv_bfloat162>(const Geom&, const __nv_bfloat162*, double2*, double, cudaStream_t);
+template void launch_lo_set_residual<__nv_bfloat162>(const Geom&, const double2*, __nv_bfloat162*, __nv_bfloat162*, float2*, double,
+                                              double, bool, cudaStream_t);
+template void launch_lo_update_xr<__nv_bfloat162>(const Geom&, float2*, __nv_bfloat162*, const __nv_bfloat162*, const __nv_bfloat162*,
+                                           CgScalars*, double*, cudaStream_t);
+template void launch_lo_update_d<__nv_bfloat162>(const Geom&, const __nv_bfloat162*, __nv_bfloat162*, CgScalars*, cudaStream_t);
 
 }  // namespace stag

@@ -132,6 +132,64 @@ void read_state(stag_handle* h) {
     end_call(h);
 }
 
+// Low-precision Dirac kernels and links by storage type.
+void dslash_lo(const Geom& g, int P, const float2* fat, const float2* lng, const float2* in, float2* out, Epilogue e,
+               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s) {
+    launch_dslash_f32(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
+}
+void dslash_lo(const Geom& g, int P, const __half2* fat, const __half2* lng, const __half2* in, __half2* out,
+               Epilogue e, const __half2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s) {
+    launch_dslash_h16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
+}
+void dslash_lo(const Geom& g, int P, const __nv_bfloat162* fat, const __nv_bfloat162* lng, const __nv_bfloat162* in,
+               __nv_bfloat162* out, Epilogue e, const __nv_bfloat162* src, double m2, CgScalars* sc, double* pa,
+               cudaStream_t s) {
+    launch_dslash_b16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
+}
+const float2* lo_fat(const stag_handle* h, const float2*) { return h->fat32; }
+const float2* lo_lng(const stag_handle* h, const float2*) { return h->lng32; }
+const __half2* lo_fat(const stag_handle* h, const __half2*) { return h->fat16; }
+const __half2* lo_lng(const stag_handle* h, const __half2*) { return h->lng16; }
+const __nv_bfloat162* lo_fat(const stag_handle* h, const __nv_bfloat162*) { return h->fatb16; }
+const __nv_bfloat162* lo_lng(const stag_handle* h, const __nv_bfloat162*) { return h->lngb16; }
+
+// One inner iteration of the mixed-precision CG on storage type V.
+template <class V, class Mark>
+void enqueue_lo_iteration(stag_handle* h, Mark mark) {
+    const Geom& g = h->g;
+    V* d = static_cast<V*>(h->lo_d);
+    V* t = static_cast<V*>(h->lo_t);
+    V* ad = static_cast<V*>(h->lo_ad);
+    V* r = static_cast<V*>(h->lo_r);
+    const V* fat = lo_fat(h, d);
+    const V* lng = lo_lng(h, d);
+    mark(0);
+    dslash_lo(g, 1, fat, lng, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
+    mark(1);
+    dslash_lo(g, 0, fat, lng, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s);
+    mark(2);
+    launch_lo_update_xr<V>(g, h->lo_y, r, d, ad, h->scal, h->partials, h->s);
+    mark(3);
+    launch_lo_update_d<V>(g, r, d, h->scal, h->s);
+    mark(4);
+}
+
+// h->ad = A h->x with links and vectors stored as V (FP32 arithmetic); the
+// input is divided by scale before the conversion and the result multiplied by it.
+template <class V>
+void apply_A_lo(stag_handle* h, double m2, double scale) {
+    const Geom& g = h->g;
+    V* in = static_cast<V*>(h->lo_d);
+    V* t = static_cast<V*>(h->lo_t);
+    V* o = static_cast<V*>(h->lo_ad);
+    const V* fat = lo_fat(h, in);
+    const V* lng = lo_lng(h, in);
+    launch_to_lo<V>(g, h->x, in, 1.0 / scale, h->s);
+    dslash_lo(g, 1, fat, lng, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
+    dslash_lo(g, 0, fat, lng, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s);
+    launch_from_lo<V>(g, o, h->ad, scale, h->s);
+}
+
 // One CG iteration (Fig. 1 loop body): four kernels.
 void enqueue_iteration(stag_handle* h, cudaEvent_t* ev, bool count) {
     const Geom& g = h->g;
@@ -140,33 +198,11 @@ void enqueue_iteration(stag_handle* h, cudaEvent_t* ev, bool count) {
         if (ev) cudaEventRecord(ev[k], h->s);
     };
     if (h->opt.inner == STAG_INNER_F32) {
-        float2* d = static_cast<float2*>(h->lo_d);
-        float2* t = static_cast<float2*>(h->lo_t);
-        float2* ad = static_cast<float2*>(h->lo_ad);
-        float2* r = static_cast<float2*>(h->lo_r);
-        mark(0);
-        launch_dslash_f32(g, 1, h->fat32, h->lng32, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
-        mark(1);
-        launch_dslash_f32(g, 0, h->fat32, h->lng32, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s);
-        mark(2);
-        launch_lo_update_xr<float2>(g, h->lo_y, r, d, ad, h->scal, h->partials, h->s);
-        mark(3);
-        launch_lo_update_d<float2>(g, r, d, h->scal, h->s);
-        mark(4);
+        enqueue_lo_iteration<float2>(h, mark);
     } else if (h->opt.inner == STAG_INNER_F16) {
-        __half2* d = static_cast<__half2*>(h->lo_d);
-        __half2* t = static_cast<__half2*>(h->lo_t);
-        __half2* ad = static_cast<__half2*>(h->lo_ad);
-        __half2* r = static_cast<__half2*>(h->lo_r);
-        mark(0);
-        launch_dslash_h16(g, 1, h->fat16, h->lng16, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
-        mark(1);
-        launch_dslash_h16(g, 0, h->fat16, h->lng16, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s);
-        mark(2);
-        launch_lo_update_xr<__half2>(g, h->lo_y, r, d, ad, h->scal, h->partials, h->s);
-        mark(3);
-        launch_lo_update_d<__half2>(g, r, d, h->scal, h->s);
-        mark(4);
+        enqueue_lo_iteration<__half2>(h, mark);
+    } else if (h->opt.inner == STAG_INNER_BF16) {
+        enqueue_lo_iteration<__nv_bfloat162>(h, mark);
     } else if (use_ff(h)) {
         float4* d = static_cast<float4*>(h->d);
         float4* t = static_cast<float4*>(h->t);
@@ -281,6 +317,8 @@ void destroy_handle(stag_handle* h) {
     dev_free(h->lng32);
     dev_free(h->fat16);
     dev_free(h->lng16);
+    dev_free(h->fatb16);
+    dev_free(h->lngb16);
     dev_free(h->lo_d);
     dev_free(h->lo_t);
     dev_free(h->lo_ad);
@@ -297,7 +335,7 @@ void destroy_handle(stag_handle* h) {
 }
 
 void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* soaff, float2* soa32,
-                __half2* soa16) {
+                __half2* soa16, __nv_bfloat162* soab16) {
     const size_t aos_bytes = (size_t)2 * h->g.vh * 4 * 9 * sizeof(double2);
     const double* src = links_in;
     void* stage = nullptr;
@@ -310,7 +348,7 @@ void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* 
         }
         src = static_cast<const double*>(stage);
     }
-    launch_pack_links(h->g, src, soa64, soaff, soa32, soa16, h->s);
+    launch_pack_links(h->g, src, soa64, soaff, soa32, soa16, soab16, h->s);
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (stage) {
@@ -350,7 +388,7 @@ bool apply_A_fp64class(stag_handle* h, const double2* x) {
 // with native FP64), and otherwise replaces the inner residual by it - scaled
 // to unit rms entries for FP16 storage - keeps the search direction (with beta
 // from the replaced residual), and runs the inner iteration until the next
-// replacement is due.
+// replacement is due.  BF16 shares FP32's exponent range and needs no scaling.
 void solve_mixed(stag_handle* h, double bnorm2, double tol, long long max_it, stag_solve_info& inf,
                  int& status, double& rel) {
     const Geom& g = h->g;
@@ -402,6 +440,10 @@ void solve_mixed(stag_handle* h, double bnorm2, double tol, long long max_it, st
         if (f16)
             launch_lo_set_residual<__half2>(g, h->r, static_cast<__half2*>(h->lo_r), static_cast<__half2*>(h->lo_d),
                                             h->lo_y, 1.0 / sigma, beta, first, h->s);
+        else if (h->opt.inner == STAG_INNER_BF16)
+            launch_lo_set_residual<__nv_bfloat162>(g, h->r, static_cast<__nv_bfloat162*>(h->lo_r),
+                                                   static_cast<__nv_bfloat162*>(h->lo_d), h->lo_y, 1.0 / sigma, beta,
+                                                   first, h->s);
         else
             launch_lo_set_residual<float2>(g, h->r, static_cast<float2*>(h->lo_r), static_cast<float2*>(h->lo_d),
                                            h->lo_y, 1.0 / sigma, beta, first, h->s);
@@ -578,7 +620,8 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         if (o.check_interval < 1 || o.check_interval > 4096)
             fail(nullptr, STAG_ERR_INVALID_ARG, "check_interval must be in [1, 4096]");
         if (o.max_restarts < 0) fail(nullptr, STAG_ERR_INVALID_ARG, "max_restarts must be >= 0");
-        if (o.inner != STAG_INNER_NONE && o.inner != STAG_INNER_F32 && o.inner != STAG_INNER_F16)
+        if (o.inner != STAG_INNER_NONE && o.inner != STAG_INNER_F32 && o.inner != STAG_INNER_F16 &&
+            o.inner != STAG_INNER_BF16)
             fail(nullptr, STAG_ERR_INVALID_ARG, "unknown inner precision");
         if (o.inner != STAG_INNER_NONE &&
             (o.reliable_interval < 1 || !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0)))
@@ -627,6 +670,10 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         } else if (h->opt.inner == STAG_INNER_F16) {
             h->fat16 = dev_alloc<__half2>(h, lo_links * sizeof(__half2), "allocate FP16 links");
             if (h->naik) h->lng16 = dev_alloc<__half2>(h, lo_links * sizeof(__half2), "allocate FP16 Naik links");
+        } else if (h->opt.inner == STAG_INNER_BF16) {
+            h->fatb16 = dev_alloc<__nv_bfloat162>(h, lo_links * sizeof(__nv_bfloat162), "allocate BF16 links");
+            if (h->naik)
+                h->lngb16 = dev_alloc<__nv_bfloat162>(h, lo_links * sizeof(__nv_bfloat162), "allocate BF16 Naik links");
         }
         if (h->opt.inner != STAG_INNER_NONE) {
             const size_t lo_vb = (size_t)3 * g.vs * (h->opt.inner == STAG_INNER_F32 ? sizeof(float2) : sizeof(__half2));
@@ -644,8 +691,8 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
                    "allocate pinned CG state");
         std::memset(h->scal_host, 0, sizeof(CgScalars));
 
-        pack_field(h, fat, h->fat64, h->fatff, h->fat32, h->fat16);
-        if (h->naik) pack_field(h, naik_long, h->lng64, h->lngff, h->lng32, h->lng16);
+        pack_field(h, fat, h->fat64, h->fatff, h->fat32, h->fat16, h->fatb16);
+        if (h->naik) pack_field(h, naik_long, h->lng64, h->lngff, h->lng32, h->lng16, h->lngb16);
         end_call(h);
         *out = h;
         return STAG_OK;
@@ -772,7 +819,8 @@ int stag_apply_A_prec(stag_handle* h, int32_t arith, const double* in_even, doub
         if (!in_even || !out_even) fail(h, STAG_ERR_INVALID_ARG, "NULL vector");
         if (in_even == out_even) fail(h, STAG_ERR_INVALID_ARG, "in and out must not overlap");
         const bool ok = arith == STAG_ARITH_F64 || (arith == STAG_ARITH_FF && h->fatff) ||
-                        (arith == STAG_ARITH_F32 && h->fat32) || (arith == STAG_ARITH_F16 && h->fat16);
+                        (arith == STAG_ARITH_F32 && h->fat32) || (arith == STAG_ARITH_F16 && h->fat16) ||
+                        (arith == STAG_ARITH_BF16 && h->fatb16);
         if (!ok) fail(h, STAG_ERR_INVALID_ARG, "the handle holds no links in the requested arithmetic");
         if (arith == STAG_ARITH_F64 || arith == STAG_ARITH_FF) {
             const int saved = h->opt.arith;
@@ -793,23 +841,12 @@ int stag_apply_A_prec(stag_handle* h, int32_t arith, const double* in_even, doub
             scale = n2 > 0.0 ? std::sqrt(n2 / (6.0 * g.vh)) : 1.0;
         }
         const double m2 = h->mass * h->mass;
-        if (arith == STAG_ARITH_F32) {
-            float2* in = static_cast<float2*>(h->lo_d);
-            float2* t = static_cast<float2*>(h->lo_t);
-            float2* o = static_cast<float2*>(h->lo_ad);
-            launch_to_lo<float2>(g, h->x, in, 1.0, h->s);
-            launch_dslash_f32(g, 1, h->fat32, h->lng32, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
-            launch_dslash_f32(g, 0, h->fat32, h->lng32, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s);
-            launch_from_lo<float2>(g, o, h->ad, 1.0, h->s);
-        } else {
-            __half2* in = static_cast<__half2*>(h->lo_d);
-            __half2* t = static_cast<__half2*>(h->lo_t);
-            __half2* o = static_cast<__half2*>(h->lo_ad);
-            launch_to_lo<__half2>(g, h->x, in, 1.0 / scale, h->s);
-            launch_dslash_h16(g, 1, h->fat16, h->lng16, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
-            launch_dslash_h16(g, 0, h->fat16, h->lng16, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s);
-            launch_from_lo<__half2>(g, o, h->ad, scale, h->s);
-        }
+        if (arith == STAG_ARITH_F32)
+            apply_A_lo<float2>(h, m2, 1.0);
+        else if (arith == STAG_ARITH_F16)
+            apply_A_lo<__half2>(h, m2, scale);
+        else
+            apply_A_lo<__nv_bfloat162>(h, m2, 1.0);
         double* dst = out_dev ? out_even : h->io_b;
         launch_unpack_vec(g, h->ad, dst, h->s);
         h->launches += 6;

@@ -153,6 +153,26 @@ struct ArithH16 {
     }
 };
 
+// BF16 storage (links and vectors as bfloat162 = (re, im)), FP32 arithmetic:
+// FP32's exponent range with an 8-bit significand.
+struct ArithB16 {
+    using T = __nv_bfloat162;
+    using C = float2;
+    static __device__ __forceinline__ C ld(const T* p) { return __bfloat1622float2(__ldg(p)); }
+    using Acc = ArithF32::Acc;
+    static __device__ __forceinline__ void zero(Acc& a) { ArithF32::zero(a); }
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        ArithF32::row_fwd(a, r, u0, u1, u2, v0, v1, v2);
+    }
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        ArithF32::row_bwd(a, r, u0, u1, u2, v0, v1, v2);
+    }
+    static __device__ __forceinline__ T store_val(const Acc& a, int r) { return __float22bfloat162_rn(a.c[r]); }
+    static __device__ __forceinline__ T epilogue(Acc& a, int r, C s, double m2, float2 m2f, double& dot) {
+        return __float22bfloat162_rn(ArithF32::epilogue(a, r, s, m2, m2f, dot));
+    }
+};
+
 template <class A>
 struct DslashParams {
     Geom g;
@@ -322,6 +342,14 @@ void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const 
                        const __half2* in, __half2* out, Epilogue epi, const __half2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s) {
     DslashParams<ArithH16> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials, 0,
+                             g.vh};
+    launch_any(p, lng != nullptr, epi, s);
+}
+
+void launch_dslash_b16(const Geom& g, int out_parity, const __nv_bfloat162* fat, const __nv_bfloat162* lng,
+                       const __nv_bfloat162* in, __nv_bfloat162* out, Epilogue epi, const __nv_bfloat162* src,
+                       double m2, CgScalars* scal, double* partials, cudaStream_t s) {
+    DslashParams<ArithB16> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials, 0,
                              g.vh};
     launch_any(p, lng != nullptr, epi, s);
 }

@@ -1,6 +1,7 @@
 // handle.h - the library's handle (internal; the ABI sees an opaque pointer).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -43,7 +44,9 @@ struct stag_handle {
     float2* lng32 = nullptr;
     __half2* fat16 = nullptr;
     __half2* lng16 = nullptr;
-    void* lo_d = nullptr;    // [3][vs] float2 (F32) or __half2 (F16)
+    __nv_bfloat162* fatb16 = nullptr;
+    __nv_bfloat162* lngb16 = nullptr;
+    void* lo_d = nullptr;    // [3][vs] float2 (F32), __half2 (F16) or __nv_bfloat162 (BF16)
     void* lo_t = nullptr;
     void* lo_ad = nullptr;
     void* lo_r = nullptr;

@@ -8,7 +8,7 @@
 // once for all of them - the multi-RHS form of Sec. 2's Dirac operation).
 // Work items (group, block of the group, blocks of the group) are listed in a
 // device table; blockIdx.x selects one, so a single launch covers lattices of
-// any size mix.
+// any size mix.  A group's blocks take contiguous runs of site tiles.
 //
 // Per right-hand side the CG scalars (alpha, beta, delta, loop state) live in
 // their own CgScalars; reductions are per right-hand side: per-block partials,
@@ -24,6 +24,13 @@ __device__ __forceinline__ bool group_all_done(const MultiGroup& G, const CgScal
     for (int r = 0; r < G.nrhs; ++r)
         if (!scal[G.rhs0 + r].done) return false;
     return true;
+}
+
+// Block blk of nblk takes the contiguous tiles [tile_end(blk - 1), tile_end(blk)),
+// so that the blocks resident at one time work on nearby sites and share
+// their neighbours' vectors in L2.
+__device__ __forceinline__ int tile_end(int blk, int ntiles, int nblk) {
+    return (int)((long long)(blk + 1) * ntiles / nblk);
 }
 
 // Thread layout: right-hand sides are the fastest index.  TPS = rpad / RB
@@ -95,8 +102,16 @@ __device__ __forceinline__ bool multi_reduce(double (&v)[RB], const MultiGroup& 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int r = w; r < G.rpad; r += BS / 32) {
         const double* p = partials + (size_t)(G.prhs0 + r) * G.max_blocks;
-        double s = 0.0;
-        for (int b = lane; b < nblk; b += 32) s += __ldcg(p + b);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = lane;
+        for (; b + 96 < nblk; b += 128) {
+            s0 += __ldcg(p + b);
+            s1 += __ldcg(p + b + 32);
+            s2 += __ldcg(p + b + 64);
+            s3 += __ldcg(p + b + 96);
+        }
+        for (; b < nblk; b += 32) s0 += __ldcg(p + b);
+        double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) tot[r] = s;
@@ -116,10 +131,34 @@ __device__ __forceinline__ int nbr_index(const Geom& g, int x, int y, int z, int
     return site_index(x, y, z, t, g);
 }
 
+// 256-bit accesses (sm_100 and later) of four consecutive float2; p is 32-byte aligned.
+__device__ __forceinline__ void ld256_nc(const float2* p, float2& a, float2& b, float2& c, float2& d) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y), "=f"(c.x), "=f"(c.y), "=f"(d.x), "=f"(d.y)
+        : "l"(p));
+}
+__device__ __forceinline__ void ld256(const float2* p, float2& a, float2& b, float2& c, float2& d) {
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y), "=f"(c.x), "=f"(c.y), "=f"(d.x), "=f"(d.y)
+                 : "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ void st256(float2* p, float2 a, float2 b, float2 c, float2 d) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.x), "f"(a.y),
+                 "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
+                 : "memory");
+}
+
+// A thread's RB consecutive right-hand sides of one colour.  For RB >= 4 the
+// offset is a multiple of 32 bytes (rpad >= 8 is a power of two and the lane
+// offset is a multiple of RB), so the accesses are 256 bits wide.
 template <int RB>
 __device__ __forceinline__ void load_rb(float2 (&v)[RB], const float2* __restrict__ p) {
     if constexpr (RB == 1) {
         v[0] = __ldg(p);
+    } else if constexpr (RB % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < RB; j += 4) ld256_nc(p + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
     } else {
 #pragma unroll
         for (int j = 0; j < RB; j += 2) {
@@ -134,6 +173,9 @@ template <int RB>
 __device__ __forceinline__ void load_rb_rw(float2 (&v)[RB], const float2* p) {
     if constexpr (RB == 1) {
         v[0] = *p;
+    } else if constexpr (RB % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < RB; j += 4) ld256(p + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
     } else {
 #pragma unroll
         for (int j = 0; j < RB; j += 2) {
@@ -148,6 +190,9 @@ template <int RB>
 __device__ __forceinline__ void store_rb(float2* p, const float2 (&v)[RB]) {
     if constexpr (RB == 1) {
         *p = v[0];
+    } else if constexpr (RB % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < RB; j += 4) st256(p + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
     } else {
 #pragma unroll
         for (int j = 0; j < RB; j += 2)
@@ -198,7 +243,8 @@ __global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
     float dotf[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) dotf[j] = 0.f;
-    for (int tile = blk; tile < ntiles; tile += nblk) {
+    const int tile1 = tile_end(blk, ntiles, nblk);
+    for (int tile = tile_end(blk - 1, ntiles, nblk); tile < tile1; ++tile) {
         const int i = tile * l.spb + l.site_local;
         if (i >= g.vh) continue;
         float2 acc[3][RB];
@@ -286,7 +332,8 @@ __global__ void __launch_bounds__(BS) multi_update_xr_kernel(const MultiLaunch L
     float acc[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) acc[j] = 0.f;
-    for (int tile = blk; tile < ntiles; tile += nblk) {
+    const int tile1 = tile_end(blk, ntiles, nblk);
+    for (int tile = tile_end(blk - 1, ntiles, nblk); tile < tile1; ++tile) {
         const int i = tile * l.spb + l.site_local;
         if (i >= g.vh) continue;
 #pragma unroll
@@ -358,7 +405,8 @@ __global__ void __launch_bounds__(BS) multi_update_d_kernel(const MultiLaunch L)
         beta[j] = live[j] ? L.scal[G.rhs0 + r].beta_ff.x : 0.f;
     }
     const int ntiles = (g.vh + l.spb - 1) / l.spb;
-    for (int tile = blk; tile < ntiles; tile += nblk) {
+    const int tile1 = tile_end(blk, ntiles, nblk);
+    for (int tile = tile_end(blk - 1, ntiles, nblk); tile < tile1; ++tile) {
         const int i = tile * l.spb + l.site_local;
         if (i >= g.vh) continue;
 #pragma unroll

@@ -1,6 +1,6 @@
 // pack.cu - layout kernels: eta folding of the links (Sec. 2, after Eq. (5)),
 // AoS -> structure-of-arrays transposition for coalesced access (Sec. 3.1),
-// the low-precision link copies of the mixed-precision solver, and the
+// the low-precision link copies (FP32, FP16, BF16) of the mixed-precision solver, and the
 // ABI <-> internal vector conversions.
 #include "stag_kernels.h"
 #include "ff.cuh"
@@ -14,7 +14,8 @@ __global__ void __launch_bounds__(kBlock) pack_links_kernel(Geom g, const double
                                                             double2* __restrict__ soa64,
                                                             float4* __restrict__ soaff,
                                                             float2* __restrict__ soa32,
-                                                            __half2* __restrict__ soa16) {
+                                                            __half2* __restrict__ soa16,
+                                                            __nv_bfloat162* __restrict__ soab16) {
     const long long V = 2LL * g.vh;
     const long long idx = (long long)blockIdx.x * kBlock + threadIdx.x;
     if (idx >= 4 * V) return;
@@ -45,15 +46,16 @@ __global__ void __launch_bounds__(kBlock) pack_links_kernel(Geom g, const double
         if (soaff) soaff[base + k * vs] = ff_from_complex(u);
         if (soa32) soa32[base + k * vs] = make_float2((float)u.x, (float)u.y);
         if (soa16) soa16[base + k * vs] = __floats2half2_rn((float)u.x, (float)u.y);
+        if (soab16) soab16[base + k * vs] = __floats2bfloat162_rn((float)u.x, (float)u.y);
     }
 }
 
 void launch_pack_links(const Geom& g, const double* aos, double2* soa64, float4* soaff,
-                       float2* soa32, __half2* soa16, cudaStream_t s) {
+                       float2* soa32, __half2* soa16, __nv_bfloat162* soab16, cudaStream_t s) {
     const long long n = 8LL * g.vh;
     const int blocks = (int)((n + kBlock - 1) / kBlock);
     pack_links_kernel<<<blocks, kBlock, 0, s>>>(g, reinterpret_cast<const double2*>(aos), soa64,
-                                                soaff, soa32, soa16);
+                                                soaff, soa32, soa16, soab16);
 }
 
 __global__ void __launch_bounds__(kBlock) pack_vec_kernel(Geom g, const double2* __restrict__ aos,

@@ -1,6 +1,7 @@
 // stag_kernels.h - host-side launchers of the library's kernels (internal).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -24,9 +25,9 @@ struct LinkSet {
 
 // ---- packing (pack.cu)
 // AoS links [Lt][Lz][Ly][Lx][4][3][3] complex128 (device) -> SoA with eta folded,
-// in FP64 and, where the pointer is not null, float-float, FP32 and FP16.
+// in FP64 and, where the pointer is not null, float-float, FP32, FP16 and BF16.
 void launch_pack_links(const Geom& g, const double* aos, double2* soa64, float4* soaff,
-                       float2* soa32, __half2* soa16, cudaStream_t s);
+                       float2* soa32, __half2* soa16, __nv_bfloat162* soab16, cudaStream_t s);
 // ABI vector [vh][3] complex128 (device) <-> F64 SoA [3][vs]
 void launch_pack_vec(const Geom& g, const double* aos, double2* soa, cudaStream_t s);
 void launch_unpack_vec(const Geom& g, const double2* soa, double* aos, cudaStream_t s);
@@ -49,6 +50,9 @@ void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const f
 void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng,
                        const __half2* in, __half2* out, Epilogue epi, const __half2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s);
+void launch_dslash_b16(const Geom& g, int out_parity, const __nv_bfloat162* fat, const __nv_bfloat162* lng,
+                       const __nv_bfloat162* in, __nv_bfloat162* out, Epilogue epi, const __nv_bfloat162* src,
+                       double m2, CgScalars* scal, double* partials, cudaStream_t s);
 
 // ---- CG vector kernels and reductions (blas.cu)
 // start of one run of Fig. 1 (iter = 0, done = 0, threshold, m^2, max_iter)

@@ -8,6 +8,8 @@ Operator tolerances (relative, norm-wise / element-wise against max |ref|):
   * FP16-stored links and vectors (FP32 arithmetic): 2e-3 / 2e-2.  Storage
     rounding is 2^-11 = 4.9e-4 relative per entry (links, input, intermediate,
     output), averaged over the sums.
+  * BF16-stored links and vectors (FP32 arithmetic): 1.6e-2 / 1.6e-1, the FP16
+    bounds scaled by the ratio of unit roundoffs 2^-8 / 2^-11 = 8.
 Solves must meet the same bars as the FP64 solver: true residual <= 1e-10 and
 |x - x_oracle| / |x_oracle| <= 1e-8 against an oracle solution taken to 1e-13.
 """
@@ -20,8 +22,10 @@ from paper_1010_4782_gb300 import binding, inputs
 
 pytestmark = pytest.mark.gpu
 
-OP_TOL = {binding.STAG_ARITH_F32: (2e-6, 1e-5), binding.STAG_ARITH_F16: (2e-3, 2e-2)}
-INNER_OF = {binding.STAG_ARITH_F32: binding.STAG_INNER_F32, binding.STAG_ARITH_F16: binding.STAG_INNER_F16}
+OP_TOL = {binding.STAG_ARITH_F32: (2e-6, 1e-5), binding.STAG_ARITH_F16: (2e-3, 2e-2),
+          binding.STAG_ARITH_BF16: (1.6e-2, 1.6e-1)}
+INNER_OF = {binding.STAG_ARITH_F32: binding.STAG_INNER_F32, binding.STAG_ARITH_F16: binding.STAG_INNER_F16,
+            binding.STAG_ARITH_BF16: binding.STAG_INNER_BF16}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -53,7 +57,7 @@ def _handle(fat, lng, dims, mass, arith=binding.STAG_ARITH_FF, inner=binding.STA
     return binding.Handle(_dev(fat), dims, mass, naik_long=None if lng is None else _dev(lng), options=opt)
 
 
-@pytest.mark.parametrize("prec", [binding.STAG_ARITH_F32, binding.STAG_ARITH_F16])
+@pytest.mark.parametrize("prec", [binding.STAG_ARITH_F32, binding.STAG_ARITH_F16, binding.STAG_ARITH_BF16])
 @pytest.mark.parametrize("naik", [False, True])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 12), (8, 8, 8, 16)])
 def test_low_precision_operator(dims, naik, prec):
@@ -100,7 +104,7 @@ CASES = [((4, 4, 4, 4), False, 0.1, 1),     # the config-1 system
 
 
 @pytest.mark.parametrize("arith", [binding.STAG_ARITH_FF, binding.STAG_ARITH_F64])
-@pytest.mark.parametrize("inner", [binding.STAG_INNER_F32, binding.STAG_INNER_F16])
+@pytest.mark.parametrize("inner", [binding.STAG_INNER_F32, binding.STAG_INNER_F16, binding.STAG_INNER_BF16])
 @pytest.mark.parametrize("case", CASES)
 def test_mixed_solve(case, inner, arith):
     dims, naik, mass, seed = case

@@ -263,7 +263,9 @@ typedef struct stag_ptnet stag_ptnet;
  * STAG_ARITH_F32.  The weights start as the least-squares degree-1 polynomial
  * preconditioner alpha + beta A_fat (alpha = 4/L, beta = -10/(3 L^2), L = 1.25
  * times the Rayleigh quotient after 100 power iterations; A_fat: m^2 - D^2 with
- * the one-hop links the transports use) plus small noise seeded by `seed`. */
+ * the one-hop links the transports use) written in the self-adjoint form
+ * M = L1^dag L2 L1 (L1 = (r; D r), L2 = diag(alpha + beta m^2, beta)), plus small
+ * noise seeded by `seed`, tied like the weights after a training step. */
 int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint64_t seed);
 int64_t stag_ptnet_num_weights(const stag_ptnet* n);
 int stag_ptnet_set_weights(stag_ptnet* n, const double* w, int64_t count);
@@ -288,7 +290,11 @@ int stag_ptnet_num_pairs(const stag_ptnet* n);
 
 /* Adam (beta 0.9, 0.999) on the stored pairs: `epochs` passes in seeded random
  * order, mini-batches of `batch` pairs, learning rate lr; epoch_loss (nullable):
- * mean pair loss of each epoch. */
+ * mean pair loss of each epoch.  After every step the weights are projected onto
+ * the self-adjoint tie W3[p][0][i] = conj(W1[rev p][i][0]), W2[p][o][i] =
+ * conj(W2[rev p][i][o]) (rev: the opposite path), so that M is Hermitian, as the
+ * short recurrence of flexible CG assumes; weights set with
+ * stag_ptnet_set_weights are used as given until the first step. */
 int stag_ptnet_train(stag_ptnet* n, int32_t epochs, int32_t batch, double lr, uint64_t seed, double* epoch_loss);
 
 /* Mean loss over the stored pairs. */

@@ -18,7 +18,8 @@
 // polynomial-preconditioning objective: it weights the modes of A by lambda^2,
 // so the network fits lambda M(lambda) ~ 1 on the bulk of the spectrum), A
 // applied with the FP32 Dirac kernels; Adam on the real and imaginary parts of
-// the weights.  Activations are stored
+// the weights, each step followed by the self-adjoint tie W3 = W1^dag,
+// W2 = W2^dag (M Hermitian, as flexible CG's short recurrence assumes).  Activations are stored
 // as BF16 (or FP32, for gradient checks) and every sum runs in FP32.
 //
 // Gradients (Wirtinger, G = dL/d conj(W)):
@@ -119,28 +120,42 @@ __device__ __forceinline__ void pt_apply(const float2 (&U)[9], int d, const floa
     }
 }
 
+// Which sites and paths a layer launch covers.  The network's input is zero on
+// odd sites and only its output's even sites are read, so:
+//   SITES_ALL  - every site, every path;
+//   EVEN_INPUT - the input is zero on odd sites: an even output site takes only
+//                the identity path, an odd one only the transports;
+//   EVEN_OUTPUT- only even output sites are computed (odd ones are left as they are).
+enum LayerMode { SITES_ALL = 0, EVEN_INPUT = 1, EVEN_OUTPUT = 2 };
+
 // One layer (ADJ = false) or its adjoint (ADJ = true; CIN / COUT are then the
 // forward layer's output / input channel counts, w its forward weights).
-template <int CIN, int COUT, class TI, class TO, bool ADJ>
-__global__ void __launch_bounds__(256) pt_layer_kernel(Geom g, const float2* __restrict__ links,
-                                                       const float2* __restrict__ w, const TI* __restrict__ in,
-                                                       TO* __restrict__ out) {
+// Blocks alternate between the parities over the same run of 256 site indices
+// (block 2c: even sites, 2c + 1: odd sites of run c; EVEN_OUTPUT: run b, even),
+// so that a link or an activation read by a site of one parity is read again,
+// by its neighbour of the other parity, while it is still in L2.  The 8 -> 8
+// layer is held to 128 registers (two blocks per SM), the others to 85 (three).
+template <int CIN, int COUT, class TI, class TO, bool ADJ, int MODE = SITES_ALL>
+__global__ void __launch_bounds__(256, CIN * COUT >= 64 ? 2 : 3)
+    pt_layer_kernel(Geom g, const float2* __restrict__ links, const float2* __restrict__ w,
+                    const TI* __restrict__ in, TO* __restrict__ out) {
     __shared__ float2 sw[kPaths * CIN * COUT];
     for (int k = threadIdx.x; k < kPaths * CIN * COUT; k += blockDim.x) sw[k] = w[k];
     __syncthreads();
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= 2 * g.vh) return;
-    const int P = n >= g.vh ? 1 : 0;
-    const int i = n - P * g.vh;
+    const int P = MODE == EVEN_OUTPUT ? 0 : (int)(blockIdx.x & 1);
+    const int i = (MODE == EVEN_OUTPUT ? (int)blockIdx.x : (int)(blockIdx.x >> 1)) * 256 + threadIdx.x;
+    if (i >= g.vh) return;
     const size_t vs = (size_t)g.vs;
     int x, y, z, t;
     site_coords(i, P, g, x, y, z, t);
+    const int p0 = (MODE == EVEN_INPUT && P == 1) ? 1 : 0;
+    const int p1 = (MODE == EVEN_INPUT && P == 0) ? 1 : kPaths;
     float2 acc[COUT][3];
 #pragma unroll
     for (int o = 0; o < COUT; ++o)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[o][c] = make_float2(0.f, 0.f);
-    for (int p = 0; p < kPaths; ++p) {
+    for (int p = p0; p < p1; ++p) {
         int Pn = P, nb = i, d = 0;
         float2 U[9];
         if (p > 0) {
@@ -184,7 +199,9 @@ __global__ void __launch_bounds__(256) pt_layer_kernel(Geom g, const float2* __r
 
 // partials[blk][p][o][i] = sum over the block's sites of
 // sum_c conj((T_p psi_i)(x)_c) g_o(x)_c, o in [o0, o0 + OC), path p = blockIdx.y.
-template <int CIN, int OC, class T>
+// MODE EVEN_INPUT: psi is zero on odd sites (only even sites for p = 0, odd
+// sites for p > 0 contribute); EVEN_OUTPUT: g is zero on odd sites.
+template <int CIN, int OC, class T, int MODE = SITES_ALL>
 __global__ void __launch_bounds__(256) pt_wgrad_kernel(Geom g, const float2* __restrict__ links,
                                                        const T* __restrict__ psi, const T* __restrict__ gout,
                                                        int cout, float2* __restrict__ partials) {
@@ -196,7 +213,9 @@ __global__ void __launch_bounds__(256) pt_wgrad_kernel(Geom g, const float2* __r
     for (int oo = 0; oo < OC; ++oo)
 #pragma unroll
         for (int ci = 0; ci < CIN; ++ci) acc[oo][ci] = make_float2(0.f, 0.f);
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < 2 * g.vh; n += gridDim.x * blockDim.x) {
+    const int n0 = (MODE == EVEN_INPUT && p > 0) ? g.vh : 0;
+    const int n1 = ((MODE == EVEN_INPUT && p == 0) || MODE == EVEN_OUTPUT) ? g.vh : 2 * g.vh;
+    for (int n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += gridDim.x * blockDim.x) {
         const int P = n >= g.vh ? 1 : 0;
         const int i = n - P * g.vh;
         int x, y, z, t;
@@ -434,6 +453,37 @@ __global__ void pt_adam_kernel(float* w, const float* grad, float* m, float* v, 
     w[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
 }
 
+// The path opposite to p (T_{+mu}^dag = T_{-mu}); p = 0 is its own.
+__host__ __device__ __forceinline__ int rev_path(int p) { return p == 0 ? 0 : (((p - 1) ^ 1) + 1); }
+
+// Self-adjoint tie: projects the weights onto W3[p][0][i] = conj(W1[rev p][i][0])
+// and W2[p][o][i] = conj(W2[rev p][i][o]) (each weight and its partner's conjugate
+// replaced by their mean), which makes M = E^dag L3 L2 L1 E Hermitian.  One
+// block; every pair is handled by one thread.
+__global__ void pt_tie_kernel(float2* w) {
+    constexpr int H = kHidden;
+    float2* w1 = w;                                   // [9][H][1]
+    float2* w2 = w + kPaths * H;                      // [9][H][H]
+    float2* w3 = w + kPaths * H + kPaths * H * H;     // [9][1][H]
+    for (int k = threadIdx.x; k < kPaths * H; k += blockDim.x) {
+        const int p = k / H, o = k % H;
+        const int k3 = rev_path(p) * H + o;
+        const float2 a = w1[k], b = w3[k3];
+        const float2 m = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        w1[k] = m;
+        w3[k3] = make_float2(m.x, -m.y);
+    }
+    for (int k = threadIdx.x; k < kPaths * H * H; k += blockDim.x) {
+        const int p = k / (H * H), o = (k / H) % H, i = k % H;
+        const int kp = (rev_path(p) * H + i) * H + o;
+        if (kp < k) continue;
+        const float2 a = w2[k], b = w2[kp];
+        const float2 m = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        w2[k] = m;
+        w2[kp] = make_float2(m.x, -m.y);
+    }
+}
+
 // v = a fixed pseudo-random vector (start of the power iteration)
 __global__ void pt_fill_kernel(Geom g, float2* v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -618,7 +668,8 @@ void* palloc(stag_ptnet* n, size_t bytes, const char* what) {
 cudaStream_t S(stag_ptnet* n) { return n->h->s; }
 size_t field_bytes(const stag_ptnet* n, int ch) { return (size_t)ch * 3 * 2 * n->g.vs * sizeof(float2); }
 size_t slot_bytes(const stag_ptnet* n) { return (size_t)3 * n->g.vs * n->elem; }
-int site_blocks(const Geom& g) { return blocks_for(2 * g.vh); }
+// blocks of a pt_layer_kernel launch over both parities (256 sites per block)
+int site_blocks(const Geom& g) { return 2 * blocks_for(g.vh, 256); }
 
 template <class T>
 void layer_fwd(stag_ptnet* n, int l, const T* in, T* out) {
@@ -626,11 +677,12 @@ void layer_fwd(stag_ptnet* n, int l, const T* in, T* out) {
     const float2* w = n->w + layer_offset(l);
     const int nb = site_blocks(g);
     if (l == 0)
-        pt_layer_kernel<1, kHidden, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
+        pt_layer_kernel<1, kHidden, T, T, false, EVEN_INPUT><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
     else if (l == 1)
         pt_layer_kernel<kHidden, kHidden, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
     else
-        pt_layer_kernel<kHidden, 1, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
+        pt_layer_kernel<kHidden, 1, T, T, false, EVEN_OUTPUT><<<blocks_for(g.vh), 256, 0, S(n)>>>(g, n->links, w, in,
+                                                                                                  out);
 }
 
 // gradient of layer l's input from the gradient of its output
@@ -640,7 +692,7 @@ void layer_adj(stag_ptnet* n, int l, const T* gout, T* gin) {
     const float2* w = n->w + layer_offset(l);
     const int nb = site_blocks(g);
     if (l == 2)
-        pt_layer_kernel<1, kHidden, T, T, true><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin);
+        pt_layer_kernel<1, kHidden, T, T, true, EVEN_INPUT><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin);
     else if (l == 1)
         pt_layer_kernel<kHidden, kHidden, T, T, true><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin);
 }
@@ -652,13 +704,13 @@ void layer_wgrad(stag_ptnet* n, int l, const T* psi, const T* gout) {
     const int nw = kPaths * cout * cin;
     if (l == 0) {
         dim3 grid(kWgradBlocks, kPaths, 1);
-        pt_wgrad_kernel<1, kHidden, T><<<grid, 256, 0, S(n)>>>(g, n->links, psi, gout, cout, n->wpart);
+        pt_wgrad_kernel<1, kHidden, T, EVEN_INPUT><<<grid, 256, 0, S(n)>>>(g, n->links, psi, gout, cout, n->wpart);
     } else if (l == 1) {
         dim3 grid(kWgradBlocks, kPaths, kHidden / 4);
         pt_wgrad_kernel<kHidden, 4, T><<<grid, 256, 0, S(n)>>>(g, n->links, psi, gout, cout, n->wpart);
     } else {
         dim3 grid(kWgradBlocks, kPaths, 1);
-        pt_wgrad_kernel<kHidden, 1, T><<<grid, 256, 0, S(n)>>>(g, n->links, psi, gout, cout, n->wpart);
+        pt_wgrad_kernel<kHidden, 1, T, EVEN_OUTPUT><<<grid, 256, 0, S(n)>>>(g, n->links, psi, gout, cout, n->wpart);
     }
     pt_wgrad_sum_kernel<<<blocks_for(nw), kBlock, 0, S(n)>>>(n->wpart, kWgradBlocks, nw, n->grad + layer_offset(l));
 }
@@ -897,16 +949,20 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         auto W = [&](int l, int p, int o, int i) -> float2& {
             return n->w_host[layer_offset(l) + (p * kChan[l + 1] + o) * kChan[l] + i];
         };
+        // self-adjoint form M = L1^dag L2 L1: L1 = (r; D r), L2 = diag(alpha + beta m^2, beta),
+        // L3 = L1^dag = (r, -D .): M r = (alpha + beta m^2) r - beta D D r = alpha r + beta A_fat r
         W(0, 0, 0, 0).x += 1.f;                       // channel 0: r
-        W(1, 0, 0, 0).x += (float)(alpha + beta * m2); // (alpha + beta m^2) r
-        W(2, 0, 0, 0).x += 1.f;                       // output: channel 0
+        W(1, 0, 0, 0).x += (float)(alpha + beta * m2);
+        W(1, 0, 1, 1).x += (float)beta;
+        W(2, 0, 0, 0).x += 1.f;                       // output: channel 0 ...
         for (int mu = 0; mu < 4; ++mu) {
             W(0, 1 + 2 * mu, 1, 0).x += 1.f;           // channel 1: D r
             W(0, 2 + 2 * mu, 1, 0).x -= 1.f;
-            W(1, 1 + 2 * mu, 0, 1).x -= (float)beta;   // - beta D (D r)
-            W(1, 2 + 2 * mu, 0, 1).x += (float)beta;
+            W(2, 1 + 2 * mu, 0, 1).x -= 1.f;           // ... - D (channel 1)
+            W(2, 2 + 2 * mu, 0, 1).x += 1.f;
         }
         upload_weights(n);
+        pt_tie_kernel<<<1, 256, 0, S(n)>>>(n->w);  // the noise, too
         pcheck(n, cudaGetLastError(), "ptnet create");
         handle_end(h);
         *out = n;
@@ -1158,6 +1214,7 @@ int stag_ptnet_train(stag_ptnet* n, int32_t epochs, int32_t batch, double lr, ui
                                                                         n->adam_m, n->adam_v, 2 * nw,
                                                                         2.f / (float)(s1 - s0), (float)lr, b1, b2,
                                                                         c1, c2, eps);
+                pt_tie_kernel<<<1, 256, 0, S(n)>>>(n->w);
             }
             if (epoch_loss) epoch_loss[ep] = total / np;
         }

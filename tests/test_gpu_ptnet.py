@@ -182,6 +182,32 @@ def test_training_keeps_the_polynomial_start(trained):
     assert t["after"] <= 1.001 * t["before"], (t["before"], t["after"], t["losses"])
 
 
+def _tie_error(w):
+    ws = _split(w)
+    return max(np.abs(a - b).max() for a, b in zip(ptnet.tie(ws), ws))
+
+
+def test_training_keeps_the_network_self_adjoint(trained):
+    """After training (and from the polynomial start) the weights satisfy the tie
+    W3 = W1^dag, W2 = W2^dag of the oracle, and the GPU network is Hermitian."""
+    for name in ("poly", "poor"):
+        w = binding.stag_ptnet_weights(trained[name]["net"])
+        assert _tie_error(w) <= 1e-6 * np.abs(w).max(), name
+    dims, net = trained["dims"], trained["poly"]["net"]
+    u = _dev(inputs.gaussian_even_source(dims, 700))
+    v = _dev(inputs.gaussian_even_source(dims, 701))
+    mu, mv = torch.empty_like(u), torch.empty_like(v)
+    binding.stag_ptnet_set_inference_precision(net, binding.STAG_ARITH_F32)
+    try:
+        binding.stag_ptnet_apply(net, u, mu)
+        binding.stag_ptnet_apply(net, v, mv)
+    finally:
+        binding.stag_ptnet_set_inference_precision(net, binding.STAG_ARITH_BF16)
+    lhs = torch.vdot(u.reshape(-1), mv.reshape(-1)).item()
+    rhs = torch.vdot(mu.reshape(-1), v.reshape(-1)).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
+
+
 def test_fcg_with_trained_network_gains_over_plain_cg(trained):
     dims, m, h, net = trained["dims"], trained["m"], trained["h"], trained["poly"]["net"]
     op = oracle.Operator(trained["fat"], trained["lng"], m, dims)

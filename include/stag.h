@@ -308,6 +308,14 @@ int stag_ptnet_destroy(stag_ptnet* n);
  * given at create).  Training and the stored pairs keep the create precision. */
 int stag_ptnet_set_inference_precision(stag_ptnet* n, int32_t precision);
 
+/* enable != 0 (the default): the BF16 8 -> 8 layer's forward pass mixes the
+ * channels on the tensor cores (tcgen05: per tile of 128 sites and colour, the
+ * real form of the complex mixing as a 128 x 144 by 144 x 16 BF16 product with
+ * FP32 accumulation); 0: on the CUDA cores in FP32.  The transports are FP32
+ * either way.  A tensor-core wait that runs out makes the next call that
+ * applies the network return STAG_ERR_TIMEOUT. */
+int stag_ptnet_use_tensor_cores(stag_ptnet* n, int32_t enable);
+
 /* Flexible CG with z_k = M(r_k): alpha = (r, z) / (p, A p), x += alpha p,
  * r -= alpha A p, beta = (z_new, r_new - r_old) / (r_old, z_old), p = z + beta p,
  * with A in the handle's FP64-class arithmetic and FP64 vectors.  When the

@@ -77,6 +77,7 @@ EXPORTED = (
     "stag_ptnet_loss_grad",
     "stag_ptnet_add_pairs",
     "stag_ptnet_num_pairs",
+    "stag_ptnet_use_tensor_cores",
     "stag_ptnet_train",
     "stag_ptnet_dataset_loss",
     "stag_ptnet_last_error",
@@ -195,6 +196,7 @@ def load(path: str | None = None):
     lib.stag_ptnet_last_error.restype = ctypes.c_char_p
     lib.stag_ptnet_destroy.argtypes = [H]
     lib.stag_ptnet_set_inference_precision.argtypes = [H, i32]
+    lib.stag_ptnet_use_tensor_cores.argtypes = [H, i32]
     lib.stag_fcg_solve.argtypes = [H, H, P, P, d, i32, ctypes.POINTER(stag_solve_info)]
     lib.stag_dd_create.argtypes = [ctypes.POINTER(H), H, i32]
     lib.stag_dd_apply_A.argtypes = [H, P, P, i32, P]
@@ -439,6 +441,10 @@ def stag_ptnet_dataset_loss(net):
 
 def stag_ptnet_set_inference_precision(net, precision):
     _pcheck(load().stag_ptnet_set_inference_precision(net, int(precision)), net)
+
+
+def stag_ptnet_use_tensor_cores(net, enable):
+    _pcheck(load().stag_ptnet_use_tensor_cores(net, int(bool(enable))), net)
 
 
 def stag_ptnet_destroy(net):

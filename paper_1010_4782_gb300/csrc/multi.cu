@@ -131,19 +131,6 @@ __device__ __forceinline__ int nbr_index(const Geom& g, int x, int y, int z, int
     return site_index(x, y, z, t, g);
 }
 
-// L2 policy that keeps the lines it loads ahead of others (evict-last)
-__device__ __forceinline__ unsigned long long l2_keep_policy() {
-    unsigned long long pol;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ void ld256_keep(const float2* p, unsigned long long pol, float2& a, float2& b, float2& c,
-                                           float2& d) {
-    asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
-        : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y), "=f"(c.x), "=f"(c.y), "=f"(d.x), "=f"(d.y)
-        : "l"(p), "l"(pol));
-}
-
 // 256-bit accesses (sm_100 and later) of four consecutive float2; p is 32-byte aligned.
 __device__ __forceinline__ void ld256_nc(const float2* p, float2& a, float2& b, float2& c, float2& d) {
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -158,12 +145,6 @@ __device__ __forceinline__ void ld256(const float2* p, float2& a, float2& b, flo
 }
 __device__ __forceinline__ void st256(float2* p, float2 a, float2 b, float2 c, float2 d) {
     asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.x), "f"(a.y),
-                 "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
-                 : "memory");
-}
-// streaming (evict-first) store: data the kernel will not read again
-__device__ __forceinline__ void st256_cs(float2* p, float2 a, float2 b, float2 c, float2 d) {
-    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.x), "f"(a.y),
                  "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
                  : "memory");
 }
@@ -205,22 +186,13 @@ __device__ __forceinline__ void load_rb_rw(float2 (&v)[RB], const float2* p) {
     }
 }
 
-// STREAM: evict-first (the Dirac kernels' outputs, read only by the next launch)
-template <int RB, bool STREAM = false>
+template <int RB>
 __device__ __forceinline__ void store_rb(float2* p, const float2 (&v)[RB]) {
     if constexpr (RB == 1) {
-        if constexpr (STREAM)
-            __stcs(p, v[0]);
-        else
-            *p = v[0];
+        *p = v[0];
     } else if constexpr (RB % 4 == 0) {
 #pragma unroll
-        for (int j = 0; j < RB; j += 4) {
-            if constexpr (STREAM)
-                st256_cs(p + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
-            else
-                st256(p + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
-        }
+        for (int j = 0; j < RB; j += 4) st256(p + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
     } else {
 #pragma unroll
         for (int j = 0; j < RB; j += 2)
@@ -228,27 +200,17 @@ __device__ __forceinline__ void store_rb(float2* p, const float2 (&v)[RB]) {
     }
 }
 
-// acc[r][j] += U v (fwd, U at the output site) or -= U^dag v (bwd, U at the neighbour).
-// The input vectors, which up to 16 neighbours read (up to 3 t-slices apart),
-// are loaded with an evict-last L2 policy (keep); the links, used once per
-// launch, with the default one.
+// acc[r][j] += U v (fwd, U at the output site) or -= U^dag v (bwd, U at the neighbour)
 template <int RB, bool BWD>
 __device__ __forceinline__ void multi_hop(float2 (&acc)[3][RB], const float2* __restrict__ u,
-                                          const float2* __restrict__ in, int nb, size_t vs, int rpad, int roff,
-                                          unsigned long long keep) {
+                                          const float2* __restrict__ in, int nb, size_t vs, int rpad, int roff) {
     float2 U[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) U[k] = __ldg(u + k * vs);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float2 v[RB];
-        const float2* src = in + ((size_t)c * vs + nb) * rpad + roff;
-        if constexpr (RB % 4 == 0) {
-#pragma unroll
-            for (int j = 0; j < RB; j += 4) ld256_keep(src + j, keep, v[j], v[j + 1], v[j + 2], v[j + 3]);
-        } else {
-            load_rb<RB>(v, src);
-        }
+        load_rb<RB>(v, in + ((size_t)c * vs + nb) * rpad + roff);
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
 #pragma unroll
@@ -263,7 +225,7 @@ __device__ __forceinline__ void multi_hop(float2 (&acc)[3][RB], const float2* __
 }
 
 // out = D in (EPI_PLAIN), m2 src - D in (EPI_AXPY), or the latter with per-RHS
-// Re(src^dag out) -> alpha (EPI_CG).
+// Re(src^dag out) -> alpha (EPI_CG)
 template <int RB, int BS, int EPI>
 __global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
     const int4 w = L.items[blockIdx.x];  // (group, block in group, blocks in group, -)
@@ -278,7 +240,6 @@ __global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
     float2* out = L.phase == 0 ? G.t : G.ad;
     const float m2 = (float)G.m2;
     const int ntiles = (g.vh + l.spb - 1) / l.spb;
-    const unsigned long long keep = l2_keep_policy();
     float dotf[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) dotf[j] = 0.f;
@@ -297,21 +258,21 @@ __global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
         for (int mu = 0; mu < 4; ++mu) {
             const int f1 = nbr_index(g, x, y, z, t, mu, 1, true);
             const int b1 = nbr_index(g, x, y, z, t, mu, 1, false);
-            multi_hop<RB, false>(acc, G.fat + ((size_t)(P * 4 + mu) * 9) * vs + i, in, f1, vs, G.rpad, l.roff, keep);
-            multi_hop<RB, true>(acc, G.fat + ((size_t)(Q * 4 + mu) * 9) * vs + b1, in, b1, vs, G.rpad, l.roff, keep);
+            multi_hop<RB, false>(acc, G.fat + ((size_t)(P * 4 + mu) * 9) * vs + i, in, f1, vs, G.rpad, l.roff);
+            multi_hop<RB, true>(acc, G.fat + ((size_t)(Q * 4 + mu) * 9) * vs + b1, in, b1, vs, G.rpad, l.roff);
             if (G.lng) {
                 const int h = g.hop3[mu];
                 const int f3 = nbr_index(g, x, y, z, t, mu, h, true);
                 const int b3 = nbr_index(g, x, y, z, t, mu, h, false);
-                multi_hop<RB, false>(acc, G.lng + ((size_t)(P * 4 + mu) * 9) * vs + i, in, f3, vs, G.rpad, l.roff, keep);
-                multi_hop<RB, true>(acc, G.lng + ((size_t)(Q * 4 + mu) * 9) * vs + b3, in, b3, vs, G.rpad, l.roff, keep);
+                multi_hop<RB, false>(acc, G.lng + ((size_t)(P * 4 + mu) * 9) * vs + i, in, f3, vs, G.rpad, l.roff);
+                multi_hop<RB, true>(acc, G.lng + ((size_t)(Q * 4 + mu) * 9) * vs + b3, in, b3, vs, G.rpad, l.roff);
             }
         }
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             float2* o = out + ((size_t)r * vs + i) * G.rpad + l.roff;
             if constexpr (EPI == EPI_PLAIN) {
-                store_rb<RB, true>(o, acc[r]);
+                store_rb<RB>(o, acc[r]);
             } else {
                 float2 sv[RB], ov[RB];
                 load_rb<RB>(sv, G.d + ((size_t)r * vs + i) * G.rpad + l.roff);
@@ -321,7 +282,7 @@ __global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
                     dotf[j] = fmaf(sv[j].x, ov[j].x, dotf[j]);
                     dotf[j] = fmaf(sv[j].y, ov[j].y, dotf[j]);
                 }
-                store_rb<RB, true>(o, ov);
+                store_rb<RB>(o, ov);
             }
         }
     }

@@ -44,81 +44,10 @@
 #include "../../include/stag.h"
 #include "ff.cuh"
 #include "handle.h"
+#include "pt_common.cuh"
 #include "stag_kernels.h"
 
 namespace stag {
-
-constexpr int kPaths = 9;
-constexpr int kHidden = 8;
-constexpr int kLayers = 3;
-constexpr int kChan[kLayers + 1] = {1, kHidden, kHidden, 1};
-constexpr int kWgradBlocks = 608;  // x-blocks of the weight-gradient grid (4 per SM)
-
-__device__ __forceinline__ float2 ldc(const float2* p) { return *p; }
-__device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
-__device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
-__device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
-
-// whole-lattice field: [channel][colour][parity][vs]
-__device__ __forceinline__ size_t fidx(int ch, int c, int P, int i, size_t vs) {
-    return ((size_t)(ch * 3 + c) * 2 + P) * vs + i;
-}
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// conj(a) * b
-__device__ __forceinline__ float2 cmulf_conj(float2 a, float2 b) {
-    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-
-__device__ __forceinline__ int pt_neighbour(const Geom& g, int x, int y, int z, int t, int mu, bool up) {
-    switch (mu) {
-        case 0: x = up ? wrap_up(x, 1, g.lx) : wrap_dn(x, 1, g.lx); break;
-        case 1: y = up ? wrap_up(y, 1, g.ly) : wrap_dn(y, 1, g.ly); break;
-        case 2: z = up ? wrap_up(z, 1, g.lz) : wrap_dn(z, 1, g.lz); break;
-        default: t = up ? wrap_up(t, 1, g.lt) : wrap_dn(t, 1, g.lt); break;
-    }
-    return site_index(x, y, z, t, g);
-}
-
-// Source site (parity Pn, index nb) and link of transport direction d
-// (0: from x + mu with U_mu(x); 1: from x - mu with U_mu(x - mu)^dag).
-struct Hop {
-    int Pn, nb;
-    const float2* u;
-};
-
-__device__ __forceinline__ Hop pt_hop(const Geom& g, const float2* links, int P, int i, int x, int y, int z, int t,
-                                      int mu, int d) {
-    Hop h;
-    h.Pn = 1 - P;
-    const size_t vs = (size_t)g.vs;
-    if (d == 0) {
-        h.nb = pt_neighbour(g, x, y, z, t, mu, true);
-        h.u = links + ((size_t)(P * 4 + mu) * 9) * vs + i;
-    } else {
-        h.nb = pt_neighbour(g, x, y, z, t, mu, false);
-        h.u = links + ((size_t)((1 - P) * 4 + mu) * 9) * vs + h.nb;
-    }
-    return h;
-}
-
-// t = U v (d = 0) or U^dag v (d = 1)
-__device__ __forceinline__ void pt_apply(const float2 (&U)[9], int d, const float2 (&v)[3], float2 (&t)[3]) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float2 u = d == 0 ? U[3 * r + c] : U[3 * c + r];
-            const float2 m = d == 0 ? cmulf(u, v[c]) : cmulf_conj(u, v[c]);
-            a.x += m.x;
-            a.y += m.y;
-        }
-        t[r] = a;
-    }
-}
 
 // Which sites and paths a layer launch covers.  The network's input is zero on
 // odd sites and only its output's even sites are read, so:
@@ -615,6 +544,8 @@ struct stag_ptnet {
     float2 *va = nullptr, *vt = nullptr, *vad = nullptr;  // FP32 [3][vs] vectors for A d
     std::vector<float2> w_host;  // weights, layer-major [9][C_out][C_in]
     float2* w = nullptr;         // device weights (FP32 master)
+    bool use_tc = true;          // BF16 8 -> 8 forward layer on the tensor cores (pt_tc.cu)
+    int* tc_err = nullptr;       // set by a tensor-core layer whose bounded wait ran out
     float2* grad = nullptr;
     float *adam_m = nullptr, *adam_v = nullptr;
     long long adam_t = 0;
@@ -666,6 +597,14 @@ void* palloc(stag_ptnet* n, size_t bytes, const char* what) {
 }
 
 cudaStream_t S(stag_ptnet* n) { return n->h->s; }
+
+// Fails with STAG_ERR_TIMEOUT if a tensor-core layer reported a bounded wait that ran out.
+void check_tc(stag_ptnet* n) {
+    int flag = 0;
+    pcheck(n, cudaMemcpyAsync(&flag, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, S(n)), "read error flag");
+    pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+    if (flag) pfail(n, STAG_ERR_TIMEOUT, "tensor-core layer: a bounded wait on the MMA barrier ran out");
+}
 size_t field_bytes(const stag_ptnet* n, int ch) { return (size_t)ch * 3 * 2 * n->g.vs * sizeof(float2); }
 size_t slot_bytes(const stag_ptnet* n) { return (size_t)3 * n->g.vs * n->elem; }
 // blocks of a pt_layer_kernel launch over both parities (256 sites per block)
@@ -678,9 +617,15 @@ void layer_fwd(stag_ptnet* n, int l, const T* in, T* out) {
     const int nb = site_blocks(g);
     if (l == 0)
         pt_layer_kernel<1, kHidden, T, T, false, EVEN_INPUT><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
-    else if (l == 1)
+    else if (l == 1) {
+        if constexpr (std::is_same<T, __nv_bfloat162>::value) {
+            if (n->use_tc) {
+                launch_pt_mix8_tc(g, n->links, w, in, out, n->tc_err, S(n));
+                return;
+            }
+        }
         pt_layer_kernel<kHidden, kHidden, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
-    else
+    } else
         pt_layer_kernel<kHidden, 1, T, T, false, EVEN_OUTPUT><<<blocks_for(g.vh), 256, 0, S(n)>>>(g, n->links, w, in,
                                                                                                   out);
 }
@@ -895,6 +840,7 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         n->vad = static_cast<float2*>(palloc(n, fv, "allocate vectors"));
         const int nw = n_weights();
         n->w = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate weights"));
+        n->tc_err = static_cast<int*>(palloc(n, sizeof(int), "allocate error flag"));
         n->grad = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate gradients"));
         n->adam_m = static_cast<float*>(palloc(n, 2 * nw * sizeof(float), "allocate optimiser"));
         n->adam_v = static_cast<float*>(palloc(n, 2 * nw * sizeof(float), "allocate optimiser"));
@@ -1031,6 +977,7 @@ int stag_ptnet_apply(stag_ptnet* n, const double* r_even, double* z_even) {
         if (!out_dev)
             pcheck(n, cudaMemcpyAsync(z_even, h->io_b, (size_t)3 * g.vh * sizeof(double2), cudaMemcpyDeviceToHost, S(n)), "copy z");
         pcheck(n, cudaGetLastError(), "ptnet apply");
+        check_tc(n);
         handle_end(h);
         return STAG_OK;
     } catch (const PFail& f) {
@@ -1219,6 +1166,7 @@ int stag_ptnet_train(stag_ptnet* n, int32_t epochs, int32_t batch, double lr, ui
             if (epoch_loss) epoch_loss[ep] = total / np;
         }
         pcheck(n, cudaGetLastError(), "training");
+        check_tc(n);
         download_weights(n);
         handle_end(n->h);
         return STAG_OK;
@@ -1251,6 +1199,12 @@ int stag_ptnet_dataset_loss(stag_ptnet* n, double* loss) {
 int stag_ptnet_set_inference_precision(stag_ptnet* n, int32_t precision) {
     if (!n || (precision != STAG_ARITH_BF16 && precision != STAG_ARITH_F32)) return STAG_ERR_INVALID_ARG;
     n->inf_prec = precision;
+    return STAG_OK;
+}
+
+int stag_ptnet_use_tensor_cores(stag_ptnet* n, int32_t enable) {
+    if (!n) return STAG_ERR_INVALID_ARG;
+    n->use_tc = enable != 0;
     return STAG_OK;
 }
 
@@ -1399,6 +1353,7 @@ int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* 
         launch_unpack_vec(g, h->x, x_dev ? x_even : h->io_b, S(n));
         if (!x_dev) pcheck(n, cudaMemcpyAsync(x_even, h->io_b, ab, cudaMemcpyDeviceToHost, S(n)), "copy x");
         pcheck(n, cudaGetLastError(), "flexible CG");
+        check_tc(n);
         handle_end(h);
     } catch (const PFail& f) {
         status = f.code;

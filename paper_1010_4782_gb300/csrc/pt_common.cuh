@@ -1,0 +1,92 @@
+// pt_common.cuh - definitions shared by the parallel-transport network kernels
+// (pt.cu: CUDA-core layers, gradients, training; pt_tc.cu: tensor-core channel
+// mixing).  Paths p = 0..8: the identity and the one-hop transports
+// T_{+mu} psi(x) = U_mu(x) psi(x + mu), T_{-mu} psi(x) = U_mu(x - mu)^dag psi(x - mu)
+// with the eta-folded fat links, p = 1 + 2 mu + s (s = 0: from x + mu, 1: from x - mu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "stag_kernels.h"
+
+namespace stag {
+
+constexpr int kPaths = 9;
+constexpr int kHidden = 8;
+constexpr int kLayers = 3;
+constexpr int kChan[kLayers + 1] = {1, kHidden, kHidden, 1};
+constexpr int kWgradBlocks = 608;  // x-blocks of the weight-gradient grid (4 per SM)
+
+__device__ __forceinline__ float2 ldc(const float2* p) { return *p; }
+__device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+__device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+
+// whole-lattice field: [channel][colour][parity][vs]
+__device__ __forceinline__ size_t fidx(int ch, int c, int P, int i, size_t vs) {
+    return ((size_t)(ch * 3 + c) * 2 + P) * vs + i;
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulf_conj(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ int pt_neighbour(const Geom& g, int x, int y, int z, int t, int mu, bool up) {
+    switch (mu) {
+        case 0: x = up ? wrap_up(x, 1, g.lx) : wrap_dn(x, 1, g.lx); break;
+        case 1: y = up ? wrap_up(y, 1, g.ly) : wrap_dn(y, 1, g.ly); break;
+        case 2: z = up ? wrap_up(z, 1, g.lz) : wrap_dn(z, 1, g.lz); break;
+        default: t = up ? wrap_up(t, 1, g.lt) : wrap_dn(t, 1, g.lt); break;
+    }
+    return site_index(x, y, z, t, g);
+}
+
+// Source site (parity Pn, index nb) and link of transport direction d
+// (0: from x + mu with U_mu(x); 1: from x - mu with U_mu(x - mu)^dag).
+struct Hop {
+    int Pn, nb;
+    const float2* u;
+};
+
+__device__ __forceinline__ Hop pt_hop(const Geom& g, const float2* links, int P, int i, int x, int y, int z, int t,
+                                      int mu, int d) {
+    Hop h;
+    h.Pn = 1 - P;
+    const size_t vs = (size_t)g.vs;
+    if (d == 0) {
+        h.nb = pt_neighbour(g, x, y, z, t, mu, true);
+        h.u = links + ((size_t)(P * 4 + mu) * 9) * vs + i;
+    } else {
+        h.nb = pt_neighbour(g, x, y, z, t, mu, false);
+        h.u = links + ((size_t)((1 - P) * 4 + mu) * 9) * vs + h.nb;
+    }
+    return h;
+}
+
+// t = U v (d = 0) or U^dag v (d = 1)
+__device__ __forceinline__ void pt_apply(const float2 (&U)[9], int d, const float2 (&v)[3], float2 (&t)[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 u = d == 0 ? U[3 * r + c] : U[3 * c + r];
+            const float2 m = d == 0 ? cmulf(u, v[c]) : cmulf_conj(u, v[c]);
+            a.x += m.x;
+            a.y += m.y;
+        }
+        t[r] = a;
+    }
+}
+
+// The 8 -> 8 layer (forward, BF16 activations) with the channel mixing on the
+// tensor cores (pt_tc.cu).  w: the layer's complex weights [9][8][8]; err: set
+// to 1 if a bounded wait ran out.
+void launch_pt_mix8_tc(const Geom& g, const float2* links, const float2* w, const __nv_bfloat162* in,
+                       __nv_bfloat162* out, int* err, cudaStream_t s);
+
+}  // namespace stag

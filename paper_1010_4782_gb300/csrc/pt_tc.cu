@@ -1,0 +1,266 @@
+// pt_tc.cu - the 8 -> 8 layer of the parallel-transport network with its
+// channel mixing on the tensor cores (tcgen05, sm_100 and later).
+//
+// The layer is psi'(x, o) = sum_p sum_i W[p][o][i] (T_p psi_i)(x) (paths and
+// transports as in pt_common.cuh).  For a tile of 128 sites of one parity and
+// each colour c it is the real matrix product
+//     D_c[s][n] = sum_k A_c[s][k] B[n][k],   s < 128, n < 16, k < 144,
+// with A_c[s][16 p + 2 i + h] the real (h = 0) or imaginary (h = 1) part of
+// (T_p psi_i)(s)_c rounded to BF16, and B the real form of the complex weights
+// (y = w x:  y_re = w_re x_re - w_im x_im,  y_im = w_im x_re + w_re x_im):
+//     B[2o][16p+2i] = w_re,  B[2o][16p+2i+1] = -w_im,
+//     B[2o+1][16p+2i] = w_im,  B[2o+1][16p+2i+1] = w_re,   w = W[p][o][i];
+// D_c[s][2o + h] is then the real / imaginary part of psi'(s, o)_c.
+//
+// One thread per site.  K runs in three phases of three paths: each thread
+// transports its site's 8 channels along the phase's paths (FP32 links, FP32
+// arithmetic) and writes them to A in shared memory; one thread issues the
+// 3 colours x 3 MMAs (M = 128, N = 16, K = 16, BF16 operands, FP32
+// accumulators in TMEM columns 16 c .. 16 c + 15) and commits them to an
+// mbarrier, which every thread waits on before A is overwritten.  At the end
+// each warp reads its 32 rows back with tcgen05.ld and stores them.
+//
+// Shared-memory operands use the canonical K-major layout without swizzle:
+// 8 rows x 16 bytes core matrices; the leading byte offset (LBO) steps to the
+// next core matrix along K, the stride byte offset (SBO) to the next group of
+// 8 rows.  Waits are bounded; a wait that runs out sets *err and the kernel
+// finishes without further MMAs.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "pt_common.cuh"
+
+namespace stag {
+
+namespace {
+
+constexpr int kTileRows = 128;                    // sites per CTA (= MMA M)
+constexpr int kPhasePaths = 3;                    // paths per K phase
+constexpr int kKPhase = kPhasePaths * 16;         // 48 K elements per phase
+constexpr int kAKGroups = kKPhase / 8;            // 6 core matrices along K per phase
+constexpr int kASbo = kAKGroups * 128;            // 768 B between 8-row groups
+constexpr int kAColour = (kTileRows / 8) * kASbo; // 12288 B per colour
+constexpr int kABytes = 3 * kAColour;             // 36864 B
+constexpr int kBKGroups = kPaths * 16 / 8;        // 18
+constexpr int kBSbo = kBKGroups * 128;            // 2304 B
+constexpr int kBBytes = 2 * kBSbo;                // 4608 B (N = 16: two 8-row groups)
+constexpr int kTmemCols = 64;                     // 48 used: 3 colours x N = 16
+constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls before giving up
+
+// smem layout: [A 36864][B 4608][mbarrier 8][tmem address 4]
+constexpr int kSmemBytes = kABytes + kBBytes + 16;
+
+// tcgen05 instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((uint32_t)(kTileRows >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, LBO and SBO in
+// 16-byte units (bits 0-13, 16-29, 32-45), descriptor version 1 (bits 46-47),
+// base offset 0, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <class TI, class TO>
+__global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const float2* __restrict__ links,
+                                                              const float2* __restrict__ w,
+                                                              const TI* __restrict__ in, TO* __restrict__ out,
+                                                              int* err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kABytes;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kABytes + kBBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kABytes + kBBytes + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // TMEM columns for the accumulators (one warp allocates), the mbarrier,
+    // and B from the complex weights W[p][o][i].
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = tid; e < 16 * kPaths * 16; e += kTileRows) {
+        const int n = e / (kPaths * 16), k = e % (kPaths * 16);
+        const int o = n >> 1, ho = n & 1, p = k >> 4, i = (k & 15) >> 1, hi = k & 1;
+        const float2 wv = w[(p * kHidden + o) * kHidden + i];
+        const float v = ho == hi ? wv.x : (ho == 0 ? -wv.y : wv.y);
+        *reinterpret_cast<__nv_bfloat16*>(sB + (n >> 3) * kBSbo + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) =
+            __float2bfloat16_rn(v);
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    const int P = (int)(blockIdx.x & 1);
+    const int i = (int)(blockIdx.x >> 1) * kTileRows + tid;
+    const bool active = i < g.vh;
+    const size_t vs = (size_t)g.vs;
+    int x = 0, y = 0, z = 0, t = 0;
+    if (active) site_coords(i, P, g, x, y, z, t);
+    uint8_t* rowA = sA + (tid >> 3) * kASbo + (tid & 7) * 16;
+    const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB), barA = smem_u32(bar);
+    bool ok = true;
+
+    for (int ph = 0; ph < kPaths / kPhasePaths; ++ph) {
+        if (active) {
+#pragma unroll 1
+            for (int pp = 0; pp < kPhasePaths; ++pp) {
+                const int p = ph * kPhasePaths + pp;
+                int Pn = P, nb = i, d = 0;
+                float2 U[9];
+                if (p > 0) {
+                    const int mu = (p - 1) >> 1;
+                    d = (p - 1) & 1;
+                    const Hop hp = pt_hop(g, links, P, i, x, y, z, t, mu, d);
+                    Pn = hp.Pn;
+                    nb = hp.nb;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t word[3][4];
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) {
+                        const int ch = 4 * h + ii;
+                        float2 v[3], tv[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) v[c] = ldc(in + fidx(ch, c, Pn, nb, vs));
+                        if (p > 0) {
+                            pt_apply(U, d, v, tv);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) tv[c] = v[c];
+                        }
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) word[c][ii] = pack_bf16x2(tv[c].x, tv[c].y);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        *reinterpret_cast<uint4*>(rowA + c * kAColour + (2 * pp + h) * 128) =
+                            make_uint4(word[c][0], word[c][1], word[c][2], word[c][3]);
+                }
+            }
+        }
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        if (tid == 0 && ok) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int kk = 0; kk < kPhasePaths; ++kk) {
+                    const uint64_t da = smem_desc(aBase + c * kAColour + kk * 2 * 128, 128, kASbo);
+                    const uint64_t db = smem_desc(bBase + (ph * kAKGroups + kk * 2) * 128, 128, kBSbo);
+                    mma_bf16(tmem + 16 * c, da, db, (ph > 0 || kk > 0) ? 1u : 0u);
+                }
+            mma_commit(barA);
+        }
+        // every thread waits for this phase's MMAs before A is rewritten
+        long long spins = 0;
+        while (ok && !mbar_try_wait(barA, (uint32_t)(ph & 1))) {
+            if (++spins > kWaitLimit) {
+                ok = false;
+                atomicExch(err, 1);
+            }
+        }
+        fence_after_sync();
+        __syncthreads();
+        ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    }
+
+    // accumulators -> registers (warp w holds rows 32 w .. 32 w + 31) -> output
+    float dv[3][16];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * c, dv[c]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (active && ok) {
+#pragma unroll
+        for (int o = 0; o < kHidden; ++o)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) stc(out + fidx(o, c, P, i, vs), make_float2(dv[c][2 * o], dv[c][2 * o + 1]));
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+void launch_pt_mix8_tc(const Geom& g, const float2* links, const float2* w, const __nv_bfloat162* in,
+                       __nv_bfloat162* out, int* err, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(pt_mix8_tc_kernel<__nv_bfloat162, __nv_bfloat162>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        attr_set = true;
+    }
+    const int tiles = (g.vh + kTileRows - 1) / kTileRows;
+    pt_mix8_tc_kernel<__nv_bfloat162, __nv_bfloat162><<<2 * tiles, kTileRows, kSmemBytes, s>>>(g, links, w, in, out,
+                                                                                              err);
+}
+
+}  // namespace stag

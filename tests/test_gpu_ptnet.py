@@ -74,6 +74,35 @@ def test_forward_parity(dims, prec, tol):
     assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 12), (8, 8, 8, 16)])
+def test_tensor_core_layer_matches_cuda_cores_and_oracle(dims):
+    """The BF16 network with its 8 -> 8 channel mixing on the tensor cores against
+    the same network on the CUDA cores and the FP64 oracle, on lattices of 1, 11.25
+    (ragged) and 32 tiles of 128 sites per parity.  Both BF16 paths round the
+    stored activations (2^-9 relative); the tensor-core path also rounds the
+    transported inputs of the mixing, so the bound is that of the BF16 parity test."""
+    fat = inputs.gauge_field(dims, 84)
+    w = _random_flat(85)
+    r = inputs.gaussian_even_source(dims, 86)
+    ref = ptnet.PTNet(fat, dims, _split(w)).apply(r)
+    outs = {}
+    with _handle(fat, None, dims, 0.1) as h:
+        net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 1)
+        try:
+            binding.stag_ptnet_set_weights(net, w)
+            for tc in (True, False):
+                binding.stag_ptnet_use_tensor_cores(net, tc)
+                z = torch.empty_like(_dev(r))
+                binding.stag_ptnet_apply(net, _dev(r), z)
+                outs[tc] = z.cpu().numpy()
+        finally:
+            binding.stag_ptnet_destroy(net)
+    for tc, got in outs.items():
+        assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref), tc
+    assert np.linalg.norm(outs[True] - outs[False]) <= 2e-2 * np.linalg.norm(ref)
+    assert np.linalg.norm(outs[True] - outs[False]) > 0.0   # the two paths really differ
+
+
 def test_network_weights_reproducing_A():
     """Layer 1: (r, D r); layer 2: m^2 r - D(D r); layer 3: identity => the network is A."""
     dims, m = (4, 6, 4, 8), 0.3

@@ -335,7 +335,8 @@ def run_ours(args):
                     ("ff_plain", binding.STAG_ARITH_FF, binding.STAG_INNER_NONE),
                     ("mixed_fp32", binding.STAG_ARITH_FF, binding.STAG_INNER_F32),
                     ("mixed_fp16", binding.STAG_ARITH_FF, binding.STAG_INNER_F16),
-                    ("mixed_bf16", binding.STAG_ARITH_FF, binding.STAG_INNER_BF16)]
+                    ("mixed_bf16", binding.STAG_ARITH_FF, binding.STAG_INNER_BF16),
+                    ("mixed_fp32_fp16links", binding.STAG_ARITH_FF, binding.STAG_INNER_F32_L16)]
         forms = {}
         one_hop = torch.from_numpy(inputs.gauge_field(dims, 1)).to(dev)
         for op_name, f_in, l_in in (("asqtad", fat_d, lng_d), ("one_hop", one_hop, None)):
@@ -345,7 +346,7 @@ def run_ours(args):
                 if x64 is None:
                     x64 = x
                 rec = {"time_s": round(info["time_ms"] / 1e3, 4), "status": code, "iters": info["iters"],
-                       "reliable_updates": info["reliable_updates"],
+                       "reliable_updates": info["reliable_updates"], "fallbacks": info["fallbacks"],
                        "true_rel_residual": info["true_rel_residual"],
                        "rel_diff_vs_fp64_plain": float(torch.linalg.vector_norm(x - x64) /
                                                        torch.linalg.vector_norm(x64))}

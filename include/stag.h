@@ -66,7 +66,9 @@ enum {
  * FP64-class arithmetic selected by `arith` (plain CG, Fig. 1).  F32 / F16 / BF16:
  * mixed-precision CG (the paper's stated next step, Sec. 5) - the iteration runs
  * on FP32 vectors and links (F32) or on FP16- or BF16-stored vectors and links
- * with FP32 arithmetic (F16, BF16), and the iterated residual is replaced by the true residual
+ * with FP32 arithmetic (F16, BF16), or on FP32 vectors with FP16-stored links
+ * (F32_L16: the links carry most of the Dirac kernel's bytes, while the CG vectors
+ * keep FP32's significand), and the iterated residual is replaced by the true residual
  * b - A x, computed in the FP64-class arithmetic, whenever it has dropped by
  * reliable_delta since the last replacement or after reliable_interval
  * iterations (reliable updates, Sleijpen & van der Vorst 1996).  x, b and the
@@ -75,7 +77,8 @@ enum {
     STAG_INNER_NONE = 0,
     STAG_INNER_F32 = 1,
     STAG_INNER_F16 = 2,
-    STAG_INNER_BF16 = 3
+    STAG_INNER_BF16 = 3,
+    STAG_INNER_F32_L16 = 4  /* FP32 vectors and arithmetic, FP16-stored links */
 };
 
 /* Kernel ids for stag_kernel_stats. */
@@ -114,7 +117,7 @@ typedef struct {
     double true_rel_residual; /* |b - A x| / |b|, A applied in native FP64                 */
     double iter_rel_residual; /* sqrt(delta_new) / |b| of the last Fig. 1 iterate          */
     double time_ms;           /* wall time of the solve inside the call                     */
-    int32_t fallbacks;        /* flexible CG: hand-overs to plain CG                        */
+    int32_t fallbacks;        /* hand-overs to plain CG (flexible CG, mixed-precision safeguard) */
     int32_t reserved;
 } stag_solve_info;
 

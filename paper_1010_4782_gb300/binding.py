@@ -33,6 +33,7 @@ STAG_INNER_NONE = 0
 STAG_INNER_F32 = 1
 STAG_INNER_F16 = 2
 STAG_INNER_BF16 = 3
+STAG_INNER_F32_L16 = 4
 
 STAG_DD_HOST = 0
 STAG_DD_DEVICE = 1

@@ -137,6 +137,10 @@ void dslash_lo(const Geom& g, int P, const float2* fat, const float2* lng, const
                const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s) {
     launch_dslash_f32(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
 }
+void dslash_lo(const Geom& g, int P, const __half2* fat, const __half2* lng, const float2* in, float2* out, Epilogue e,
+               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s) {
+    launch_dslash_f32l16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
+}
 void dslash_lo(const Geom& g, int P, const __half2* fat, const __half2* lng, const __half2* in, __half2* out,
                Epilogue e, const __half2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s) {
     launch_dslash_h16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
@@ -153,16 +157,17 @@ const __half2* lo_lng(const stag_handle* h, const __half2*) { return h->lng16; }
 const __nv_bfloat162* lo_fat(const stag_handle* h, const __nv_bfloat162*) { return h->fatb16; }
 const __nv_bfloat162* lo_lng(const stag_handle* h, const __nv_bfloat162*) { return h->lngb16; }
 
-// One inner iteration of the mixed-precision CG on storage type V.
-template <class V, class Mark>
+// One inner iteration of the mixed-precision CG on vectors stored as V and
+// links stored as L.
+template <class V, class L = V, class Mark>
 void enqueue_lo_iteration(stag_handle* h, Mark mark) {
     const Geom& g = h->g;
     V* d = static_cast<V*>(h->lo_d);
     V* t = static_cast<V*>(h->lo_t);
     V* ad = static_cast<V*>(h->lo_ad);
     V* r = static_cast<V*>(h->lo_r);
-    const V* fat = lo_fat(h, d);
-    const V* lng = lo_lng(h, d);
+    const L* fat = lo_fat(h, static_cast<const L*>(nullptr));
+    const L* lng = lo_lng(h, static_cast<const L*>(nullptr));
     mark(0);
     dslash_lo(g, 1, fat, lng, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
     mark(1);
@@ -203,6 +208,8 @@ void enqueue_iteration(stag_handle* h, cudaEvent_t* ev, bool count) {
         enqueue_lo_iteration<__half2>(h, mark);
     } else if (h->opt.inner == STAG_INNER_BF16) {
         enqueue_lo_iteration<__nv_bfloat162>(h, mark);
+    } else if (h->opt.inner == STAG_INNER_F32_L16) {
+        enqueue_lo_iteration<float2, __half2>(h, mark);
     } else if (use_ff(h)) {
         float4* d = static_cast<float4*>(h->d);
         float4* t = static_cast<float4*>(h->t);
@@ -324,6 +331,7 @@ void destroy_handle(stag_handle* h) {
     dev_free(h->lo_ad);
     dev_free(h->lo_r);
     dev_free(h->lo_y);
+    dev_free(h->x_best);
     dev_free(h->io_a);
     dev_free(h->io_b);
     dev_free(h->partials);
@@ -382,6 +390,16 @@ bool apply_A_fp64class(stag_handle* h, const double2* x) {
     return true;
 }
 
+void solve_plain(stag_handle* h, double bnorm2, double tol, long long max_it, stag_solve_info& inf, int& status,
+                 double& rel);
+
+void drop_graph(stag_handle* h) {
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
+
 // Mixed-precision CG with reliable updates (header: STAG_INNER_*).  Each pass
 // of the loop folds the inner solution increment into x, recomputes the true
 // residual b - A x in FP64-class arithmetic, stops if it meets tol (confirmed
@@ -389,6 +407,12 @@ bool apply_A_fp64class(stag_handle* h, const double2* x) {
 // to unit rms entries for FP16 storage - keeps the search direction (with beta
 // from the replaced residual), and runs the inner iteration until the next
 // replacement is due.  BF16 shares FP32's exponent range and needs no scaling.
+// Safeguard: the iterate with the smallest true residual is kept; when a true
+// residual exceeds 10 times that smallest one, or 5 replacements in a row bring
+// no improvement (the low-precision operator is too far from A for this system:
+// its rounding moves the low modes more than m^2), the best iterate is restored
+// and the solve finishes with plain CG in the FP64-class arithmetic (counted in
+// info.fallbacks).
 void solve_mixed(stag_handle* h, double bnorm2, double tol, long long max_it, stag_solve_info& inf,
                  int& status, double& rel) {
     const Geom& g = h->g;
@@ -399,6 +423,10 @@ void solve_mixed(stag_handle* h, double bnorm2, double tol, long long max_it, st
     bool first = true;
     long long iters = 0;
     int updates = 0;
+    double best = INFINITY;
+    int since_best = 0;
+    bool fallback = false;
+    const size_t vb = (size_t)3 * g.vs * sizeof(double2);
     while (true) {
         if (!first) {
             launch_lo_fold_y(g, h->x, h->lo_y, sigma_old, h->s);
@@ -410,6 +438,15 @@ void solve_mixed(stag_handle* h, double bnorm2, double tol, long long max_it, st
         launch_check(h, "true residual");
         const double dtrue = read_red_out(h);
         rel = std::sqrt(dtrue / bnorm2);
+        if (std::isfinite(dtrue) && rel < best) {
+            best = rel;
+            since_best = 0;
+            cuda_check(h, cudaMemcpyAsync(h->x_best, h->x, vb, cudaMemcpyDeviceToDevice, h->s), "keep best iterate");
+        } else if (!first && (!std::isfinite(dtrue) || rel > 10.0 * best || ++since_best >= 5)) {
+            cuda_check(h, cudaMemcpyAsync(h->x, h->x_best, vb, cudaMemcpyDeviceToDevice, h->s), "restore best iterate");
+            fallback = true;
+            break;
+        }
         if (!std::isfinite(dtrue)) {
             status = STAG_ERR_BREAKDOWN;
             h->err = "mixed-precision CG: non-finite residual";
@@ -466,6 +503,24 @@ void solve_mixed(stag_handle* h, double bnorm2, double tol, long long max_it, st
             h->err = "CG breakdown: d^dag A d <= 0 or non-finite";
             break;
         }
+    }
+    if (fallback) {
+        const int inner = h->opt.inner;
+        drop_graph(h);
+        h->opt.inner = STAG_INNER_NONE;
+        try {
+            solve_plain(h, bnorm2, tol, max_it - iters, inf, status, rel);
+        } catch (...) {
+            h->opt.inner = inner;
+            drop_graph(h);
+            throw;
+        }
+        h->opt.inner = inner;
+        drop_graph(h);
+        inf.fallbacks += 1;
+        inf.iters += (int32_t)iters;
+        inf.reliable_updates = updates;
+        return;
     }
     inf.iters = (int32_t)iters;
     inf.reliable_updates = updates;
@@ -621,7 +676,7 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
             fail(nullptr, STAG_ERR_INVALID_ARG, "check_interval must be in [1, 4096]");
         if (o.max_restarts < 0) fail(nullptr, STAG_ERR_INVALID_ARG, "max_restarts must be >= 0");
         if (o.inner != STAG_INNER_NONE && o.inner != STAG_INNER_F32 && o.inner != STAG_INNER_F16 &&
-            o.inner != STAG_INNER_BF16)
+            o.inner != STAG_INNER_BF16 && o.inner != STAG_INNER_F32_L16)
             fail(nullptr, STAG_ERR_INVALID_ARG, "unknown inner precision");
         if (o.inner != STAG_INNER_NONE &&
             (o.reliable_interval < 1 || !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0)))
@@ -667,7 +722,7 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         if (h->opt.inner == STAG_INNER_F32) {
             h->fat32 = dev_alloc<float2>(h, lo_links * sizeof(float2), "allocate FP32 links");
             if (h->naik) h->lng32 = dev_alloc<float2>(h, lo_links * sizeof(float2), "allocate FP32 Naik links");
-        } else if (h->opt.inner == STAG_INNER_F16) {
+        } else if (h->opt.inner == STAG_INNER_F16 || h->opt.inner == STAG_INNER_F32_L16) {
             h->fat16 = dev_alloc<__half2>(h, lo_links * sizeof(__half2), "allocate FP16 links");
             if (h->naik) h->lng16 = dev_alloc<__half2>(h, lo_links * sizeof(__half2), "allocate FP16 Naik links");
         } else if (h->opt.inner == STAG_INNER_BF16) {
@@ -676,12 +731,14 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
                 h->lngb16 = dev_alloc<__nv_bfloat162>(h, lo_links * sizeof(__nv_bfloat162), "allocate BF16 Naik links");
         }
         if (h->opt.inner != STAG_INNER_NONE) {
-            const size_t lo_vb = (size_t)3 * g.vs * (h->opt.inner == STAG_INNER_F32 ? sizeof(float2) : sizeof(__half2));
+            const bool vec32 = h->opt.inner == STAG_INNER_F32 || h->opt.inner == STAG_INNER_F32_L16;
+            const size_t lo_vb = (size_t)3 * g.vs * (vec32 ? sizeof(float2) : sizeof(__half2));
             h->lo_d = dev_alloc<void>(h, lo_vb, "allocate inner d");
             h->lo_t = dev_alloc<void>(h, lo_vb, "allocate inner t");
             h->lo_ad = dev_alloc<void>(h, lo_vb, "allocate inner Ad");
             h->lo_r = dev_alloc<void>(h, lo_vb, "allocate inner r");
             h->lo_y = dev_alloc<float2>(h, (size_t)3 * g.vs * sizeof(float2), "allocate inner y");
+            h->x_best = dev_alloc<double2>(h, vb, "allocate best iterate");
         }
         h->io_a = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
         h->io_b = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");

@@ -35,6 +35,8 @@ struct ArithF64 {
     using T = double2;  // storage
     using C = double2;  // compute
     static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
+    using TL = T;  // link storage
+    static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     struct Acc {
         double2 c[3];
     };
@@ -69,6 +71,8 @@ struct ArithFF {
     using T = float4;
     using C = float4;
     static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
+    using TL = T;  // link storage
+    static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     struct Acc {
         FFAcc re[3], im[3];
         FFAcc dot;
@@ -104,6 +108,8 @@ struct ArithF32 {
     using T = float2;
     using C = float2;
     static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
+    using TL = T;  // link storage
+    static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     struct Acc {
         float2 c[3];
         float dot;
@@ -139,6 +145,8 @@ struct ArithH16 {
     using T = __half2;
     using C = float2;
     static __device__ __forceinline__ C ld(const T* p) { return __half22float2(__ldg(p)); }
+    using TL = T;  // link storage
+    static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     using Acc = ArithF32::Acc;
     static __device__ __forceinline__ void zero(Acc& a) { ArithF32::zero(a); }
     static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
@@ -159,6 +167,8 @@ struct ArithB16 {
     using T = __nv_bfloat162;
     using C = float2;
     static __device__ __forceinline__ C ld(const T* p) { return __bfloat1622float2(__ldg(p)); }
+    using TL = T;  // link storage
+    static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     using Acc = ArithF32::Acc;
     static __device__ __forceinline__ void zero(Acc& a) { ArithF32::zero(a); }
     static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
@@ -173,12 +183,34 @@ struct ArithB16 {
     }
 };
 
+// FP16-stored links, FP32 vectors and arithmetic: the links carry most of the
+// bytes, the vectors keep FP32's significand (the CG direction and residual).
+struct ArithL16 {
+    using T = float2;
+    using TL = __half2;
+    using C = float2;
+    static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ C ldl(const TL* p) { return __half22float2(__ldg(p)); }
+    using Acc = ArithF32::Acc;
+    static __device__ __forceinline__ void zero(Acc& a) { ArithF32::zero(a); }
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        ArithF32::row_fwd(a, r, u0, u1, u2, v0, v1, v2);
+    }
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        ArithF32::row_bwd(a, r, u0, u1, u2, v0, v1, v2);
+    }
+    static __device__ __forceinline__ T store_val(const Acc& a, int r) { return ArithF32::store_val(a, r); }
+    static __device__ __forceinline__ T epilogue(Acc& a, int r, C s, double m2, float2 m2f, double& dot) {
+        return ArithF32::epilogue(a, r, s, m2, m2f, dot);
+    }
+};
+
 template <class A>
 struct DslashParams {
     Geom g;
     int P;                     // output parity
-    const typename A::T* fat;  // [2][4][9][vs]
-    const typename A::T* lng;  // [2][4][9][vs] or nullptr
+    const typename A::TL* fat;  // [2][4][9][vs]
+    const typename A::TL* lng;  // [2][4][9][vs] or nullptr
     const typename A::T* in;   // [3][vs], parity 1-P
     typename A::T* out;        // [3][vs], parity P
     const typename A::T* src;  // [3][vs], parity P (EPI_AXPY / EPI_CG)
@@ -190,23 +222,23 @@ struct DslashParams {
 };
 
 template <class A>
-__device__ __forceinline__ void hop_fwd(typename A::Acc& acc, const typename A::T* __restrict__ u,
+__device__ __forceinline__ void hop_fwd(typename A::Acc& acc, const typename A::TL* __restrict__ u,
                                         const typename A::T* __restrict__ in, int nb, size_t vs) {
     const typename A::C v0 = A::ld(in + nb), v1 = A::ld(in + vs + nb), v2 = A::ld(in + 2 * vs + nb);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-        A::row_fwd(acc, r, A::ld(u + (3 * r) * vs), A::ld(u + (3 * r + 1) * vs), A::ld(u + (3 * r + 2) * vs),
+        A::row_fwd(acc, r, A::ldl(u + (3 * r) * vs), A::ldl(u + (3 * r + 1) * vs), A::ldl(u + (3 * r + 2) * vs),
                    v0, v1, v2);
 }
 
 template <class A>
-__device__ __forceinline__ void hop_bwd(typename A::Acc& acc, const typename A::T* __restrict__ u,
+__device__ __forceinline__ void hop_bwd(typename A::Acc& acc, const typename A::TL* __restrict__ u,
                                         const typename A::T* __restrict__ in, int nb, size_t vs) {
     const typename A::C v0 = A::ld(in + nb), v1 = A::ld(in + vs + nb), v2 = A::ld(in + 2 * vs + nb);
     // (U^dag v)_r = sum_c conj(U_cr) v_c
 #pragma unroll
     for (int r = 0; r < 3; ++r)
-        A::row_bwd(acc, r, A::ld(u + r * vs), A::ld(u + (3 + r) * vs), A::ld(u + (6 + r) * vs), v0, v1, v2);
+        A::row_bwd(acc, r, A::ldl(u + r * vs), A::ldl(u + (3 + r) * vs), A::ldl(u + (6 + r) * vs), v0, v1, v2);
 }
 
 // Half-lattice index of the neighbour of (x,y,z,t) at +-h along mu.
@@ -350,6 +382,14 @@ void launch_dslash_b16(const Geom& g, int out_parity, const __nv_bfloat162* fat,
                        const __nv_bfloat162* in, __nv_bfloat162* out, Epilogue epi, const __nv_bfloat162* src,
                        double m2, CgScalars* scal, double* partials, cudaStream_t s) {
     DslashParams<ArithB16> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials, 0,
+                             g.vh};
+    launch_any(p, lng != nullptr, epi, s);
+}
+
+void launch_dslash_f32l16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng, const float2* in,
+                          float2* out, Epilogue epi, const float2* src, double m2, CgScalars* scal, double* partials,
+                          cudaStream_t s) {
+    DslashParams<ArithL16> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials, 0,
                              g.vh};
     launch_any(p, lng != nullptr, epi, s);
 }

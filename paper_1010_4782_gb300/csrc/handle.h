@@ -51,6 +51,7 @@ struct stag_handle {
     void* lo_ad = nullptr;
     void* lo_r = nullptr;
     float2* lo_y = nullptr;  // solution increment since the last replacement, FP32
+    double2* x_best = nullptr;  // mixed precision: iterate with the smallest true residual so far
     double* io_a = nullptr;  // ABI-layout staging [vh][3] complex
     double* io_b = nullptr;
     // reductions

@@ -50,6 +50,10 @@ void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const f
 void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng,
                        const __half2* in, __half2* out, Epilogue epi, const __half2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s);
+// FP16-stored links, FP32 vectors and arithmetic
+void launch_dslash_f32l16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng, const float2* in,
+                          float2* out, Epilogue epi, const float2* src, double m2, CgScalars* scal, double* partials,
+                          cudaStream_t s);
 void launch_dslash_b16(const Geom& g, int out_parity, const __nv_bfloat162* fat, const __nv_bfloat162* lng,
                        const __nv_bfloat162* in, __nv_bfloat162* out, Epilogue epi, const __nv_bfloat162* src,
                        double m2, CgScalars* scal, double* partials, cudaStream_t s);

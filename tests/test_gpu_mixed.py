@@ -104,7 +104,8 @@ CASES = [((4, 4, 4, 4), False, 0.1, 1),     # the config-1 system
 
 
 @pytest.mark.parametrize("arith", [binding.STAG_ARITH_FF, binding.STAG_ARITH_F64])
-@pytest.mark.parametrize("inner", [binding.STAG_INNER_F32, binding.STAG_INNER_F16, binding.STAG_INNER_BF16])
+@pytest.mark.parametrize("inner", [binding.STAG_INNER_F32, binding.STAG_INNER_F16, binding.STAG_INNER_BF16,
+                                   binding.STAG_INNER_F32_L16])
 @pytest.mark.parametrize("case", CASES)
 def test_mixed_solve(case, inner, arith):
     dims, naik, mass, seed = case
@@ -125,17 +126,22 @@ def test_mixed_solve(case, inner, arith):
 
 
 def test_mixed_fp32_iteration_count_close_to_fp64():
+    """FP32 vectors cost at most 30 % more iterations than FP64-class CG with FP32
+    links, and at most 50 % more with FP16-stored links: rounding the links to FP16
+    (2^-11 relative) perturbs the inner operator by ~5e-4, so each inner cycle
+    gets less far before its residual is replaced (measured: +33 % on this system)."""
     dims, mass = (8, 8, 8, 16), 0.05
     fat, lng = _fields(dims, True, 11)
     b = _dev(inputs.gaussian_even_source(dims, 0))
     its = {}
-    for inner in (binding.STAG_INNER_NONE, binding.STAG_INNER_F32):
+    for inner in (binding.STAG_INNER_NONE, binding.STAG_INNER_F32, binding.STAG_INNER_F32_L16):
         with _handle(fat, lng, dims, mass, inner=inner) as h:
             x = torch.zeros_like(b)
             code, info = binding.stag_cg_solve(h.h, b, x, 1e-10)
             assert code == binding.STAG_OK
             its[inner] = info["iters"]
     assert its[binding.STAG_INNER_F32] <= 1.3 * its[binding.STAG_INNER_NONE]
+    assert its[binding.STAG_INNER_F32_L16] <= 1.5 * its[binding.STAG_INNER_NONE], its
 
 
 def test_mixed_rejects_bad_options():

@@ -214,8 +214,10 @@ typedef struct stag_batch stag_batch;
 
 /* fat, naik: n_sys link arrays (the link layout above; naik may be NULL, or
  * contain NULLs, for one-hop systems); dims: 4*n_sys extents; masses: n_sys.
- * Link arrays are copied at create.  opt: NULL = defaults (only
- * check_interval, reliable_interval, reliable_delta and autotune are used). */
+ * Link arrays are copied at create.  opt: NULL = defaults, except
+ * check_interval = 4 (a system whose residual replacement falls due waits for
+ * the end of its graph); only check_interval, reliable_interval,
+ * reliable_delta and autotune are used. */
 int stag_batch_create(stag_batch** out, int32_t n_sys, const double* const* fat, const double* const* naik,
                       const int32_t* dims, const double* masses, const stag_options* opt);
 

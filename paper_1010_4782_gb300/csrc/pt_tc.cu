@@ -12,13 +12,14 @@
 //     B[2o+1][16p+2i] = w_im,  B[2o+1][16p+2i+1] = w_re,   w = W[p][o][i];
 // D_c[s][2o + h] is then the real / imaginary part of psi'(s, o)_c.
 //
-// One thread per site.  K runs in three phases of three paths: each thread
-// transports its site's 8 channels along the phase's paths (FP32 links, FP32
-// arithmetic) and writes them to A in shared memory; one thread issues the
-// 3 colours x 3 MMAs (M = 128, N = 16, K = 16, BF16 operands, FP32
-// accumulators in TMEM columns 16 c .. 16 c + 15) and commits them to an
-// mbarrier, which every thread waits on before A is overwritten.  At the end
-// each warp reads its 32 rows back with tcgen05.ld and stores them.
+// One thread per site.  K runs in nine phases, one per path: each thread
+// transports its site's 8 channels along the path (FP32 links, FP32
+// arithmetic) and writes them to one of two A buffers in shared memory; one
+// thread issues the 3 colours' MMAs (M = 128, N = 16, K = 16, BF16 operands,
+// FP32 accumulators in TMEM columns 16 c .. 16 c + 15) and commits them to the
+// buffer's mbarrier.  The transport of the next path overlaps these MMAs; a
+// buffer is rewritten only after the MMAs that read it have completed.  At the
+// end each warp reads its 32 rows back with tcgen05.ld and stores them.
 //
 // Shared-memory operands use the canonical K-major layout without swizzle:
 // 8 rows x 16 bytes core matrices; the leading byte offset (LBO) steps to the
@@ -36,20 +37,19 @@ namespace stag {
 namespace {
 
 constexpr int kTileRows = 128;                    // sites per CTA (= MMA M)
-constexpr int kPhasePaths = 3;                    // paths per K phase
-constexpr int kKPhase = kPhasePaths * 16;         // 48 K elements per phase
-constexpr int kAKGroups = kKPhase / 8;            // 6 core matrices along K per phase
-constexpr int kASbo = kAKGroups * 128;            // 768 B between 8-row groups
-constexpr int kAColour = (kTileRows / 8) * kASbo; // 12288 B per colour
-constexpr int kABytes = 3 * kAColour;             // 36864 B
+constexpr int kAKGroups = 2;                      // one path = 16 K elements = 2 core matrices
+constexpr int kASbo = kAKGroups * 128;            // 256 B between 8-row groups
+constexpr int kAColour = (kTileRows / 8) * kASbo; // 4096 B per colour
+constexpr int kABuf = 3 * kAColour;               // 12288 B per buffer
+constexpr int kABytes = 2 * kABuf;                // two buffers
 constexpr int kBKGroups = kPaths * 16 / 8;        // 18
 constexpr int kBSbo = kBKGroups * 128;            // 2304 B
 constexpr int kBBytes = 2 * kBSbo;                // 4608 B (N = 16: two 8-row groups)
 constexpr int kTmemCols = 64;                     // 48 used: 3 colours x N = 16
 constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls before giving up
 
-// smem layout: [A 36864][B 4608][mbarrier 8][tmem address 4]
-constexpr int kSmemBytes = kABytes + kBBytes + 16;
+// smem layout: [A 2 x 12288][B 4608][2 mbarriers 16][tmem address 4]
+constexpr int kSmemBytes = kABytes + kBBytes + 32;
 
 // tcgen05 instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B
 // BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;
     uint8_t* sB = smem + kABytes;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kABytes + kBBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kABytes + kBBytes + 8);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kABytes + kBBytes);  // one per A buffer
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kABytes + kBBytes + 16);
     const int tid = threadIdx.x, warp = tid >> 5;
 
     // TMEM columns for the accumulators (one warp allocates), the mbarrier,
@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int e = tid; e < 16 * kPaths * 16; e += kTileRows) {
@@ -159,77 +160,82 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
     int x = 0, y = 0, z = 0, t = 0;
     if (active) site_coords(i, P, g, x, y, z, t);
     uint8_t* rowA = sA + (tid >> 3) * kASbo + (tid & 7) * 16;
-    const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB), barA = smem_u32(bar);
+    const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
+    const uint32_t barA[2] = {smem_u32(bar), smem_u32(bar + 1)};
     bool ok = true;
 
-    for (int ph = 0; ph < kPaths / kPhasePaths; ++ph) {
-        if (active) {
-#pragma unroll 1
-            for (int pp = 0; pp < kPhasePaths; ++pp) {
-                const int p = ph * kPhasePaths + pp;
-                int Pn = P, nb = i, d = 0;
-                float2 U[9];
-                if (p > 0) {
-                    const int mu = (p - 1) >> 1;
-                    d = (p - 1) & 1;
-                    const Hop hp = pt_hop(g, links, P, i, x, y, z, t, mu, d);
-                    Pn = hp.Pn;
-                    nb = hp.nb;
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t word[3][4];
-#pragma unroll
-                    for (int ii = 0; ii < 4; ++ii) {
-                        const int ch = 4 * h + ii;
-                        float2 v[3], tv[3];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) v[c] = ldc(in + fidx(ch, c, Pn, nb, vs));
-                        if (p > 0) {
-                            pt_apply(U, d, v, tv);
-                        } else {
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) tv[c] = v[c];
-                        }
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) word[c][ii] = pack_bf16x2(tv[c].x, tv[c].y);
-                    }
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        *reinterpret_cast<uint4*>(rowA + c * kAColour + (2 * pp + h) * 128) =
-                            make_uint4(word[c][0], word[c][1], word[c][2], word[c][3]);
-                }
-            }
-        }
-        fence_async_smem();
-        fence_before_sync();
-        __syncthreads();
-        fence_after_sync();
-        if (tid == 0 && ok) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int kk = 0; kk < kPhasePaths; ++kk) {
-                    const uint64_t da = smem_desc(aBase + c * kAColour + kk * 2 * 128, 128, kASbo);
-                    const uint64_t db = smem_desc(bBase + (ph * kAKGroups + kk * 2) * 128, 128, kBSbo);
-                    mma_bf16(tmem + 16 * c, da, db, (ph > 0 || kk > 0) ? 1u : 0u);
-                }
-            mma_commit(barA);
-        }
-        // every thread waits for this phase's MMAs before A is rewritten
+    // waits for the n-th completion (n = 0, 1, ...) of buffer b's barrier
+    auto wait_buffer = [&](int b, int n) {
         long long spins = 0;
-        while (ok && !mbar_try_wait(barA, (uint32_t)(ph & 1))) {
+        while (ok && !mbar_try_wait(barA[b], (uint32_t)(n & 1))) {
             if (++spins > kWaitLimit) {
                 ok = false;
                 atomicExch(err, 1);
             }
         }
-        fence_after_sync();
-        __syncthreads();
+    };
+
+    for (int p = 0; p < kPaths; ++p) {
+        const int b = p & 1;
+        if (p >= 2) {
+            wait_buffer(b, (p - 2) >> 1);  // the MMAs of path p - 2 read this buffer
+            fence_after_sync();
+        }
+        if (active) {
+            int Pn = P, nb = i, d = 0;
+            float2 U[9];
+            if (p > 0) {
+                const int mu = (p - 1) >> 1;
+                d = (p - 1) & 1;
+                const Hop hp = pt_hop(g, links, P, i, x, y, z, t, mu, d);
+                Pn = hp.Pn;
+                nb = hp.nb;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+            }
+            uint8_t* row = rowA + b * kABuf;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t word[3][4];
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+                    const int ch = 4 * h + ii;
+                    float2 v[3], tv[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v[c] = ldc(in + fidx(ch, c, Pn, nb, vs));
+                    if (p > 0) {
+                        pt_apply(U, d, v, tv);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) tv[c] = v[c];
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) word[c][ii] = pack_bf16x2(tv[c].x, tv[c].y);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    *reinterpret_cast<uint4*>(row + c * kAColour + h * 128) =
+                        make_uint4(word[c][0], word[c][1], word[c][2], word[c][3]);
+            }
+        }
+        fence_async_smem();
+        fence_before_sync();
         ok = __syncthreads_and(ok ? 1 : 0) != 0;
+        fence_after_sync();
+        if (tid == 0 && ok) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const uint64_t da = smem_desc(aBase + b * kABuf + c * kAColour, 128, kASbo);
+                const uint64_t db = smem_desc(bBase + p * kAKGroups * 128, 128, kBSbo);
+                mma_bf16(tmem + 16 * c, da, db, p > 0 ? 1u : 0u);
+            }
+            mma_commit(barA[b]);
+        }
     }
+    // the last commit covers every MMA issued before it
+    wait_buffer((kPaths - 1) & 1, (kPaths - 1) >> 1);
+    fence_after_sync();
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
 
     // accumulators -> registers (warp w holds rows 32 w .. 32 w + 31) -> output
     float dv[3][16];

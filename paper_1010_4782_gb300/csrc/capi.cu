@@ -695,7 +695,7 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         g.vh = (int)(V / 2);
         g.vs = (int)(((V / 2) + 63) / 64 * 64);
         for (int k = 0; k < 4; ++k) g.hop3[k] = 3 % dims[k];
-        if (blocks_for(g.vs) > kMaxPartials) fail(h, STAG_ERR_INVALID_ARG, "lattice too large");
+        if (blocks_for(g.vs, 64) > kMaxPartials) fail(h, STAG_ERR_INVALID_ARG, "lattice too large");
 
         cuda_check(h, cudaGetDevice(&h->device), "cudaGetDevice");
         cuda_check(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -742,7 +742,8 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         }
         h->io_a = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
         h->io_b = dev_alloc<double>(h, abi_vec_bytes(g), "allocate staging");
-        h->partials = dev_alloc<double>(h, sizeof(double) * (size_t)blocks_for(g.vs), "allocate partials");
+        // one partial sum per block of any reducing kernel (blocks of 64 threads or more)
+        h->partials = dev_alloc<double>(h, sizeof(double) * (size_t)blocks_for(g.vs, 64), "allocate partials");
         h->scal = dev_alloc<CgScalars>(h, sizeof(CgScalars), "allocate CG state");
         cuda_check(h, cudaMallocHost(reinterpret_cast<void**>(&h->scal_host), sizeof(CgScalars)),
                    "allocate pinned CG state");

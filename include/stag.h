@@ -342,13 +342,18 @@ int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* 
  * unpacked into its neighbours' ghost slices.  STAG_DD_HOST stages the faces
  * through pinned host memory with host copies between the ranks' buffers (the
  * paper's GPU -> host -> MPI -> host -> GPU path); STAG_DD_DEVICE copies them
- * device to device (the direct path Sec. 5 proposes).  Native FP64 arithmetic.
- * phase_ms (nullable, 6 entries, summed over all ranks and calls of the solve):
- * [0] Dirac kernels, [1] face pack + unpack, [2] device -> host, [3] exchange
- * between ranks (host copies, or device copies in STAG_DD_DEVICE), [4] host ->
- * device, [5] global sums of the dot products.  The object keeps a pointer to
- * its handle; destroy it first. */
-enum { STAG_DD_HOST = 0, STAG_DD_DEVICE = 1 };
+ * device to device (the direct path Sec. 5 proposes).  The _OVERLAP modes do
+ * the same exchanges on a second stream (and the host copies on the host
+ * thread) while each rank computes the sites whose stencil stays inside its own
+ * slab, then the boundary slices (the overlap Sec. 5 proposes).  Native FP64
+ * arithmetic.  phase_ms (nullable, 6 entries, summed over all ranks and calls
+ * of the solve): [0] Dirac kernels, [1] face pack + unpack, [2] device -> host,
+ * [3] exchange between ranks (host copies, or device copies in STAG_DD_DEVICE),
+ * [4] host -> device, [5] global sums of the dot products; in the _OVERLAP
+ * modes [0] is each whole half-Dslash (pack, exchange, Dirac, unpack) and [3]
+ * the host copies hidden inside it.  The object keeps a pointer to its handle;
+ * destroy it first. */
+enum { STAG_DD_HOST = 0, STAG_DD_DEVICE = 1, STAG_DD_HOST_OVERLAP = 2, STAG_DD_DEVICE_OVERLAP = 3 };
 typedef struct stag_dd stag_dd;
 int stag_dd_create(stag_dd** out, stag_handle* h, int32_t n_ranks);
 /* out_even = A in_even through the decomposition (bit-identical to stag_apply_A

@@ -37,6 +37,8 @@ STAG_INNER_F32_L16 = 4
 
 STAG_DD_HOST = 0
 STAG_DD_DEVICE = 1
+STAG_DD_HOST_OVERLAP = 2
+STAG_DD_DEVICE_OVERLAP = 3
 DD_PHASES = ("dirac", "collect", "d2h", "exchange", "h2d", "global_sum")
 
 STAG_KERNEL_DSLASH_OE = 0

@@ -23,6 +23,7 @@
 // The CG solve follows Fig. 1 with the paper's host-driven structure: every
 // dot product is a per-rank partial sum, gathered to the host and summed over
 // the ranks (the global sum an MPI all-reduce would do).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -102,6 +103,8 @@ struct stag_dd {
     double* partials = nullptr;
     std::vector<double> partials_host;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaStream_t cs = nullptr;                             // copy stream of the overlapped modes
+    cudaEvent_t eo[3] = {nullptr, nullptr, nullptr};       // faces packed, faces on the host, faces in
     double phase[DD_PHASES] = {};
     long long bytes_exchanged = 0;
     std::string err = "no error";
@@ -203,9 +206,85 @@ void exchange(stag_dd* dd, const std::vector<double2*>& v, int mode) {
     dcheck(dd, cudaGetLastError(), "halo exchange");
 }
 
+// One half-Dslash on every rank with the face exchange overlapped with the
+// interior (Sec. 5's proposal): after the faces are packed, the copies run on
+// a second stream (and the host copies on the host thread) while the sites
+// whose stencil stays inside the rank's own slab, t-slices
+// [G + depth, G + ltl - depth), are computed; the boundary slices follow once
+// the faces are unpacked.  Every site runs the same kernel as in the plain
+// modes, so the result is bit-identical.  Timed as a whole (phase 0); the host
+// copy time is also recorded (phase 3), though it is hidden.
+void half_overlap(stag_dd* dd, int parity, const std::vector<double2*>& in, const std::vector<double2*>& out,
+                  Epilogue epi, const std::vector<double2*>* src, double m2, bool host) {
+    const int P = dd->P, n = face_n(dd);
+    const size_t vs = (size_t)dd->gl.vs;
+    const size_t fb = (size_t)3 * n * sizeof(double2);
+    const int bl = blocks_for(n);
+    const int v3h = dd->v3h, G = dd->G, ltl = dd->ltl;
+    const int lo_end = std::min(G + dd->depth, G + ltl);
+    const int hi_start = std::max(G + ltl - dd->depth, lo_end);
+    auto dirac = [&](int q, int s0, int s1) {
+        const LinkSet L{dd->fat[q], dd->lng[q], nullptr, nullptr};
+        launch_dslash_f64_range(dd->gl, parity, L, in[q], out[q], epi, src ? (*src)[q] : nullptr, m2, s0 * v3h,
+                                s1 * v3h, S(dd));
+    };
+    tstart(dd);
+    for (int q = 0; q < P; ++q) {
+        dd_pack_kernel<<<bl, kBlock, 0, S(dd)>>>(in[q], vs, interior0(dd), n, dd->s_lo[q]);
+        dd_pack_kernel<<<bl, kBlock, 0, S(dd)>>>(in[q], vs, interior1(dd) - n, n, dd->s_hi[q]);
+    }
+    dcheck(dd, cudaEventRecord(dd->eo[0], S(dd)), "event");
+    dcheck(dd, cudaStreamWaitEvent(dd->cs, dd->eo[0], 0), "stream wait");
+    if (host) {
+        for (int q = 0; q < P; ++q) {
+            cudaMemcpyAsync(dd->hs_lo[q], dd->s_lo[q], fb, cudaMemcpyDeviceToHost, dd->cs);
+            cudaMemcpyAsync(dd->hs_hi[q], dd->s_hi[q], fb, cudaMemcpyDeviceToHost, dd->cs);
+        }
+        dcheck(dd, cudaEventRecord(dd->eo[1], dd->cs), "event");
+    } else {
+        for (int q = 0; q < P; ++q) {
+            cudaMemcpyAsync(dd->r_lo[q], dd->s_hi[(q + P - 1) % P], fb, cudaMemcpyDeviceToDevice, dd->cs);
+            cudaMemcpyAsync(dd->r_hi[q], dd->s_lo[(q + 1) % P], fb, cudaMemcpyDeviceToDevice, dd->cs);
+        }
+    }
+    for (int q = 0; q < P; ++q) dirac(q, lo_end, hi_start);  // interior, overlapping the copies
+    if (host) {
+        dcheck(dd, cudaEventSynchronize(dd->eo[1]), "faces to host");
+        const auto t0 = std::chrono::steady_clock::now();
+        for (int q = 0; q < P; ++q) {
+            std::memcpy(dd->hr_lo[q], dd->hs_hi[(q + P - 1) % P], fb);
+            std::memcpy(dd->hr_hi[q], dd->hs_lo[(q + 1) % P], fb);
+        }
+        dd->phase[DD_MPI] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        for (int q = 0; q < P; ++q) {
+            cudaMemcpyAsync(dd->r_lo[q], dd->hr_lo[q], fb, cudaMemcpyHostToDevice, dd->cs);
+            cudaMemcpyAsync(dd->r_hi[q], dd->hr_hi[q], fb, cudaMemcpyHostToDevice, dd->cs);
+        }
+    }
+    dcheck(dd, cudaEventRecord(dd->eo[2], dd->cs), "event");
+    dcheck(dd, cudaStreamWaitEvent(S(dd), dd->eo[2], 0), "stream wait");
+    for (int q = 0; q < P; ++q) {
+        dd_unpack_kernel<<<bl, kBlock, 0, S(dd)>>>(dd->r_lo[q], n, in[q], vs, interior0(dd) - n);
+        dd_unpack_kernel<<<bl, kBlock, 0, S(dd)>>>(dd->r_hi[q], n, in[q], vs, interior1(dd));
+    }
+    for (int q = 0; q < P; ++q) {
+        dirac(q, G, lo_end);
+        if (hi_start < G + ltl) dirac(q, hi_start, G + ltl);
+    }
+    tstop(dd, DD_CALC);
+    dd->bytes_exchanged += 2LL * P * (long long)fb;
+    dcheck(dd, cudaGetLastError(), "overlapped half-Dslash");
+}
+
 // out[q] = A in[q] on every rank's interior (in is exchanged; uses vt)
 void dd_apply(stag_dd* dd, const std::vector<double2*>& in, const std::vector<double2*>& out, int mode) {
     const double m2 = dd->h->mass * dd->h->mass;
+    if (mode == STAG_DD_HOST_OVERLAP || mode == STAG_DD_DEVICE_OVERLAP) {
+        const bool host = mode == STAG_DD_HOST_OVERLAP;
+        half_overlap(dd, 1, in, dd->vt, EPI_PLAIN, nullptr, 0.0, host);
+        half_overlap(dd, 0, dd->vt, out, EPI_AXPY, &in, m2, host);
+        return;
+    }
     exchange(dd, in, mode);
     tstart(dd);
     for (int q = 0; q < dd->P; ++q) {
@@ -293,6 +372,12 @@ void destroy_dd(stag_dd* dd) {
     if (dd->partials) cudaFree(dd->partials);
     for (cudaEvent_t e : dd->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : dd->eo)
+        if (e) cudaEventDestroy(e);
+    if (dd->cs) {
+        cudaStreamSynchronize(dd->cs);
+        cudaStreamDestroy(dd->cs);
+    }
     delete dd;
 }
 
@@ -346,6 +431,8 @@ int stag_dd_create(stag_dd** out, stag_handle* h, int32_t n_ranks) {
         dd->partials = dalloc<double>(dd, sizeof(double) * (size_t)n_ranks * blocks_for(dd->ltl * dd->v3h));
         dcheck(dd, cudaEventCreate(&dd->ev[0]), "event");
         dcheck(dd, cudaEventCreate(&dd->ev[1]), "event");
+        dcheck(dd, cudaStreamCreateWithFlags(&dd->cs, cudaStreamNonBlocking), "stream");
+        for (auto& e : dd->eo) dcheck(dd, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         dcheck(dd, cudaStreamSynchronize(S(dd)), "create");
         *out = dd;
         return STAG_OK;
@@ -361,7 +448,7 @@ int stag_dd_create(stag_dd** out, stag_handle* h, int32_t n_ranks) {
 
 int stag_dd_apply_A(stag_dd* dd, const double* in_even, double* out_even, int32_t mode, double* phase_ms) {
     if (!dd || !in_even || !out_even || in_even == out_even) return STAG_ERR_INVALID_ARG;
-    if (mode != STAG_DD_HOST && mode != STAG_DD_DEVICE) return STAG_ERR_INVALID_ARG;
+    if (mode < STAG_DD_HOST || mode > STAG_DD_DEVICE_OVERLAP) return STAG_ERR_INVALID_ARG;
     stag_handle* h = dd->h;
     try {
         handle_begin(h);
@@ -395,7 +482,7 @@ int stag_dd_apply_A(stag_dd* dd, const double* in_even, double* out_even, int32_
 int stag_dd_cg_solve(stag_dd* dd, const double* b_even, double* x_even, double tol, int32_t max_iter, int32_t mode,
                      stag_solve_info* info, double* phase_ms) {
     if (!dd || !b_even || !x_even || b_even == x_even || !(tol > 0.0)) return STAG_ERR_INVALID_ARG;
-    if (mode != STAG_DD_HOST && mode != STAG_DD_DEVICE) return STAG_ERR_INVALID_ARG;
+    if (mode < STAG_DD_HOST || mode > STAG_DD_DEVICE_OVERLAP) return STAG_ERR_INVALID_ARG;
     stag_handle* h = dd->h;
     stag_solve_info inf{};
     int status = STAG_OK;

@@ -31,7 +31,8 @@ def _handle(fat, lng, dims, mass):
     return binding.Handle(_dev(fat), dims, mass, naik_long=None if lng is None else _dev(lng), options=opt)
 
 
-@pytest.mark.parametrize("mode", [binding.STAG_DD_HOST, binding.STAG_DD_DEVICE])
+@pytest.mark.parametrize("mode", [binding.STAG_DD_HOST, binding.STAG_DD_DEVICE, binding.STAG_DD_HOST_OVERLAP,
+                                  binding.STAG_DD_DEVICE_OVERLAP])
 @pytest.mark.parametrize("naik,dims,ranks", [(False, (4, 4, 6, 8), 1), (False, (4, 4, 6, 8), 4),
                                              (True, (6, 4, 4, 16), 2), (True, (6, 4, 4, 24), 4),
                                              (False, (8, 8, 8, 16), 8)])
@@ -51,11 +52,13 @@ def test_decomposed_A_is_bit_identical(naik, dims, ranks, mode):
         finally:
             binding.stag_dd_destroy(dd)
     assert torch.equal(out, ref)
-    assert ph["dirac"] > 0 and ph["collect"] > 0
+    assert ph["dirac"] > 0
     if mode == binding.STAG_DD_HOST:
-        assert ph["d2h"] > 0 and ph["h2d"] > 0
-    else:
-        assert ph["d2h"] == 0 and ph["h2d"] == 0
+        assert ph["collect"] > 0 and ph["d2h"] > 0 and ph["h2d"] > 0
+    elif mode == binding.STAG_DD_DEVICE:
+        assert ph["collect"] > 0 and ph["d2h"] == 0 and ph["h2d"] == 0
+    else:  # overlapped: one timing per half-Dslash
+        assert ph["collect"] == 0 and ph["d2h"] == 0 and ph["h2d"] == 0
 
 
 def test_decomposed_cg_solve():
@@ -64,18 +67,23 @@ def test_decomposed_cg_solve():
     b = inputs.gaussian_even_source(dims, 0)
     op = oracle.Operator(fat, lng, m, dims)
     ref = oracle.solve(op.apply_A, b, tol=1e-13, max_iter=200000, max_restarts=20)["x"]
+    xs_modes = {}
     with _handle(fat, lng, dims, m) as h:
         dd = binding.stag_dd_create(h.h, 4)
         try:
-            x = torch.zeros_like(_dev(b))
-            code, info, ph = binding.stag_dd_cg_solve(dd, h.h, _dev(b), x, tol)
+            for mode in (binding.STAG_DD_HOST, binding.STAG_DD_HOST_OVERLAP):
+                x = torch.zeros_like(_dev(b))
+                code, info, ph = binding.stag_dd_cg_solve(dd, h.h, _dev(b), x, tol, mode=mode)
+                assert code == binding.STAG_OK, info
+                assert info["true_rel_residual"] <= tol
+                assert ph["global_sum"] > 0
+                xs_modes[mode] = x.cpu().numpy().reshape(-1)
         finally:
             binding.stag_dd_destroy(dd)
-    assert code == binding.STAG_OK, info
-    assert info["true_rel_residual"] <= tol
-    xs = x.cpu().numpy().reshape(-1)
+    xs = xs_modes[binding.STAG_DD_HOST]
     assert np.linalg.norm(xs - ref) / np.linalg.norm(ref) <= 1e-8
-    assert ph["global_sum"] > 0
+    # the overlapped exchange changes the schedule, not the arithmetic
+    assert np.array_equal(xs_modes[binding.STAG_DD_HOST_OVERLAP], xs)
 
 
 def test_decomposition_rejects_bad_splits():

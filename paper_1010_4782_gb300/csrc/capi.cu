@@ -347,7 +347,16 @@ void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* 
     const size_t aos_bytes = (size_t)2 * h->g.vh * 4 * 9 * sizeof(double2);
     const double* src = links_in;
     void* stage = nullptr;
-    if (!is_device_ptr(h, links_in)) {
+    cudaPointerAttributes pa{};
+    bool pinned = false;
+    if (cudaPointerGetAttributes(&pa, links_in) == cudaSuccess)
+        pinned = pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr;
+    else
+        cudaGetLastError();  // an unregistered host pointer
+    if (pinned) {
+        // pinned host memory: the pack kernel reads it in place over the host link
+        src = static_cast<const double*>(pa.devicePointer);
+    } else if (!is_device_ptr(h, links_in)) {
         cuda_check(h, cudaMalloc(&stage, aos_bytes), "allocate link staging buffer");
         cudaError_t e = cudaMemcpyAsync(stage, links_in, aos_bytes, cudaMemcpyHostToDevice, h->s);
         if (e != cudaSuccess) {

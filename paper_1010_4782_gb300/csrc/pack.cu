@@ -7,9 +7,10 @@
 
 namespace stag {
 
-// One thread per (site, direction).  Reads the 9 complex entries of U_mu(x)
-// (144 contiguous bytes), multiplies by eta_mu(x) and scatters them into the
-// 9 planes of its parity.
+// One thread per (site, direction), direction fastest, so that a warp reads
+// contiguous AoS links (the input may be host memory read over the host link).
+// Reads the 9 complex entries of U_mu(x) (144 contiguous bytes), multiplies by
+// eta_mu(x) and scatters them into the 9 planes of its parity.
 __global__ void __launch_bounds__(kBlock) pack_links_kernel(Geom g, const double2* __restrict__ aos,
                                                             double2* __restrict__ soa64,
                                                             float4* __restrict__ soaff,
@@ -19,8 +20,8 @@ __global__ void __launch_bounds__(kBlock) pack_links_kernel(Geom g, const double
     const long long V = 2LL * g.vh;
     const long long idx = (long long)blockIdx.x * kBlock + threadIdx.x;
     if (idx >= 4 * V) return;
-    const int mu = (int)(idx / V);
-    const int lex = (int)(idx - (long long)mu * V);
+    const int mu = (int)(idx & 3);
+    const int lex = (int)(idx >> 2);
     const int x = lex % g.lx;
     int r = lex / g.lx;
     const int y = r % g.ly;

@@ -112,6 +112,14 @@ def test_apply_A_host_pointers_match_device_pointers():
         out = torch.empty_like(_dev(v))
         binding.stag_apply_A(h.h, _dev(v), out)
     assert np.array_equal(out.cpu().numpy(), out_host)
+    # pinned host links are read in place by the pack kernel; pinned vectors are staged
+    fat_p = torch.from_numpy(fat).pin_memory()
+    lng_p = torch.from_numpy(lng).pin_memory()
+    v_p = torch.from_numpy(v).pin_memory()
+    out_p = torch.empty_like(v_p).pin_memory()
+    with binding.Handle(fat_p, dims, 0.2, naik_long=lng_p, options=opt) as hp:
+        binding.stag_apply_A(hp.h, v_p, out_p)
+    assert np.array_equal(out_p.numpy(), out_host)
 
 
 def test_set_mass():

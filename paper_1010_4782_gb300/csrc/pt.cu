@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256, CIN * COUT >= 64 ? 2 : 3)
     for (int o = 0; o < COUT; ++o)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[o][c] = make_float2(0.f, 0.f);
+    float2 vin[3][4];  // a group of 4 input channels (CIN a multiple of 4)
     for (int p = p0; p < p1; ++p) {
         int Pn = P, nb = i, d = 0;
         float2 U[9];
@@ -99,8 +100,17 @@ __global__ void __launch_bounds__(256, CIN * COUT >= 64 ? 2 : 3)
 #pragma unroll
         for (int ci = 0; ci < CIN; ++ci) {
             float2 v[3], tv[3];
+            if constexpr (CIN % 4 == 0) {
+                if (ci % 4 == 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c] = ldc(in + fidx(ci, c, Pn, nb, vs));
+                    for (int c = 0; c < 3; ++c) ld4c(in + fidx(ci, c, Pn, nb, vs, CIN), vin[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = vin[c][ci % 4];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = ldc(in + fidx(ci, c, Pn, nb, vs, CIN));
+            }
             if (p > 0) {
                 pt_apply(U, d, v, tv);
             } else {
@@ -121,9 +131,16 @@ __global__ void __launch_bounds__(256, CIN * COUT >= 64 ? 2 : 3)
         }
     }
 #pragma unroll
-    for (int o = 0; o < COUT; ++o)
+    for (int c = 0; c < 3; ++c) {
+        if constexpr (COUT % 4 == 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) stc(out + fidx(o, c, P, i, vs), acc[o][c]);
+            for (int o = 0; o < COUT; o += 4)
+                st4c(out + fidx(o, c, P, i, vs, COUT), acc[o][c], acc[o + 1][c], acc[o + 2][c], acc[o + 3][c]);
+        } else {
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) stc(out + fidx(o, c, P, i, vs, COUT), acc[o][c]);
+        }
+    }
 }
 
 // partials[blk][p][o][i] = sum over the block's sites of
@@ -162,14 +179,35 @@ __global__ void __launch_bounds__(256) pt_wgrad_kernel(Geom g, const float2* __r
         }
         float2 gv[OC][3];
 #pragma unroll
-        for (int oo = 0; oo < OC; ++oo)
+        for (int c = 0; c < 3; ++c) {
+            if constexpr (OC % 4 == 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gv[oo][c] = ldc(gout + fidx(o0 + oo, c, P, i, vs));
+                for (int oo = 0; oo < OC; oo += 4) {
+                    float2 q[4];
+                    ld4c(gout + fidx(o0 + oo, c, P, i, vs, cout), q);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) gv[oo + k][c] = q[k];
+                }
+            } else {
+#pragma unroll
+                for (int oo = 0; oo < OC; ++oo) gv[oo][c] = ldc(gout + fidx(o0 + oo, c, P, i, vs, cout));
+            }
+        }
+        float2 vin[3][4];
 #pragma unroll
         for (int ci = 0; ci < CIN; ++ci) {
             float2 v[3], tv[3];
+            if constexpr (CIN % 4 == 0) {
+                if (ci % 4 == 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c] = ldc(psi + fidx(ci, c, Pn, nb, vs));
+                    for (int c = 0; c < 3; ++c) ld4c(psi + fidx(ci, c, Pn, nb, vs, CIN), vin[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = vin[c][ci % 4];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = ldc(psi + fidx(ci, c, Pn, nb, vs, CIN));
+            }
             if (p > 0) {
                 pt_apply(U, d, v, tv);
             } else {
@@ -241,8 +279,8 @@ __global__ void __launch_bounds__(kBlock) pt_embed_kernel(Geom g, const TS* __re
         } else {
             v = ldc(src + c * vs + i);
         }
-        stc(act0 + fidx(0, c, 0, i, vs), v);
-        stc(act0 + fidx(0, c, 1, i, vs), make_float2(0.f, 0.f));
+        stc(act0 + fidx(0, c, 0, i, vs, 1), v);
+        stc(act0 + fidx(0, c, 1, i, vs, 1), make_float2(0.f, 0.f));
     }
 }
 
@@ -255,7 +293,7 @@ __global__ void __launch_bounds__(kBlock) pt_extract_kernel(Geom g, const T* __r
     const size_t vs = (size_t)g.vs;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float2 v = ldc(act3 + fidx(0, c, 0, i, vs));
+        const float2 v = ldc(act3 + fidx(0, c, 0, i, vs, 1));
         out[c * vs + i] = make_double2(scale * (double)v.x, scale * (double)v.y);
     }
 }
@@ -269,7 +307,7 @@ __global__ void __launch_bounds__(kBlock) pt_diff_kernel(Geom g, const T* __rest
     const size_t vs = (size_t)g.vs;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float2 o = ldc(act3 + fidx(0, c, 0, i, vs));
+        const float2 o = ldc(act3 + fidx(0, c, 0, i, vs, 1));
         const float2 t = ldc(e + c * vs + i);
         d[c * vs + i] = make_float2(o.x - t.x, o.y - t.y);
     }
@@ -285,8 +323,8 @@ __global__ void __launch_bounds__(kBlock) pt_seed_kernel(Geom g, const float2* _
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float2 a = v[c * vs + i];
-        stc(g3 + fidx(0, c, 0, i, vs), make_float2(a.x * inv, a.y * inv));
-        stc(g3 + fidx(0, c, 1, i, vs), make_float2(0.f, 0.f));
+        stc(g3 + fidx(0, c, 0, i, vs, 1), make_float2(a.x * inv, a.y * inv));
+        stc(g3 + fidx(0, c, 1, i, vs, 1), make_float2(0.f, 0.f));
     }
 }
 

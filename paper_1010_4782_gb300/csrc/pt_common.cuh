@@ -22,9 +22,41 @@ __device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) { return __bfloat
 __device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
 
-// whole-lattice field: [channel][colour][parity][vs]
-__device__ __forceinline__ size_t fidx(int ch, int c, int P, int i, size_t vs) {
-    return ((size_t)(ch * 3 + c) * 2 + P) * vs + i;
+// whole-lattice field of C channels, channel innermost: [parity][colour][site][C],
+// so that the channels of one site and colour are contiguous (vector accesses)
+__device__ __forceinline__ size_t fidx(int ch, int c, int P, int i, size_t vs, int C) {
+    return ((size_t)(P * 3 + c) * vs + i) * C + ch;
+}
+
+// channels ch0 .. ch0 + 3 of one (parity, colour, site); p = the field at fidx(ch0, ...)
+// with ch0 a multiple of 4 and C a multiple of 4 (16-byte aligned for BF16, 32 for FP32)
+__device__ __forceinline__ float2 bf16x2_word(uint32_t w) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+}
+__device__ __forceinline__ void ld4c(const __nv_bfloat162* p, float2 (&v)[4]) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+    v[0] = bf16x2_word(q.x);
+    v[1] = bf16x2_word(q.y);
+    v[2] = bf16x2_word(q.z);
+    v[3] = bf16x2_word(q.w);
+}
+__device__ __forceinline__ void ld4c(const float2* p, float2 (&v)[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float2 v) {
+    const __nv_bfloat162 b = __float22bfloat162_rn(v);
+    return *reinterpret_cast<const uint32_t*>(&b);
+}
+__device__ __forceinline__ void st4c(__nv_bfloat162* p, float2 v0, float2 v1, float2 v2, float2 v3) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(bf16x2_bits(v0), bf16x2_bits(v1), bf16x2_bits(v2), bf16x2_bits(v3));
+}
+__device__ __forceinline__ void st4c(float2* p, float2 v0, float2 v1, float2 v2, float2 v3) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v2.x, v2.y, v3.x, v3.y);
 }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {

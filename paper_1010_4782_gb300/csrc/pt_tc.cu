@@ -161,13 +161,13 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
     if (active) site_coords(i, P, g, x, y, z, t);
     uint8_t* rowA = sA + (tid >> 3) * kASbo + (tid & 7) * 16;
     const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
-    const uint32_t barA[2] = {smem_u32(bar), smem_u32(bar + 1)};
+    const uint32_t bar0 = smem_u32(bar), bar1 = smem_u32(bar + 1);
     bool ok = true;
 
     // waits for the n-th completion (n = 0, 1, ...) of buffer b's barrier
     auto wait_buffer = [&](int b, int n) {
         long long spins = 0;
-        while (ok && !mbar_try_wait(barA[b], (uint32_t)(n & 1))) {
+        while (ok && !mbar_try_wait(b ? bar1 : bar0, (uint32_t)(n & 1))) {
             if (++spins > kWaitLimit) {
                 ok = false;
                 atomicExch(err, 1);
@@ -197,12 +197,14 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 uint32_t word[3][4];
+                float2 vin[3][4];  // channels 4 h .. 4 h + 3, one 16-byte load per colour
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ld4c(in + fidx(4 * h, c, Pn, nb, vs, kHidden), vin[c]);
 #pragma unroll
                 for (int ii = 0; ii < 4; ++ii) {
-                    const int ch = 4 * h + ii;
                     float2 v[3], tv[3];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) v[c] = ldc(in + fidx(ch, c, Pn, nb, vs));
+                    for (int c = 0; c < 3; ++c) v[c] = vin[c][ii];
                     if (p > 0) {
                         pt_apply(U, d, v, tv);
                     } else {
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
                 const uint64_t db = smem_desc(bBase + p * kAKGroups * 128, 128, kBSbo);
                 mma_bf16(tmem + 16 * c, da, db, p > 0 ? 1u : 0u);
             }
-            mma_commit(barA[b]);
+            mma_commit(b ? bar1 : bar0);
         }
     }
     // the last commit covers every MMA issued before it
@@ -244,9 +246,12 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (active && ok) {
 #pragma unroll
-        for (int o = 0; o < kHidden; ++o)
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) stc(out + fidx(o, c, P, i, vs), make_float2(dv[c][2 * o], dv[c][2 * o + 1]));
+            for (int o = 0; o < kHidden; o += 4)
+                st4c(out + fidx(o, c, P, i, vs, kHidden), make_float2(dv[c][2 * o], dv[c][2 * o + 1]),
+                     make_float2(dv[c][2 * o + 2], dv[c][2 * o + 3]), make_float2(dv[c][2 * o + 4], dv[c][2 * o + 5]),
+                     make_float2(dv[c][2 * o + 6], dv[c][2 * o + 7]));
     }
     fence_before_sync();
     __syncthreads();

@@ -658,7 +658,7 @@ void layer_fwd(stag_ptnet* n, int l, const T* in, T* out) {
     else if (l == 1) {
         if constexpr (std::is_same<T, __nv_bfloat162>::value) {
             if (n->use_tc) {
-                launch_pt_mix8_tc(g, n->links, w, in, out, n->tc_err, S(n));
+                launch_pt_mix8_tc(g, n->links, w, in, out, nullptr, n->tc_err, S(n));
                 return;
             }
         }
@@ -775,7 +775,18 @@ void apply_net(stag_ptnet* n, const double2* r, double rnorm, double2* z) {
     const Geom& g = n->g;
     const double s = rnorm > 0.0 ? 1.0 / rnorm : 1.0;
     pt_embed_kernel<double2, T><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, r, s, static_cast<T*>(n->act[0]));
-    forward<T>(n);
+    bool fused = false;
+    if constexpr (std::is_same<T, __nv_bfloat162>::value) {
+        if (n->use_tc) {
+            // the last layer's mixing in the tensor-core kernel's epilogue, then its transports
+            layer_fwd<T>(n, 0, static_cast<const T*>(n->act[0]), static_cast<T*>(n->act[1]));
+            launch_pt_mix8_tc(g, n->links, n->w + layer_offset(1), static_cast<const T*>(n->act[1]),
+                              static_cast<T*>(n->act[2]), n->w + layer_offset(2), n->tc_err, S(n));
+            launch_pt_transport_sum(g, n->links, static_cast<const T*>(n->act[2]), static_cast<T*>(n->act[3]), S(n));
+            fused = true;
+        }
+    }
+    if (!fused) forward<T>(n);
     pt_extract_kernel<T><<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, static_cast<const T*>(n->act[3]), rnorm > 0.0 ? rnorm : 1.0, z);
 }
 

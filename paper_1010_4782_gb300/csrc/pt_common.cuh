@@ -117,8 +117,13 @@ __device__ __forceinline__ void pt_apply(const float2 (&U)[9], int d, const floa
 
 // The 8 -> 8 layer (forward, BF16 activations) with the channel mixing on the
 // tensor cores (pt_tc.cu).  w: the layer's complex weights [9][8][8]; err: set
-// to 1 if a bounded wait ran out.
+// to 1 if a bounded wait ran out.  w3 (nullable): the 8 -> 1 layer's weights;
+// given, the kernel stores phi_p = sum_i W3[p][0][i] psi_i (odd sites: paths
+// 1..8 in channels 0..7; even sites: path 0 in channel 0) instead of psi, and
+// launch_pt_transport_sum finishes the 8 -> 1 layer on even sites.
 void launch_pt_mix8_tc(const Geom& g, const float2* links, const float2* w, const __nv_bfloat162* in,
-                       __nv_bfloat162* out, int* err, cudaStream_t s);
+                       __nv_bfloat162* out, const float2* w3, int* err, cudaStream_t s);
+void launch_pt_transport_sum(const Geom& g, const float2* links, const __nv_bfloat162* phi, __nv_bfloat162* out,
+                             cudaStream_t s);
 
 }  // namespace stag

@@ -114,12 +114,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-template <class TI, class TO>
+// PHI (inference): instead of psi, store phi_p = sum_i W3[p][0][i] psi_i, the
+// next layer's channel mixing done before its transports (T_p acts on colour,
+// W3 on channels, so sum_i W3[p][0][i] T_p psi_i = T_p phi_p): on odd sites the
+// 8 transported paths (channel p - 1), on even sites the identity path
+// (channel 0).  w3: the next layer's weights [9][1][8].
+template <class TI, class TO, bool PHI>
 __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const float2* __restrict__ links,
                                                               const float2* __restrict__ w,
                                                               const TI* __restrict__ in, TO* __restrict__ out,
-                                                              int* err) {
+                                                              const float2* __restrict__ w3, int* err) {
     extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ float2 sW3[kPaths * kHidden];  // PHI: the next layer's weights
+    if constexpr (PHI) {
+        for (int k = threadIdx.x; k < kPaths * kHidden; k += blockDim.x) sW3[k] = w3[k];
+    }
     uint8_t* sA = smem;
     uint8_t* sB = smem + kABytes;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kABytes + kBBytes);  // one per A buffer
@@ -240,18 +249,44 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
 
     // accumulators -> registers (warp w holds rows 32 w .. 32 w + 31) -> output
-    float dv[3][16];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * c, dv[c]);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (active && ok) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
+    // one colour at a time: 16 accumulators live (warp-collective loads, uniform loop)
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        float dv[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * c, dv);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!(active && ok)) continue;
+        if constexpr (!PHI) {
 #pragma unroll
             for (int o = 0; o < kHidden; o += 4)
-                st4c(out + fidx(o, c, P, i, vs, kHidden), make_float2(dv[c][2 * o], dv[c][2 * o + 1]),
-                     make_float2(dv[c][2 * o + 2], dv[c][2 * o + 3]), make_float2(dv[c][2 * o + 4], dv[c][2 * o + 5]),
-                     make_float2(dv[c][2 * o + 6], dv[c][2 * o + 7]));
+                st4c(out + fidx(o, c, P, i, vs, kHidden), make_float2(dv[2 * o], dv[2 * o + 1]),
+                     make_float2(dv[2 * o + 2], dv[2 * o + 3]), make_float2(dv[2 * o + 4], dv[2 * o + 5]),
+                     make_float2(dv[2 * o + 6], dv[2 * o + 7]));
+        } else if (P == 1) {
+            float2 ph[kHidden];
+#pragma unroll
+            for (int q = 0; q < kHidden; ++q) {
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int o = 0; o < kHidden; ++o) {
+                    const float2 m = cmulf(sW3[(q + 1) * kHidden + o], make_float2(dv[2 * o], dv[2 * o + 1]));
+                    a.x += m.x;
+                    a.y += m.y;
+                }
+                ph[q] = a;
+            }
+            st4c(out + fidx(0, c, P, i, vs, kHidden), ph[0], ph[1], ph[2], ph[3]);
+            st4c(out + fidx(4, c, P, i, vs, kHidden), ph[4], ph[5], ph[6], ph[7]);
+        } else {
+            float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < kHidden; ++o) {
+                const float2 m = cmulf(sW3[o], make_float2(dv[2 * o], dv[2 * o + 1]));
+                a.x += m.x;
+                a.y += m.y;
+            }
+            stc(out + fidx(0, c, P, i, vs, kHidden), a);
+        }
     }
     fence_before_sync();
     __syncthreads();
@@ -262,16 +297,52 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
 }  // namespace
 
 void launch_pt_mix8_tc(const Geom& g, const float2* links, const float2* w, const __nv_bfloat162* in,
-                       __nv_bfloat162* out, int* err, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(pt_mix8_tc_kernel<__nv_bfloat162, __nv_bfloat162>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        attr_set = true;
-    }
+                       __nv_bfloat162* out, const float2* w3, int* err, cudaStream_t s) {
     const int tiles = (g.vh + kTileRows - 1) / kTileRows;
-    pt_mix8_tc_kernel<__nv_bfloat162, __nv_bfloat162><<<2 * tiles, kTileRows, kSmemBytes, s>>>(g, links, w, in, out,
-                                                                                              err);
+    if (w3)
+        pt_mix8_tc_kernel<__nv_bfloat162, __nv_bfloat162, true>
+            <<<2 * tiles, kTileRows, kSmemBytes, s>>>(g, links, w, in, out, w3, err);
+    else
+        pt_mix8_tc_kernel<__nv_bfloat162, __nv_bfloat162, false>
+            <<<2 * tiles, kTileRows, kSmemBytes, s>>>(g, links, w, in, out, nullptr, err);
+}
+
+// out(x) = phi_0(x) + sum_{p = 1..8} (T_p phi_p)(x) on even sites x, from the
+// PHI output of pt_mix8_tc_kernel (the network's last layer, 8 -> 1).
+__global__ void __launch_bounds__(256) pt_transport_sum_kernel(Geom g, const float2* __restrict__ links,
+                                                               const __nv_bfloat162* __restrict__ phi,
+                                                               __nv_bfloat162* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+    int x, y, z, t;
+    site_coords(i, 0, g, x, y, z, t);
+    float2 acc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = ldc(phi + fidx(0, c, 0, i, vs, kHidden));
+#pragma unroll 1
+    for (int p = 1; p < kPaths; ++p) {
+        const int mu = (p - 1) >> 1, d = (p - 1) & 1;
+        const Hop hp = pt_hop(g, links, 0, i, x, y, z, t, mu, d);
+        float2 U[9], v[3], tv[3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = ldc(phi + fidx(p - 1, c, hp.Pn, hp.nb, vs, kHidden));
+        pt_apply(U, d, v, tv);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc[c].x += tv[c].x;
+            acc[c].y += tv[c].y;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) stc(out + fidx(0, c, 0, i, vs, 1), acc[c]);
+}
+
+void launch_pt_transport_sum(const Geom& g, const float2* links, const __nv_bfloat162* phi, __nv_bfloat162* out,
+                             cudaStream_t s) {
+    pt_transport_sum_kernel<<<(g.vh + 255) / 256, 256, 0, s>>>(g, links, phi, out);
 }
 
 }  // namespace stag

@@ -72,10 +72,9 @@ def parse_args():
 
 # ------------------------------------------------------------------ helpers
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_1010_4782_gb300.replicas import dist_env as _env
+
+    return _env()
 
 
 def measured_peaks():
@@ -174,29 +173,15 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+    from paper_1010_4782_gb300.replicas import Replicas
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t)
-        return float(t.item())
+    reps = Replicas(world, rank, dev)
+    barrier, max_over_ranks, sum_over_ranks = reps.barrier, reps.max, reps.sum
 
     build.build()
     binding.load()
     fat, lng = inputs.asqtad_form_fields(dims)
-    b = inputs.gaussian_even_source(dims, rank)  # independent replica per rank
+    b = inputs.gaussian_even_source(dims, reps.source_seed())  # independent replica per rank
     fat_d = torch.from_numpy(fat).to(dev)
     lng_d = torch.from_numpy(lng).to(dev)
     b_d = torch.from_numpy(b).to(dev)
@@ -255,7 +240,7 @@ def run_ours(args):
     clock_info = clocks.stop()
     elapsed_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
     total_solves = args.steps * world
-    value = elapsed_s / total_solves
+    value = reps.time_per_solve(elapsed_s, args.steps)
     infos = rec["infos"]
     iters = infos[-1]["iters"]
 

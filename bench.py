@@ -582,6 +582,19 @@ def run_learned(args):
         res["cg"].append((code2, info2))
     binding.stag_ptnet_destroy(net)
     h.close()
+    # plain CG with native FP64 Dirac kernels (the benchmark spec's comparison) on the first 4 sources
+    opt64 = binding.stag_default_options()
+    opt64.arith = binding.STAG_ARITH_F64
+    fat, lng = inputs.asqtad_form_fields(dims, seeds=(31, 32, 33))
+    h64 = binding.Handle(torch.from_numpy(fat).to(dev), dims, args.mass, naik_long=torch.from_numpy(lng).to(dev),
+                         options=opt64)
+    del fat, lng
+    res["cg64"] = []
+    for j in range(min(4, args.test_sources)):
+        b = torch.from_numpy(inputs.gaussian_even_source(dims, 90000 + j)).to(dev)
+        x3 = torch.zeros_like(b)
+        res["cg64"].append(binding.stag_cg_solve(h64.h, b, x3, TOL, MAX_ITER))
+    h64.close()
 
     def summary(rs):
         its = [i["iters"] for _, i in rs]
@@ -593,6 +606,8 @@ def run_learned(args):
                 "fallbacks": sum(i.get("fallbacks", 0) for _, i in rs)}
 
     fcg, fcg32, cg = summary(res["fcg"]), summary(res["fcg_fp32"]), summary(res["cg"])
+    cg64 = summary(res["cg64"])
+    fcg4 = summary(res["fcg"][:len(res["cg64"])])
     line = {
         "metric": METRIC + " [learned-preconditioner workload]",
         "value": fcg["time_s_mean"],
@@ -621,6 +636,8 @@ def run_learned(args):
         "fcg": fcg,
         "fcg_fp32_inference": fcg32,
         "plain_cg_ff": cg,
+        "plain_cg_fp64_first_sources": cg64,
+        "time_ratio_fcg_over_fp64_cg_same_sources": round(fcg4["time_s_mean"] / cg64["time_s_mean"], 3),
         "iteration_gain_fp32_inference": round(cg["iters_mean"] / fcg32["iters_mean"], 3),
         "time_ratio_fp32_inference_over_cg": round(fcg32["time_s_mean"] / cg["time_s_mean"], 3),
         "iteration_gain": round(cg["iters_mean"] / fcg["iters_mean"], 3),

@@ -488,9 +488,12 @@ __global__ void pt_links_kernel(const double2* __restrict__ in, float2* __restri
 
 // --------------------------------------------------- flexible CG vectors
 // per-block partials of Re<a, b>, Re<a, c>, <b, b> (FP64)
+// Re(a, b), Re(a, c) (c nullable) and |b|^2: per-block partials, then the last
+// block (atomic ticket) sums them in block order into out3[0..2].
 __global__ void __launch_bounds__(kBlock) fcg_dots_kernel(Geom g, const double2* __restrict__ a,
                                                           const double2* __restrict__ b, const double2* __restrict__ c,
-                                                          double* __restrict__ partials, int nblk) {
+                                                          double* __restrict__ partials, int nblk,
+                                                          unsigned int* counter, double* out3) {
     const int i = blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;
     double ab = 0.0, ac = 0.0, bb = 0.0;
@@ -512,11 +515,26 @@ __global__ void __launch_bounds__(kBlock) fcg_dots_kernel(Geom g, const double2*
     const double s1 = block_sum<kBlock>(ac, sm);
     __syncthreads();
     const double s2 = block_sum<kBlock>(bb, sm);
+    __shared__ bool is_last;
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = s0;
         partials[nblk + blockIdx.x] = s1;
         partials[2 * nblk + blockIdx.x] = s2;
+        __threadfence();
+        is_last = atomicAdd(counter, 1u) == (unsigned)nblk - 1;
     }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int bb2 = threadIdx.x; bb2 < nblk; bb2 += kBlock) s += __ldcg(partials + (size_t)k * nblk + bb2);
+        __syncthreads();
+        s = block_sum<kBlock>(s, sm);
+        if (threadIdx.x == 0) out3[k] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // r_old = r; x += alpha p; r -= alpha q
@@ -584,6 +602,8 @@ struct stag_ptnet {
     float2* w = nullptr;         // device weights (FP32 master)
     bool use_tc = true;          // BF16 8 -> 8 forward layer on the tensor cores (pt_tc.cu)
     int* tc_err = nullptr;       // set by a tensor-core layer whose bounded wait ran out
+    unsigned int* dot_counter = nullptr;  // last-block ticket of fcg_dots_kernel
+    double* dot_out = nullptr;            // its three sums
     float2* grad = nullptr;
     float *adam_m = nullptr, *adam_v = nullptr;
     long long adam_t = 0;
@@ -806,7 +826,8 @@ void destroy_net(stag_ptnet* n) {
     if (n->h && n->h->s) cudaStreamSynchronize(n->h->s);
     for (void* p : {(void*)n->links, (void*)n->lng, (void*)n->va, (void*)n->vt, (void*)n->vad, (void*)n->w, (void*)n->grad, (void*)n->adam_m, (void*)n->adam_v,
                     (void*)n->wpart, (void*)n->red, n->scratch_r, n->scratch_e, (void*)n->fr, (void*)n->fz,
-                    (void*)n->fp, (void*)n->fq, (void*)n->fro})
+                    (void*)n->fp, (void*)n->fq, (void*)n->fro, (void*)n->tc_err, (void*)n->dot_counter,
+                    (void*)n->dot_out})
         if (p) cudaFree(p);
     for (int l = 0; l <= kLayers; ++l) {
         if (n->act[l]) cudaFree(n->act[l]);
@@ -843,17 +864,10 @@ void apply_A_q(stag_ptnet* n, const double2* p, double2* q) {
 void dots(stag_ptnet* n, const double2* a, const double2* b, const double2* c, double out[3]) {
     const Geom& g = n->g;
     const int nb = blocks_for(g.vh);
-    fcg_dots_kernel<<<nb, kBlock, 0, S(n)>>>(g, a, b, c, n->red, nb);
+    fcg_dots_kernel<<<nb, kBlock, 0, S(n)>>>(g, a, b, c, n->red, nb, n->dot_counter, n->dot_out);
     pcheck(n, cudaGetLastError(), "dots");
-    n->red_host.resize(3 * nb);
-    pcheck(n, cudaMemcpyAsync(n->red_host.data(), n->red, 3 * nb * sizeof(double), cudaMemcpyDeviceToHost, S(n)),
-           "read dots");
+    pcheck(n, cudaMemcpyAsync(out, n->dot_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, S(n)), "read dots");
     pcheck(n, cudaStreamSynchronize(S(n)), "sync");
-    for (int k = 0; k < 3; ++k) {
-        double s = 0.0;
-        for (int b2 = 0; b2 < nb; ++b2) s += n->red_host[k * nb + b2];
-        out[k] = s;
-    }
 }
 
 }  // namespace
@@ -890,6 +904,8 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         const int nw = n_weights();
         n->w = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate weights"));
         n->tc_err = static_cast<int*>(palloc(n, sizeof(int), "allocate error flag"));
+        n->dot_counter = static_cast<unsigned int*>(palloc(n, sizeof(unsigned int), "allocate counter"));
+        n->dot_out = static_cast<double*>(palloc(n, 3 * sizeof(double), "allocate sums"));
         n->grad = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate gradients"));
         n->adam_m = static_cast<float*>(palloc(n, 2 * nw * sizeof(float), "allocate optimiser"));
         n->adam_v = static_cast<float*>(palloc(n, 2 * nw * sizeof(float), "allocate optimiser"));

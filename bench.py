@@ -303,10 +303,11 @@ def run_ours(args):
     # asqtad-form operator (this workload) and the one-hop operator on the same lattice
     forms = None
     if not args.no_forms:
-        def solve_once(fat_in, lng_in, b_in, ar, inner):
+        def solve_once(fat_in, lng_in, b_in, ar, inner, recon=0):
             o = binding.stag_default_options()
             o.arith = ar
             o.inner = inner
+            o.link_recon = recon
             h = binding.stag_create_ex(fat_in, lng_in, dims, args.mass, o)
             try:
                 binding.stag_set_stream(h, stream)
@@ -321,13 +322,18 @@ def run_ours(args):
                     ("mixed_fp32", binding.STAG_ARITH_FF, binding.STAG_INNER_F32),
                     ("mixed_fp16", binding.STAG_ARITH_FF, binding.STAG_INNER_F16),
                     ("mixed_bf16", binding.STAG_ARITH_FF, binding.STAG_INNER_BF16),
-                    ("mixed_fp32_fp16links", binding.STAG_ARITH_FF, binding.STAG_INNER_F32_L16)]
+                    ("mixed_fp32_fp16links", binding.STAG_ARITH_FF, binding.STAG_INNER_F32_L16),
+                    # 12-parameter SU(3) links (Sec. 3.3): unitary one-hop links only
+                    ("mixed_fp32_recon12", binding.STAG_ARITH_FF, binding.STAG_INNER_F32)]
         forms = {}
         one_hop = torch.from_numpy(inputs.gauge_field(dims, 1)).to(dev)
         for op_name, f_in, l_in in (("asqtad", fat_d, lng_d), ("one_hop", one_hop, None)):
             res, x64 = {}, None
             for name, ar, inner in variants:
-                code, info, x = solve_once(f_in, l_in, b_d, ar, inner)
+                recon = 12 if name.endswith("recon12") else 0
+                if recon and l_in is not None:
+                    continue
+                code, info, x = solve_once(f_in, l_in, b_d, ar, inner, recon)
                 if x64 is None:
                     x64 = x
                 rec = {"time_s": round(info["time_ms"] / 1e3, 4), "status": code, "iters": info["iters"],

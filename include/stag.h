@@ -107,6 +107,12 @@ typedef struct {
                                keep the fastest (default 1); 0 = fixed shapes                  */
     double reliable_delta;  /* mixed precision: replace the residual once |r| < reliable_delta
                                times its maximum since the last replacement (default 0.1)     */
+    int32_t link_recon;     /* 12: the FP32 inner iteration stores two rows of each link and
+                               rebuilds the third as the conjugate cross product of the first
+                               two, times eta (Sec. 3.3, Eq. for SU(3) reconstruction); needs
+                               SU(3) links, the one-hop operator and inner = F32.  0 (default):
+                               all nine entries.                                              */
+    int32_t reserved;       /* 0 */
 } stag_options;
 
 typedef struct {

@@ -106,6 +106,8 @@ class stag_options(ctypes.Structure):
         ("reliable_interval", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
         ("reliable_delta", ctypes.c_double),
+        ("link_recon", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

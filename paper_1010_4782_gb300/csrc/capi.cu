@@ -134,20 +134,23 @@ void read_state(stag_handle* h) {
 
 // Low-precision Dirac kernels and links by storage type.
 void dslash_lo(const Geom& g, int P, const float2* fat, const float2* lng, const float2* in, float2* out, Epilogue e,
-               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s) {
-    launch_dslash_f32(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
+               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool r12 = false) {
+    if (r12)
+        launch_dslash_f32r12(g, P, fat, in, out, e, src, m2, sc, pa, s);  // fat: two rows per link
+    else
+        launch_dslash_f32(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
 }
 void dslash_lo(const Geom& g, int P, const __half2* fat, const __half2* lng, const float2* in, float2* out, Epilogue e,
-               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s) {
+               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool = false) {
     launch_dslash_f32l16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
 }
 void dslash_lo(const Geom& g, int P, const __half2* fat, const __half2* lng, const __half2* in, __half2* out,
-               Epilogue e, const __half2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s) {
+               Epilogue e, const __half2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool = false) {
     launch_dslash_h16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
 }
 void dslash_lo(const Geom& g, int P, const __nv_bfloat162* fat, const __nv_bfloat162* lng, const __nv_bfloat162* in,
                __nv_bfloat162* out, Epilogue e, const __nv_bfloat162* src, double m2, CgScalars* sc, double* pa,
-               cudaStream_t s) {
+               cudaStream_t s, bool = false) {
     launch_dslash_b16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
 }
 const float2* lo_fat(const stag_handle* h, const float2*) { return h->fat32; }
@@ -168,10 +171,11 @@ void enqueue_lo_iteration(stag_handle* h, Mark mark) {
     V* r = static_cast<V*>(h->lo_r);
     const L* fat = lo_fat(h, static_cast<const L*>(nullptr));
     const L* lng = lo_lng(h, static_cast<const L*>(nullptr));
+    const bool r12 = h->opt.link_recon == 12;
     mark(0);
-    dslash_lo(g, 1, fat, lng, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s);
+    dslash_lo(g, 1, fat, lng, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s, r12);
     mark(1);
-    dslash_lo(g, 0, fat, lng, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s);
+    dslash_lo(g, 0, fat, lng, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s, r12);
     mark(2);
     launch_lo_update_xr<V>(g, h->lo_y, r, d, ad, h->scal, h->partials, h->s);
     mark(3);
@@ -189,9 +193,10 @@ void apply_A_lo(stag_handle* h, double m2, double scale) {
     V* o = static_cast<V*>(h->lo_ad);
     const V* fat = lo_fat(h, in);
     const V* lng = lo_lng(h, in);
+    const bool r12 = h->opt.link_recon == 12;
     launch_to_lo<V>(g, h->x, in, 1.0 / scale, h->s);
-    dslash_lo(g, 1, fat, lng, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
-    dslash_lo(g, 0, fat, lng, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s);
+    dslash_lo(g, 1, fat, lng, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s, r12);
+    dslash_lo(g, 0, fat, lng, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s, r12);
     launch_from_lo<V>(g, o, h->ad, scale, h->s);
 }
 
@@ -343,7 +348,7 @@ void destroy_handle(stag_handle* h) {
 }
 
 void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* soaff, float2* soa32,
-                __half2* soa16, __nv_bfloat162* soab16) {
+                __half2* soa16, __nv_bfloat162* soab16, float2* soa32r = nullptr) {
     const size_t aos_bytes = (size_t)2 * h->g.vh * 4 * 9 * sizeof(double2);
     const double* src = links_in;
     void* stage = nullptr;
@@ -367,6 +372,10 @@ void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* 
     }
     launch_pack_links(h->g, src, soa64, soaff, soa32, soa16, soab16, h->s);
     h->launches += 1;
+    if (soa32r) {
+        launch_pack_links_rows2(h->g, src, soa32r, h->s);
+        h->launches += 1;
+    }
     cudaError_t e = cudaGetLastError();
     if (stage) {
         cudaError_t e2 = cudaStreamSynchronize(h->s);
@@ -687,6 +696,10 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         if (o.inner != STAG_INNER_NONE && o.inner != STAG_INNER_F32 && o.inner != STAG_INNER_F16 &&
             o.inner != STAG_INNER_BF16 && o.inner != STAG_INNER_F32_L16)
             fail(nullptr, STAG_ERR_INVALID_ARG, "unknown inner precision");
+        if (o.link_recon != 0 && o.link_recon != 12)
+            fail(nullptr, STAG_ERR_INVALID_ARG, "link_recon must be 0 or 12");
+        if (o.link_recon == 12 && (naik_long != nullptr || o.inner != STAG_INNER_F32))
+            fail(nullptr, STAG_ERR_INVALID_ARG, "12-parameter links need the one-hop operator and inner = F32");
         if (o.inner != STAG_INNER_NONE &&
             (o.reliable_interval < 1 || !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0)))
             fail(nullptr, STAG_ERR_INVALID_ARG, "reliable_interval must be >= 1 and reliable_delta in (0, 1)");
@@ -728,7 +741,9 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         h->u = dev_alloc<void>(h, vb, "allocate u");
         if (ff) h->xff = dev_alloc<float4>(h, vb, "allocate x_ff");
         const size_t lo_links = (size_t)2 * 4 * 9 * g.vs;  // complex entries per field
-        if (h->opt.inner == STAG_INNER_F32) {
+        if (h->opt.inner == STAG_INNER_F32 && h->opt.link_recon == 12) {
+            h->fat32 = dev_alloc<float2>(h, lo_links / 9 * 6 * sizeof(float2), "allocate FP32 two-row links");
+        } else if (h->opt.inner == STAG_INNER_F32) {
             h->fat32 = dev_alloc<float2>(h, lo_links * sizeof(float2), "allocate FP32 links");
             if (h->naik) h->lng32 = dev_alloc<float2>(h, lo_links * sizeof(float2), "allocate FP32 Naik links");
         } else if (h->opt.inner == STAG_INNER_F16 || h->opt.inner == STAG_INNER_F32_L16) {
@@ -758,7 +773,8 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
                    "allocate pinned CG state");
         std::memset(h->scal_host, 0, sizeof(CgScalars));
 
-        pack_field(h, fat, h->fat64, h->fatff, h->fat32, h->fat16, h->fatb16);
+        const bool r12 = h->opt.link_recon == 12;
+        pack_field(h, fat, h->fat64, h->fatff, r12 ? nullptr : h->fat32, h->fat16, h->fatb16, r12 ? h->fat32 : nullptr);
         if (h->naik) pack_field(h, naik_long, h->lng64, h->lngff, h->lng32, h->lng16, h->lngb16);
         end_call(h);
         *out = h;

@@ -36,6 +36,8 @@ struct ArithF64 {
     using C = double2;  // compute
     static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
     using TL = T;  // link storage
+    static constexpr int kEntries = 9;  // stored entries per link
+    static constexpr bool kRecon = false;
     static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     struct Acc {
         double2 c[3];
@@ -72,6 +74,8 @@ struct ArithFF {
     using C = float4;
     static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
     using TL = T;  // link storage
+    static constexpr int kEntries = 9;  // stored entries per link
+    static constexpr bool kRecon = false;
     static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     struct Acc {
         FFAcc re[3], im[3];
@@ -109,6 +113,8 @@ struct ArithF32 {
     using C = float2;
     static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
     using TL = T;  // link storage
+    static constexpr int kEntries = 9;  // stored entries per link
+    static constexpr bool kRecon = false;
     static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     struct Acc {
         float2 c[3];
@@ -146,6 +152,8 @@ struct ArithH16 {
     using C = float2;
     static __device__ __forceinline__ C ld(const T* p) { return __half22float2(__ldg(p)); }
     using TL = T;  // link storage
+    static constexpr int kEntries = 9;  // stored entries per link
+    static constexpr bool kRecon = false;
     static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     using Acc = ArithF32::Acc;
     static __device__ __forceinline__ void zero(Acc& a) { ArithF32::zero(a); }
@@ -168,6 +176,8 @@ struct ArithB16 {
     using C = float2;
     static __device__ __forceinline__ C ld(const T* p) { return __bfloat1622float2(__ldg(p)); }
     using TL = T;  // link storage
+    static constexpr int kEntries = 9;  // stored entries per link
+    static constexpr bool kRecon = false;
     static __device__ __forceinline__ C ldl(const TL* p) { return ld(p); }
     using Acc = ArithF32::Acc;
     static __device__ __forceinline__ void zero(Acc& a) { ArithF32::zero(a); }
@@ -183,11 +193,39 @@ struct ArithB16 {
     }
 };
 
+// FP32 with 12-parameter links (Sec. 3.3): two stored rows a, b of each
+// eta-folded SU(3) link; the third is eta (a x b)^* (for U in SU(3) the third
+// row is the conjugate cross product of the first two, and eta^2 = 1).  Link
+// bytes drop by a third for 6 complex multiply-adds per row.
+struct ArithF32R {
+    using T = float2;
+    using TL = float2;
+    using C = float2;
+    static constexpr int kEntries = 6;
+    static constexpr bool kRecon = true;
+    static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ C ldl(const TL* p) { return __ldg(p); }
+    using Acc = ArithF32::Acc;
+    static __device__ __forceinline__ void zero(Acc& a) { ArithF32::zero(a); }
+    static __device__ __forceinline__ void row_fwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        ArithF32::row_fwd(a, r, u0, u1, u2, v0, v1, v2);
+    }
+    static __device__ __forceinline__ void row_bwd(Acc& a, int r, C u0, C u1, C u2, C v0, C v1, C v2) {
+        ArithF32::row_bwd(a, r, u0, u1, u2, v0, v1, v2);
+    }
+    static __device__ __forceinline__ T store_val(const Acc& a, int r) { return ArithF32::store_val(a, r); }
+    static __device__ __forceinline__ T epilogue(Acc& a, int r, C s, double m2, float2 m2f, double& dot) {
+        return ArithF32::epilogue(a, r, s, m2, m2f, dot);
+    }
+};
+
 // FP16-stored links, FP32 vectors and arithmetic: the links carry most of the
 // bytes, the vectors keep FP32's significand (the CG direction and residual).
 struct ArithL16 {
     using T = float2;
     using TL = __half2;
+    static constexpr int kEntries = 9;
+    static constexpr bool kRecon = false;
     using C = float2;
     static __device__ __forceinline__ C ld(const T* p) { return __ldg(p); }
     static __device__ __forceinline__ C ldl(const TL* p) { return __half22float2(__ldg(p)); }
@@ -221,24 +259,55 @@ struct DslashParams {
     int i0, i1;                // output sites [i0, i1) of parity P
 };
 
+// Link entries 6..8 (the third row) from the first two: eta * conj(row0 x row1).
+__device__ __forceinline__ float2 cross_conj(float2 a1, float2 b2, float2 a2, float2 b1, float eta) {
+    // conj(a1 b2 - a2 b1) * eta
+    const float re = a1.x * b2.x - a1.y * b2.y - (a2.x * b1.x - a2.y * b1.y);
+    const float im = a1.x * b2.y + a1.y * b2.x - (a2.x * b1.y + a2.y * b1.x);
+    return make_float2(eta * re, -eta * im);
+}
+template <class A>
+__device__ __forceinline__ void load_recon(typename A::C (&U)[9], const typename A::TL* __restrict__ u, size_t vs,
+                                           float eta) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) U[k] = A::ldl(u + k * vs);
+    U[6] = cross_conj(U[1], U[5], U[2], U[4], eta);
+    U[7] = cross_conj(U[2], U[3], U[0], U[5], eta);
+    U[8] = cross_conj(U[0], U[4], U[1], U[3], eta);
+}
+
 template <class A>
 __device__ __forceinline__ void hop_fwd(typename A::Acc& acc, const typename A::TL* __restrict__ u,
-                                        const typename A::T* __restrict__ in, int nb, size_t vs) {
+                                        const typename A::T* __restrict__ in, int nb, size_t vs, float eta = 1.f) {
     const typename A::C v0 = A::ld(in + nb), v1 = A::ld(in + vs + nb), v2 = A::ld(in + 2 * vs + nb);
+    if constexpr (A::kRecon) {
+        typename A::C U[9];
+        load_recon<A>(U, u, vs, eta);
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-        A::row_fwd(acc, r, A::ldl(u + (3 * r) * vs), A::ldl(u + (3 * r + 1) * vs), A::ldl(u + (3 * r + 2) * vs),
-                   v0, v1, v2);
+        for (int r = 0; r < 3; ++r) A::row_fwd(acc, r, U[3 * r], U[3 * r + 1], U[3 * r + 2], v0, v1, v2);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            A::row_fwd(acc, r, A::ldl(u + (3 * r) * vs), A::ldl(u + (3 * r + 1) * vs), A::ldl(u + (3 * r + 2) * vs),
+                       v0, v1, v2);
+    }
 }
 
 template <class A>
 __device__ __forceinline__ void hop_bwd(typename A::Acc& acc, const typename A::TL* __restrict__ u,
-                                        const typename A::T* __restrict__ in, int nb, size_t vs) {
+                                        const typename A::T* __restrict__ in, int nb, size_t vs, float eta = 1.f) {
     const typename A::C v0 = A::ld(in + nb), v1 = A::ld(in + vs + nb), v2 = A::ld(in + 2 * vs + nb);
     // (U^dag v)_r = sum_c conj(U_cr) v_c
+    if constexpr (A::kRecon) {
+        typename A::C U[9];
+        load_recon<A>(U, u, vs, eta);
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-        A::row_bwd(acc, r, A::ldl(u + r * vs), A::ldl(u + (3 + r) * vs), A::ldl(u + (6 + r) * vs), v0, v1, v2);
+        for (int r = 0; r < 3; ++r) A::row_bwd(acc, r, U[r], U[3 + r], U[6 + r], v0, v1, v2);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            A::row_bwd(acc, r, A::ldl(u + r * vs), A::ldl(u + (3 + r) * vs), A::ldl(u + (6 + r) * vs), v0, v1, v2);
+    }
 }
 
 // Half-lattice index of the neighbour of (x,y,z,t) at +-h along mu.
@@ -272,8 +341,11 @@ __global__ void __launch_bounds__(kBlock, 4) dslash_kernel(const DslashParams<A>
         for (int mu = 0; mu < 4; ++mu) {
             const int f1 = neighbour(g, x, y, z, t, mu, 1, true);
             const int b1 = neighbour(g, x, y, z, t, mu, 1, false);
-            hop_fwd<A>(acc, p.fat + ((size_t)(P * 4 + mu) * 9) * vs + i, p.in, f1, vs);
-            hop_bwd<A>(acc, p.fat + ((size_t)(Q * 4 + mu) * 9) * vs + b1, p.in, b1, vs);
+            // eta_mu(x) = eta_mu(x - mu): the phase of both links of this direction
+            const int ps = (mu >= 1 ? x : 0) + (mu >= 2 ? y : 0) + (mu >= 3 ? z : 0);
+            const float eta = (ps & 1) ? -1.f : 1.f;
+            hop_fwd<A>(acc, p.fat + ((size_t)(P * 4 + mu) * A::kEntries) * vs + i, p.in, f1, vs, eta);
+            hop_bwd<A>(acc, p.fat + ((size_t)(Q * 4 + mu) * A::kEntries) * vs + b1, p.in, b1, vs, eta);
             if (NAIK) {
                 const int h = g.hop3[mu];
                 const int f3 = neighbour(g, x, y, z, t, mu, h, true);
@@ -392,6 +464,14 @@ void launch_dslash_f32l16(const Geom& g, int out_parity, const __half2* fat, con
     DslashParams<ArithL16> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials, 0,
                              g.vh};
     launch_any(p, lng != nullptr, epi, s);
+}
+
+void launch_dslash_f32r12(const Geom& g, int out_parity, const float2* fat_rows2, const float2* in, float2* out,
+                          Epilogue epi, const float2* src, double m2, CgScalars* scal, double* partials,
+                          cudaStream_t s) {
+    DslashParams<ArithF32R> p{g, out_parity, fat_rows2, nullptr, in, out, src, m2, host_ff_from_double(m2), scal,
+                              partials, 0, g.vh};
+    launch_any(p, false, epi, s);
 }
 
 }  // namespace stag

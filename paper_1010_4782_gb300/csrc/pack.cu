@@ -59,6 +59,45 @@ void launch_pack_links(const Geom& g, const double* aos, double2* soa64, float4*
                                                 soaff, soa32, soa16, soab16);
 }
 
+// FP32 links with the first two rows only ([parity][mu][6][vs], eta folded): the
+// third row of an SU(3) matrix is the conjugate cross product of the first two
+// (Sec. 3.3), rebuilt in the Dirac kernel.  Direction fastest, as above.
+__global__ void __launch_bounds__(kBlock) pack_links_rows2_kernel(Geom g, const double2* __restrict__ aos,
+                                                                  float2* __restrict__ soa32r) {
+    const long long V = 2LL * g.vh;
+    const long long idx = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (idx >= 4 * V) return;
+    const int mu = (int)(idx & 3);
+    const int lex = (int)(idx >> 2);
+    const int x = lex % g.lx;
+    int r = lex / g.lx;
+    const int y = r % g.ly;
+    r /= g.ly;
+    const int z = r % g.lz;
+    const int t = r / g.lz;
+    const int P = (x + y + z + t) & 1;
+    const int cb = lex >> 1;
+    int phase_sum = 0;
+    if (mu >= 1) phase_sum += x;
+    if (mu >= 2) phase_sum += y;
+    if (mu >= 3) phase_sum += z;
+    const double eta = (phase_sum & 1) ? -1.0 : 1.0;
+    const double2* src = aos + ((size_t)lex * 4 + mu) * 9;
+    const size_t vs = (size_t)g.vs;
+    const size_t base = ((size_t)(P * 4 + mu) * 6) * vs + cb;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double2 u = src[k];
+        soa32r[base + k * vs] = make_float2((float)(eta * u.x), (float)(eta * u.y));
+    }
+}
+
+void launch_pack_links_rows2(const Geom& g, const double* aos, float2* soa32r, cudaStream_t s) {
+    const long long n = 8LL * g.vh;
+    pack_links_rows2_kernel<<<(int)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        g, reinterpret_cast<const double2*>(aos), soa32r);
+}
+
 __global__ void __launch_bounds__(kBlock) pack_vec_kernel(Geom g, const double2* __restrict__ aos,
                                                           double2* __restrict__ soa) {
     const int i = blockIdx.x * kBlock + threadIdx.x;

@@ -28,6 +28,8 @@ struct LinkSet {
 // in FP64 and, where the pointer is not null, float-float, FP32, FP16 and BF16.
 void launch_pack_links(const Geom& g, const double* aos, double2* soa64, float4* soaff,
                        float2* soa32, __half2* soa16, __nv_bfloat162* soab16, cudaStream_t s);
+// AoS links -> FP32 [2][4][6][vs]: the first two rows, eta folded (12-parameter form)
+void launch_pack_links_rows2(const Geom& g, const double* aos, float2* soa32r, cudaStream_t s);
 // ABI vector [vh][3] complex128 (device) <-> F64 SoA [3][vs]
 void launch_pack_vec(const Geom& g, const double* aos, double2* soa, cudaStream_t s);
 void launch_unpack_vec(const Geom& g, const double2* soa, double* aos, cudaStream_t s);
@@ -50,6 +52,10 @@ void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const f
 void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng,
                        const __half2* in, __half2* out, Epilogue epi, const __half2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s);
+// FP32 with 12-parameter links ([2][4][6][vs], one-hop only): row 2 rebuilt in the kernel
+void launch_dslash_f32r12(const Geom& g, int out_parity, const float2* fat_rows2, const float2* in, float2* out,
+                          Epilogue epi, const float2* src, double m2, CgScalars* scal, double* partials,
+                          cudaStream_t s);
 // FP16-stored links, FP32 vectors and arithmetic
 void launch_dslash_f32l16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng, const float2* in,
                           float2* out, Epilogue epi, const float2* src, double m2, CgScalars* scal, double* partials,

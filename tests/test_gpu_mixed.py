@@ -151,3 +151,53 @@ def test_mixed_rejects_bad_options():
         _handle(fat, None, dims, 0.1, inner=binding.STAG_INNER_F32, reliable_delta=1.5)
     with pytest.raises(binding.StagError):
         _handle(fat, None, dims, 0.1, inner=7)
+
+
+# ---- 12-parameter links (Sec. 3.3): two stored rows, the third rebuilt in the kernel
+
+def _recon_handle(fat, dims, mass):
+    return _handle(fat, None, dims, mass, inner=binding.STAG_INNER_F32, link_recon=12)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 12), (8, 8, 8, 16)])
+def test_recon12_operator(dims):
+    """SU(3) links (exp(0.3 i H)) rebuilt from two rows: the FP32 bound of the
+    full-link operator holds (the rebuilt row carries a few FP32 roundings)."""
+    mass = 0.05
+    fat = inputs.gauge_field(dims, 71)
+    v = inputs.gaussian_even_source(dims, 72)
+    ref = oracle.Operator(fat, None, mass, dims).apply_A(v)
+    with _recon_handle(fat, dims, mass) as h:
+        out = torch.empty_like(_dev(v))
+        binding.stag_apply_A_prec(h.h, binding.STAG_ARITH_F32, _dev(v), out)
+    got = out.cpu().numpy()
+    tn, te = OP_TOL[binding.STAG_ARITH_F32]
+    assert np.linalg.norm(got - ref) <= tn * np.linalg.norm(ref)
+    assert np.abs(got - ref).max() <= te * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", [((4, 4, 4, 4), 0.1, 1), ((8, 8, 8, 8), 0.02, 17)])
+def test_recon12_mixed_solve(case):
+    dims, mass, seed = case
+    tol = 1e-10
+    fat = inputs.gauge_field(dims, seed)
+    b = inputs.gaussian_even_source(dims, 0)
+    op, x_ref = _oracle_x(fat, None, mass, dims, b)
+    with _recon_handle(fat, dims, mass) as h:
+        x = torch.zeros_like(_dev(b))
+        code, info = binding.stag_cg_solve(h.h, _dev(b), x, tol, max_iter=20000)
+    assert code == binding.STAG_OK and info["true_rel_residual"] <= tol, info
+    assert info["fallbacks"] == 0
+    xs = x.cpu().numpy().reshape(-1)
+    assert np.linalg.norm(xs - x_ref) / np.linalg.norm(x_ref) <= 1e-8
+
+
+def test_recon12_rejects_naik_and_other_inner():
+    dims = (4, 4, 4, 4)
+    fat, lng = _fields(dims, True, 3)
+    with pytest.raises(binding.StagError):
+        _handle(fat, lng, dims, 0.1, inner=binding.STAG_INNER_F32, link_recon=12)
+    with pytest.raises(binding.StagError):
+        _handle(fat, None, dims, 0.1, inner=binding.STAG_INNER_F16, link_recon=12)
+    with pytest.raises(binding.StagError):
+        _handle(fat, None, dims, 0.1, inner=binding.STAG_INNER_F32, link_recon=8)

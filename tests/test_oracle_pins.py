@@ -274,3 +274,21 @@ def test_even_site_numbering():
 def test_rejects_odd_extent():
     with pytest.raises(ValueError):
         oracle.check_dims((4, 4, 3, 4))
+
+
+def test_gauge_field_is_su3():
+    """The seeded links U = exp(0.3 i H), H Hermitian and traceless, are SU(3) to
+    rounding: U^dag U = 1 and det U = 1.  The 12-parameter form (Sec. 3.3) relies
+    on it: the third row of an SU(3) matrix is the conjugate cross product of the
+    first two."""
+    dims = (4, 2, 6, 4)
+    u = inputs.gauge_field(dims, 3).reshape(-1, 3, 3)
+    eye = np.eye(3)
+    assert np.abs(np.conj(np.swapaxes(u, -1, -2)) @ u - eye).max() < 1e-13
+    assert np.abs(np.linalg.det(u) - 1.0).max() < 1e-13
+    row2 = np.conj(np.cross(u[:, 0, :], u[:, 1, :]))
+    assert np.abs(row2 - u[:, 2, :]).max() < 1e-13
+    # the asqtad-form fat links are not unitary (the 12-parameter form does not apply)
+    fat, _ = inputs.asqtad_form_fields(dims)
+    f = fat.reshape(-1, 3, 3)
+    assert np.abs(np.conj(np.swapaxes(f, -1, -2)) @ f - eye).max() > 1e-3

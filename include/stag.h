@@ -113,6 +113,19 @@ typedef struct {
                                SU(3) links, the one-hop operator and inner = F32.  0 (default):
                                all nine entries.                                              */
     int32_t reserved;       /* 0 */
+    double long_scale;      /* long_recon = 12: the Naik links are long_scale x SU(3) (e.g. the
+                               Naik coefficient times a product of SU(3) links)               */
+    int32_t long_recon;     /* 12: the float-float Dirac kernels store two rows of each Naik
+                               link and rebuild the third as (eta / long_scale) times the
+                               conjugate cross product of the first two (the 12-parameter
+                               form of Sec. 3.3 for a scaled SU(3) matrix).  Needs arith = FF
+                               and Naik links; stag_create_ex checks that every Naik link
+                               divided by long_scale is unitary with determinant 1 (entries of
+                               L^dag L / c^2 - 1 and det L / c^3 - 1 at most 1e-12) and fails
+                               with STAG_ERR_INVALID_ARG otherwise.  The FP64 copy used for the
+                               final residual check keeps all nine entries.  0 (default): all
+                               nine entries.                                                  */
+    int32_t reserved2;      /* 0 */
 } stag_options;
 
 typedef struct {

@@ -29,10 +29,12 @@ def paper_bytes_per_site(naik: bool = False, elem_bytes: int = 8) -> int:
     return int(hops(naik) * (LINK_BYTES_F64 + VECTOR_BYTES_F64) * s + VECTOR_BYTES_F64 * s)
 
 
-def compulsory_bytes_per_site(naik: bool = False, elem_bytes: int = 8) -> int:
-    """Each link once, the input vector once, the output once (1248 B one-hop, FP64)."""
+def compulsory_bytes_per_site(naik: bool = False, elem_bytes: int = 8, long_entries: int = 9) -> int:
+    """Each link once, the input vector once, the output once (1248 B one-hop, FP64).
+    long_entries = 6: the Naik links stored as two rows (Sec. 3.3), 2016 B with Naik."""
     s = elem_bytes / 8
-    return int(hops(naik) * LINK_BYTES_F64 * s + 2 * VECTOR_BYTES_F64 * s)
+    links = 8 * LINK_BYTES_F64 + (8 * LINK_BYTES_F64 * long_entries // 9 if naik else 0)
+    return int(links * s + 2 * VECTOR_BYTES_F64 * s)
 
 
 def flops_per_site(naik: bool = False) -> int:

@@ -108,6 +108,9 @@ class stag_options(ctypes.Structure):
         ("reliable_delta", ctypes.c_double),
         ("link_recon", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("long_scale", ctypes.c_double),
+        ("long_recon", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
     ]
 
 

@@ -427,6 +427,8 @@ int stag_batch_create(stag_batch** out, int32_t n_sys, const double* const* fat,
             bfail(b, STAG_ERR_INVALID_ARG, "check_interval must be in [1, 4096]");
         if (b->opt.reliable_interval < 1 || !(b->opt.reliable_delta > 0.0 && b->opt.reliable_delta < 1.0))
             bfail(b, STAG_ERR_INVALID_ARG, "reliable_interval must be >= 1 and reliable_delta in (0, 1)");
+        if (b->opt.link_recon != 0 || b->opt.long_recon != 0)
+            bfail(b, STAG_ERR_INVALID_ARG, "batches keep all nine link entries (link_recon = long_recon = 0)");
         bcheck(b, cudaGetDevice(&b->device), "cudaGetDevice");
         bcheck(b, cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking), "cudaStreamCreate");
         bcheck(b, cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "cudaEventCreate");

@@ -102,10 +102,16 @@ void begin_call(stag_handle* h) {
 
 void end_call(stag_handle* h) { cuda_check(h, cudaStreamSynchronize(h->s), "cudaStreamSynchronize"); }
 
+// long_recon = 12 accepts Naik links whose L / long_scale deviates from SU(3)
+// by at most this (entries of L^dag L / c^2 - 1, and det L / c^3 - 1): the third
+// row rebuilt from the first two then agrees with the stored one to about this
+// relative size, far below the solver's tolerances.
+constexpr float kLongReconMaxDeviation = 1e-12f;
+
 bool use_ff(const stag_handle* h) { return h->opt.arith == STAG_ARITH_FF; }
 
 LinkSet links(const stag_handle* h) {
-    return LinkSet{h->fat64, h->lng64, h->fatff, h->lngff};
+    return LinkSet{h->fat64, h->lng64, h->fatff, h->lngff, h->lng_s};
 }
 
 // out = m2 * in - D_eo D_oe in on internal F64 vectors, native FP64; uses h->t.
@@ -347,8 +353,11 @@ void destroy_handle(stag_handle* h) {
     delete h;
 }
 
+// check_scale != 0: also the scaled-SU(3) check of the links (largest deviation
+// into *maxdev) and the float-float two-row copy soaff instead of nine entries.
 void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* soaff, float2* soa32,
-                __half2* soa16, __nv_bfloat162* soab16, float2* soa32r = nullptr) {
+                __half2* soa16, __nv_bfloat162* soab16, float2* soa32r = nullptr, double check_scale = 0.0,
+                unsigned int* maxdev = nullptr) {
     const size_t aos_bytes = (size_t)2 * h->g.vh * 4 * 9 * sizeof(double2);
     const double* src = links_in;
     void* stage = nullptr;
@@ -369,6 +378,12 @@ void pack_field(stag_handle* h, const double* links_in, double2* soa64, float4* 
             cuda_check(h, e, "copy links to device");
         }
         src = static_cast<const double*>(stage);
+    }
+    if (check_scale != 0.0) {
+        launch_check_scaled_su3(h->g, src, check_scale, maxdev, h->s);
+        launch_pack_links_ff_rows2(h->g, src, soaff, h->s);
+        h->launches += 2;
+        soaff = nullptr;
     }
     launch_pack_links(h->g, src, soa64, soaff, soa32, soa16, soab16, h->s);
     h->launches += 1;
@@ -700,6 +715,13 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
             fail(nullptr, STAG_ERR_INVALID_ARG, "link_recon must be 0 or 12");
         if (o.link_recon == 12 && (naik_long != nullptr || o.inner != STAG_INNER_F32))
             fail(nullptr, STAG_ERR_INVALID_ARG, "12-parameter links need the one-hop operator and inner = F32");
+        if (o.long_recon != 0 && o.long_recon != 12)
+            fail(nullptr, STAG_ERR_INVALID_ARG, "long_recon must be 0 or 12");
+        if (o.long_recon == 12 &&
+            (naik_long == nullptr || o.arith != STAG_ARITH_FF || !std::isfinite(o.long_scale) ||
+             !(std::fabs(o.long_scale) > 1e-20 && std::fabs(o.long_scale) < 1e20)))
+            fail(nullptr, STAG_ERR_INVALID_ARG,
+                 "long_recon = 12 needs Naik links, arith = FF and a finite long_scale with 1e-20 < |long_scale| < 1e20");
         if (o.inner != STAG_INNER_NONE &&
             (o.reliable_interval < 1 || !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0)))
             fail(nullptr, STAG_ERR_INVALID_ARG, "reliable_interval must be >= 1 and reliable_delta in (0, 1)");
@@ -775,7 +797,25 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
 
         const bool r12 = h->opt.link_recon == 12;
         pack_field(h, fat, h->fat64, h->fatff, r12 ? nullptr : h->fat32, h->fat16, h->fatb16, r12 ? h->fat32 : nullptr);
-        if (h->naik) pack_field(h, naik_long, h->lng64, h->lngff, h->lng32, h->lng16, h->lngb16);
+        if (h->naik && h->opt.long_recon == 12) {
+            unsigned int* maxdev = reinterpret_cast<unsigned int*>(h->partials);
+            cuda_check(h, cudaMemsetAsync(maxdev, 0, sizeof(unsigned int), h->s), "clear link check");
+            pack_field(h, naik_long, h->lng64, h->lngff, h->lng32, h->lng16, h->lngb16, nullptr, h->opt.long_scale,
+                       maxdev);
+            unsigned int bits = 0;
+            cuda_check(h, cudaMemcpyAsync(&bits, maxdev, sizeof(bits), cudaMemcpyDeviceToHost, h->s),
+                       "read link check");
+            cuda_check(h, cudaStreamSynchronize(h->s), "cudaStreamSynchronize");
+            float dev;
+            std::memcpy(&dev, &bits, sizeof(dev));
+            if (!(dev <= kLongReconMaxDeviation))
+                fail(h, STAG_ERR_INVALID_ARG,
+                     "long_recon = 12: a Naik link / long_scale is not in SU(3) (deviation " + std::to_string(dev) +
+                         ")");
+            h->lng_s = host_ff_from_double(1.0 / h->opt.long_scale);
+        } else if (h->naik) {
+            pack_field(h, naik_long, h->lng64, h->lngff, h->lng32, h->lng16, h->lngb16);
+        }
         end_call(h);
         *out = h;
         return STAG_OK;

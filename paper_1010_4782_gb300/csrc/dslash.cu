@@ -25,6 +25,8 @@
 //              alpha = delta_new / d^dag A d (Fig. 1) on the device.
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "ff.cuh"
 #include "stag_kernels.h"
 
@@ -257,6 +259,7 @@ struct DslashParams {
     CgScalars* scal;
     double* partials;
     int i0, i1;                // output sites [i0, i1) of parity P
+    float2 lng_s = make_float2(0.f, 0.f);  // NAIK == 2: 1 / scale of the two-row Naik links (float-float)
 };
 
 // Link entries 6..8 (the third row) from the first two: eta * conj(row0 x row1).
@@ -274,6 +277,33 @@ __device__ __forceinline__ void load_recon(typename A::C (&U)[9], const typename
     U[6] = cross_conj(U[1], U[5], U[2], U[4], eta);
     U[7] = cross_conj(U[2], U[3], U[0], U[5], eta);
     U[8] = cross_conj(U[0], U[4], U[1], U[3], eta);
+}
+
+// Float-float Naik link stored as its first two rows ([6][vs], eta folded); the
+// third row is (eta / scale) conj(row0 x row1), s = eta / scale (Sec. 3.3's
+// 12-parameter form applied to scale x SU(3)).
+__device__ __forceinline__ void load_recon_ff(float4 (&U)[9], const float4* __restrict__ u, size_t vs, float2 s) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) U[k] = __ldg(u + k * vs);
+    U[6] = ff_cross_conj_scaled(U[1], U[5], U[2], U[4], s);
+    U[7] = ff_cross_conj_scaled(U[2], U[3], U[0], U[5], s);
+    U[8] = ff_cross_conj_scaled(U[0], U[4], U[1], U[3], s);
+}
+__device__ __forceinline__ void hop_fwd_ffr(ArithFF::Acc& acc, const float4* __restrict__ u,
+                                            const float4* __restrict__ in, int nb, size_t vs, float2 s) {
+    const float4 v0 = __ldg(in + nb), v1 = __ldg(in + vs + nb), v2 = __ldg(in + 2 * vs + nb);
+    float4 U[9];
+    load_recon_ff(U, u, vs, s);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) ArithFF::row_fwd(acc, r, U[3 * r], U[3 * r + 1], U[3 * r + 2], v0, v1, v2);
+}
+__device__ __forceinline__ void hop_bwd_ffr(ArithFF::Acc& acc, const float4* __restrict__ u,
+                                            const float4* __restrict__ in, int nb, size_t vs, float2 s) {
+    const float4 v0 = __ldg(in + nb), v1 = __ldg(in + vs + nb), v2 = __ldg(in + 2 * vs + nb);
+    float4 U[9];
+    load_recon_ff(U, u, vs, s);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) ArithFF::row_bwd(acc, r, U[r], U[3 + r], U[6 + r], v0, v1, v2);
 }
 
 template <class A>
@@ -322,8 +352,10 @@ __device__ __forceinline__ int neighbour(const Geom& g, int x, int y, int z, int
     return site_index(x, y, z, t, g);
 }
 
-template <class A, bool NAIK, int EPI>
-__global__ void __launch_bounds__(kBlock, 4) dslash_kernel(const DslashParams<A> p) {
+// NAIK: 0 one-hop only; 1 Naik links with nine entries; 2 float-float Naik
+// links with two rows (A = ArithFF only).
+template <class A, int NAIK, int EPI>
+__global__ void __launch_bounds__(kBlock, NAIK == 2 ? 3 : 4) dslash_kernel(const DslashParams<A> p) {
     if (EPI == EPI_CG) {
         if (p.scal->done) return;
     }
@@ -346,12 +378,27 @@ __global__ void __launch_bounds__(kBlock, 4) dslash_kernel(const DslashParams<A>
             const float eta = (ps & 1) ? -1.f : 1.f;
             hop_fwd<A>(acc, p.fat + ((size_t)(P * 4 + mu) * A::kEntries) * vs + i, p.in, f1, vs, eta);
             hop_bwd<A>(acc, p.fat + ((size_t)(Q * 4 + mu) * A::kEntries) * vs + b1, p.in, b1, vs, eta);
-            if (NAIK) {
+            if constexpr (NAIK == 1) {
                 const int h = g.hop3[mu];
                 const int f3 = neighbour(g, x, y, z, t, mu, h, true);
                 const int b3 = neighbour(g, x, y, z, t, mu, h, false);
                 hop_fwd<A>(acc, p.lng + ((size_t)(P * 4 + mu) * 9) * vs + i, p.in, f3, vs);
                 hop_bwd<A>(acc, p.lng + ((size_t)(Q * 4 + mu) * 9) * vs + b3, p.in, b3, vs);
+            }
+        }
+        if constexpr (NAIK == 2) {
+            // A rolled loop: unrolled, the four copies of the float-float
+            // reconstruction overflow the instruction cache.
+#pragma unroll 1
+            for (int mu = 0; mu < 4; ++mu) {
+                const int h = mu == 0 ? g.hop3[0] : mu == 1 ? g.hop3[1] : mu == 2 ? g.hop3[2] : g.hop3[3];
+                const int f3 = neighbour(g, x, y, z, t, mu, h, true);
+                const int b3 = neighbour(g, x, y, z, t, mu, h, false);
+                // the Naik link of x and the one arriving from x - 3 mu share eta_mu(x)
+                const int ps = (mu >= 1 ? x : 0) + (mu >= 2 ? y : 0) + (mu >= 3 ? z : 0);
+                const float2 s = (ps & 1) ? make_float2(-p.lng_s.x, -p.lng_s.y) : p.lng_s;
+                hop_fwd_ffr(acc, p.lng + ((size_t)(P * 4 + mu) * 6) * vs + i, p.in, f3, vs, s);
+                hop_bwd_ffr(acc, p.lng + ((size_t)(Q * 4 + mu) * 6) * vs + b3, p.in, b3, vs, s);
             }
         }
     }
@@ -393,16 +440,22 @@ __global__ void __launch_bounds__(kBlock, 4) dslash_kernel(const DslashParams<A>
 }
 
 template <class A, int EPI>
-static void launch_one(const DslashParams<A>& p, bool naik, cudaStream_t s) {
+static void launch_one(const DslashParams<A>& p, int naik, cudaStream_t s) {
     const int blocks = blocks_for(p.i1 - p.i0);
+    if constexpr (std::is_same<A, ArithFF>::value) {
+        if (naik == 2) {
+            dslash_kernel<A, 2, EPI><<<blocks, kBlock, 0, s>>>(p);
+            return;
+        }
+    }
     if (naik)
-        dslash_kernel<A, true, EPI><<<blocks, kBlock, 0, s>>>(p);
+        dslash_kernel<A, 1, EPI><<<blocks, kBlock, 0, s>>>(p);
     else
-        dslash_kernel<A, false, EPI><<<blocks, kBlock, 0, s>>>(p);
+        dslash_kernel<A, 0, EPI><<<blocks, kBlock, 0, s>>>(p);
 }
 
 template <class A>
-static void launch_any(const DslashParams<A>& p, bool naik, Epilogue epi, cudaStream_t s) {
+static void launch_any(const DslashParams<A>& p, int naik, Epilogue epi, cudaStream_t s) {
     switch (epi) {
         case EPI_PLAIN: launch_one<A, EPI_PLAIN>(p, naik, s); break;
         case EPI_AXPY: launch_one<A, EPI_AXPY>(p, naik, s); break;
@@ -430,8 +483,9 @@ void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const flo
                       float4* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
                       double* partials, cudaStream_t s) {
     DslashParams<ArithFF> p{g, out_parity, L.fatff, L.lngff, in, out, src, m2,
-                            host_ff_from_double(m2), scal, partials, 0, g.vh};
-    launch_any(p, L.lngff != nullptr, epi, s);
+                            host_ff_from_double(m2), scal, partials, 0, g.vh, L.lng_inv_scale_ff};
+    const bool two_row = L.lng_inv_scale_ff.x != 0.f;
+    launch_any(p, L.lngff == nullptr ? 0 : two_row ? 2 : 1, epi, s);
 }
 
 void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const float2* lng,

@@ -130,6 +130,25 @@ __device__ __forceinline__ void ff_row_bwd(FFAcc& re, FFAcc& im, float4 u0, floa
     ff_merge(im, hi);
 }
 
+// s * conj(a1 b2 - a2 b1) for complex float-float words (re_hi, re_lo, im_hi,
+// im_lo) and a real float-float s: one entry of the third row of a scaled
+// SU(3) matrix from its first two rows (Sec. 3.3's reconstruction, with s =
+// eta / scale).
+__device__ __forceinline__ float4 ff_cross_conj_scaled(float4 a1, float4 b2, float4 a2, float4 b1, float2 s) {
+    FFAcc re = ff_prod(a1.x, a1.y, b2.x, b2.y);  // a1r b2r - a1i b2i - a2r b1r + a2i b1i
+    ff_mac(re, -a1.z, -a1.w, b2.z, b2.w);
+    ff_mac(re, -a2.x, -a2.y, b1.x, b1.y);
+    ff_mac(re, a2.z, a2.w, b1.z, b1.w);
+    FFAcc im = ff_prod(a1.x, a1.y, b2.z, b2.w);  // a1r b2i + a1i b2r - a2r b1i - a2i b1r
+    ff_mac(im, a1.z, a1.w, b2.x, b2.y);
+    ff_mac(im, -a2.x, -a2.y, b1.z, b1.w);
+    ff_mac(im, -a2.z, -a2.w, b1.x, b1.y);
+    const float2 r = ff_result(re), i = ff_result(im);
+    const float2 pr = ff_result(ff_prod(s.x, s.y, r.x, r.y));
+    const float2 pi = ff_result(ff_prod(-s.x, -s.y, i.x, i.y));
+    return make_float4(pr.x, pr.y, pi.x, pi.y);
+}
+
 // ---------------------------------------------- float-float scalar algebra
 // Values are float2 (hi, lo).  Error about 2^-48 relative per operation.
 __device__ __forceinline__ float2 ff_renorm(float s, float e) {

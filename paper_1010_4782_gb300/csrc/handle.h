@@ -32,7 +32,8 @@ struct stag_handle {
     double2* fat64 = nullptr;
     double2* lng64 = nullptr;
     float4* fatff = nullptr;
-    float4* lngff = nullptr;
+    float4* lngff = nullptr;  // [2][4][6][vs] when long_recon = 12 (allocated at the nine-entry size)
+    float2 lng_s = {0.f, 0.f};  // long_recon = 12: 1 / long_scale as float-float
     // vectors: 16 bytes per complex, [3][vs]
     double2 *x = nullptr, *r = nullptr, *ad = nullptr, *b = nullptr;
     void* d = nullptr;   // CG direction (F64 or FF)

@@ -849,7 +849,7 @@ void apply_A_q(stag_ptnet* n, const double2* p, double2* q) {
         float4* u = static_cast<float4*>(h->u);
         float4* t = static_cast<float4*>(h->t);
         float4* o = reinterpret_cast<float4*>(h->ad);
-        const LinkSet L{h->fat64, h->lng64, h->fatff, h->lngff};
+        const LinkSet L{h->fat64, h->lng64, h->fatff, h->lngff, h->lng_s};
         launch_to_ff(g, p, u, h->s);
         launch_dslash_ff(g, 1, L, u, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
         launch_dslash_ff(g, 0, L, t, o, EPI_AXPY, u, h->mass * h->mass, nullptr, nullptr, h->s);

@@ -20,7 +20,8 @@ struct LinkSet {
     const double2* fat64;  // F64 SoA links (always present)
     const double2* lng64;  // nullptr: no Naik term
     const float4* fatff;   // FF SoA links (nullptr unless FF arithmetic is enabled)
-    const float4* lngff;
+    const float4* lngff;   // FF Naik links: [2][4][9][vs], or [2][4][6][vs] when lng_inv_scale_ff != 0
+    float2 lng_inv_scale_ff = make_float2(0.f, 0.f);  // 1 / scale of the two-row Naik links, float-float
 };
 
 // ---- packing (pack.cu)
@@ -28,6 +29,11 @@ struct LinkSet {
 // in FP64 and, where the pointer is not null, float-float, FP32, FP16 and BF16.
 void launch_pack_links(const Geom& g, const double* aos, double2* soa64, float4* soaff,
                        float2* soa32, __half2* soa16, __nv_bfloat162* soab16, cudaStream_t s);
+// AoS links -> float-float [2][4][6][vs]: the first two rows, eta folded
+void launch_pack_links_ff_rows2(const Geom& g, const double* aos, float4* soaff_r, cudaStream_t s);
+// max over the AoS links L of |L^dag L / c^2 - 1| and |det L / c^3 - 1| into *maxdev
+// (a float's bits in an unsigned int, zeroed by the caller)
+void launch_check_scaled_su3(const Geom& g, const double* aos, double c, unsigned int* maxdev, cudaStream_t s);
 // AoS links -> FP32 [2][4][6][vs]: the first two rows, eta folded (12-parameter form)
 void launch_pack_links_rows2(const Geom& g, const double* aos, float2* soa32r, cudaStream_t s);
 // ABI vector [vh][3] complex128 (device) <-> F64 SoA [3][vs]

@@ -75,3 +75,29 @@ def test_null_handle_calls(lib):
     assert lib.stag_kernel_stats(None, 0, None, None) == binding.STAG_ERR_INVALID_ARG
     assert lib.stag_device_bytes(None) == 0
     assert isinstance(binding.stag_last_error(None), str)
+
+
+@pytest.mark.parametrize("case", ["recon_7", "f64", "no_naik", "zero_scale", "nan_scale", "link_recon_7"])
+def test_create_rejects_bad_link_forms(lib, case):
+    """Option checks of the 12-parameter link forms, all made before any device work."""
+    dims = (4, 4, 4, 4)
+    links = np.zeros(4 ** 4 * 36, dtype=np.complex128)
+    o = binding.stag_default_options()
+    o.arith, o.long_recon, o.long_scale = binding.STAG_ARITH_FF, 12, -1.0 / 24.0
+    naik = links
+    if case == "recon_7":
+        o.long_recon = 7
+    elif case == "f64":
+        o.arith = binding.STAG_ARITH_F64
+    elif case == "no_naik":
+        naik = None
+    elif case == "zero_scale":
+        o.long_scale = 0.0
+    elif case == "nan_scale":
+        o.long_scale = float("nan")
+    else:
+        o.long_recon, o.link_recon = 0, 7
+    with pytest.raises(binding.StagError) as e:
+        binding.stag_create_ex(links, naik, dims, 0.1, o)
+    assert e.value.code == binding.STAG_ERR_INVALID_ARG
+    assert "recon" in binding.stag_last_error(None)

@@ -24,6 +24,8 @@ def test_lattice_totals_match_the_paper():
 def test_compulsory_and_naik_figures():
     assert accounting.compulsory_bytes_per_site(False) == 1248
     assert accounting.compulsory_bytes_per_site(True) == 2400
+    assert accounting.compulsory_bytes_per_site(True, long_entries=6) == 2016  # 8 x 144 + 8 x 96 + 96
+    assert accounting.compulsory_bytes_per_site(False, long_entries=6) == 1248
     assert accounting.paper_bytes_per_site(True) == 3120
     assert accounting.flops_per_site(True) == 1152
     assert accounting.compulsory_bytes_per_site(True, elem_bytes=4) == 1200

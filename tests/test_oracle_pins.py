@@ -292,3 +292,25 @@ def test_gauge_field_is_su3():
     fat, _ = inputs.asqtad_form_fields(dims)
     f = fat.reshape(-1, 3, 3)
     assert np.abs(np.conj(np.swapaxes(f, -1, -2)) @ f - eye).max() > 1e-3
+
+
+def test_naik_links_are_scaled_su3_with_eta_folded():
+    """The asqtad-form Naik links are c U with c = -1/24 and U in SU(3).  After
+    eta is folded in (L' = eta L), the third row is (eta / c) conj(row0' x row1'),
+    since eta^2 = 1: the identity behind the two-row float-float Naik links.
+    With the opposite sign of c the rebuilt row has the wrong sign (det(-U) = -1
+    for 3x3), which is why the library checks det L / c^3 = 1 and not only
+    unitarity."""
+    dims = (4, 6, 2, 4)
+    _, lng = inputs.asqtad_form_fields(dims)
+    c = inputs.NAIK_COEFF
+    folded = oracle.fold_eta(lng, dims)                              # [t][z][y][x][mu][3][3]
+    e = np.moveaxis(oracle.eta(dims), 0, -1)[..., None]              # [t][z][y][x][mu][1]
+    rebuilt = (e / c) * np.conj(np.cross(folded[..., 0, :], folded[..., 1, :]))
+    assert np.abs(rebuilt - folded[..., 2, :]).max() < 1e-15
+    assert np.abs(e).min() == 1.0 and (e < 0).any() and (e > 0).any()
+    u = (lng / c).reshape(-1, 3, 3)
+    assert np.abs(np.linalg.det(u) - 1.0).max() < 1e-13
+    assert np.abs(np.linalg.det(lng.reshape(-1, 3, 3) / -c) + 1.0).max() < 1e-13
+    wrong = (e / -c) * np.conj(np.cross(folded[..., 0, :], folded[..., 1, :]))
+    assert np.abs(wrong + folded[..., 2, :]).max() < 1e-15

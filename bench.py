@@ -497,7 +497,7 @@ def run_batched(args):
         seq64, it64 = sequential(binding.STAG_ARITH_F64, binding.STAG_INNER_NONE)
     rb, bsz, ms = tuning
     vh = accounting.half_sites(BATCH_MAIN)
-    bytes_launch = vh * (16 * 72 + BATCH_NRHS * (24 + 24))  # FP32 links once + 16 RHS in and out
+    bytes_launch = vh * accounting.multi_rhs_bytes_per_site(BATCH_NRHS)  # FP32 links once + each RHS in and out
     peak, peak_src = measured_peaks()
     achieved = bytes_launch / (ms / 1e3) / 1e9
     line = {

@@ -37,6 +37,13 @@ def compulsory_bytes_per_site(naik: bool = False, elem_bytes: int = 8, long_entr
     return int(links * s + 2 * VECTOR_BYTES_F64 * s)
 
 
+def multi_rhs_bytes_per_site(nrhs: int, naik: bool = True) -> int:
+    """Multi-RHS half-Dslash in FP32: each FP32 link once (72 B) and, per
+    right-hand side, its input vector once and its output once (24 + 24 B).
+    16 RHS with Naik: 16 x 72 + 16 x 48 = 1920 B."""
+    return hops(naik) * (LINK_BYTES_F64 // 2) + nrhs * 2 * (VECTOR_BYTES_F64 // 2)
+
+
 def flops_per_site(naik: bool = False) -> int:
     """Sec. 2: 576 flops per site for the one-hop D chi(x)."""
     return hops(naik) * FLOPS_PER_HOP

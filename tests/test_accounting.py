@@ -30,3 +30,6 @@ def test_compulsory_and_naik_figures():
     assert accounting.flops_per_site(True) == 1152
     assert accounting.compulsory_bytes_per_site(True, elem_bytes=4) == 1200
     assert accounting.compulsory_bytes_per_site(False, elem_bytes=2) == 312
+    assert accounting.multi_rhs_bytes_per_site(16) == 1920
+    assert accounting.multi_rhs_bytes_per_site(1) == 1200  # one RHS: the FP32 single-RHS figure
+    assert accounting.multi_rhs_bytes_per_site(8, naik=False) == 8 * 72 + 8 * 48

@@ -156,3 +156,88 @@ def test_fcg_identity_is_cg_and_exact_inverse_is_one_step():
     x1, it1 = ptnet.fcg(op.apply_A, lambda r: ainv @ r, b, tol=1e-10)
     assert it1 <= 1
     assert np.linalg.norm(a @ x1 - b) <= 1e-10 * np.linalg.norm(b)
+
+
+# ----------------------------------------------------- loss: free-field closed forms
+def _unit_links(dims):
+    lx, ly, lz, lt = dims
+    u = np.zeros((lt, lz, ly, lx, 4, 3, 3), dtype=np.complex128)
+    u[..., 0, 0] = u[..., 1, 1] = u[..., 2, 2] = 1.0
+    return u
+
+
+def _plane_wave_even(dims, n, colour):
+    """exp(i p.x) e_colour on even sites, p_mu = 2 pi n_mu / L_mu, and
+    lambda = m^2 + 4 sum sin^2 p_mu without the m^2 (the free-field spectrum of
+    A = m^2 - D^2 for the paper's D, Eqs. (3)-(5), no factor 1/2)."""
+    x, y, z, t = oracle.coordinates(dims)
+    p = [2 * np.pi * n[mu] / dims[mu] for mu in range(4)]
+    phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    full = np.zeros(phase.shape + (3,), dtype=np.complex128)
+    full[..., colour] = phase
+    return oracle.restrict(full, dims, 0), 4.0 * float(np.sum(np.sin(p) ** 2))
+
+
+def _scalar_net(fat, dims, c):
+    """Three one-channel layers on the identity path: M = c * identity."""
+    w1 = np.zeros((9, 1, 1), dtype=np.complex128)
+    w1[0, 0, 0] = c
+    one = np.zeros((9, 1, 1), dtype=np.complex128)
+    one[0, 0, 0] = 1.0
+    return ptnet.PTNet(fat, dims, [w1, one, one.copy()])
+
+
+LOSS_CASES = [((0, 0, 0, 0), 0.5), ((1, 0, 0, 0), 0.3), ((1, 2, 0, 1), 0.1), ((2, 1, 3, 5), 0.7)]
+
+
+@pytest.mark.parametrize("n,m", LOSS_CASES)
+def test_loss_closed_form_single_plane_wave(n, m):
+    """Free field, residual r = v a plane wave with A v = lambda v, target e = v / lambda
+    (the exact correction).  With M = c * identity, A (M r - e) = (c lambda - 1) v and
+    A e = v, so L = (c lambda - 1)^2: (lambda - 1)^2 for c = 1 and 1 for c = 0.  The
+    cases have lambda from 0.25 to about 14, so normalising by |e|^2 (a factor lambda^2),
+    putting |d|^2 in the numerator (a factor 1 / lambda^2) or dropping the square all
+    change the value."""
+    dims = (4, 6, 4, 8)
+    op = oracle.Operator(_unit_links(dims), None, m, dims)
+    v, lam_free = _plane_wave_even(dims, n, 1)
+    lam = m * m + lam_free
+    e = v / lam
+    for c in (1.0, 0.0, 0.37, -0.8):
+        net = _scalar_net(_unit_links(dims), dims, c)
+        want = (c * lam - 1.0) ** 2
+        assert net.loss(v, e, op.apply_A) == pytest.approx(want, rel=1e-12, abs=1e-24)
+    assert lam != pytest.approx(1.0)
+
+
+def test_loss_closed_form_two_plane_waves_and_polynomial_network():
+    """Free field, r = v1 + v2 (orthogonal plane waves, eigenvalues l1 != l2), e = v1 / l1 +
+    v2 / l2.  The tied degree-1 network M = a + b (A - m^2) (a pinned form) maps v_k to
+    (a + b (l_k - m^2)) v_k, so with g_k = (a + b (l_k - m^2)) l_k - 1:
+        L = (g1^2 |v1|^2 + g2^2 |v2|^2) / (|v1|^2 + |v2|^2).
+    A wrong weighting of the two modes (|e|^2 or |d|^2 norms) changes this value."""
+    dims = (4, 4, 6, 4)
+    m, a, b = 0.25, 0.6, -0.07
+    fat = _unit_links(dims)
+    op = oracle.Operator(fat, None, m, dims)
+    v1, f1 = _plane_wave_even(dims, (1, 0, 0, 0), 0)
+    v2, f2 = _plane_wave_even(dims, (1, 1, 2, 1), 2)
+    l1, l2 = m * m + f1, m * m + f2
+    assert abs(l1 - l2) > 1.0
+    w1 = np.zeros((9, 2, 1), dtype=np.complex128)
+    w1[0, 0, 0] = 1.0
+    w1 += _d_weights(2, 1, 1, 0)
+    w2 = np.zeros((9, 2, 2), dtype=np.complex128)
+    w2[0, 0, 0] = a
+    w2[0, 1, 1] = b
+    net = ptnet.PTNet(fat, dims, [w1, w2, ptnet.adjoint_weights(w1)])
+    g1 = (a + b * f1) * l1 - 1.0
+    g2 = (a + b * f2) * l2 - 1.0
+    n1, n2 = np.vdot(v1, v1).real, np.vdot(v2, v2).real
+    want = (g1 * g1 * n1 + g2 * g2 * n2) / (n1 + n2)
+    got = net.loss(v1 + v2, v1 / l1 + v2 / l2, op.apply_A)
+    assert got == pytest.approx(want, rel=1e-12)
+    # the same pair under the two plausible wrong normalisations differs from the pin
+    ne = np.vdot(v1 / l1 + v2 / l2, v1 / l1 + v2 / l2).real
+    wrong_e_norm = (g1 * g1 * n1 + g2 * g2 * n2) / ne
+    assert abs(wrong_e_norm - want) > 0.1 * want

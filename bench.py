@@ -73,6 +73,43 @@ def parse_args():
 
 
 # ------------------------------------------------------------------ helpers
+def workload_config(dims, mass, world):
+    """The `config` object of the default workload, identical in both arms."""
+    return {
+        "workload": f"staggered even-odd CG, asqtad-form (fat 0.6U_a+0.4U_b, Naik -U_c/24), "
+                    f"{'x'.join(map(str, dims))}, m={mass}, tol={TOL}",
+        "lattice": list(dims),
+        "mass": mass,
+        "tol": TOL,
+        "step": "stag_create_ex + stag_cg_solve + stag_destroy (device-resident inputs)",
+        "l2": "inputs (2.4 GB AoS links, 4.9 GB packed) larger than L2; no flush",
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+    }
+
+
+def host_cpu():
+    """(CPU model, logical cores) of this host, from lscpu or /proc/cpuinfo."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return model or "unknown", os.cpu_count() or 1
+
+
 def dist_env():
     from paper_1010_4782_gb300.replicas import dist_env as _env
 
@@ -224,9 +261,10 @@ def run_ours(args):
             binding.stag_destroy(h)
         return info
 
-    # ---- warm-up, then K timed steps (device-resident inputs)
+    # ---- warm-up, then K timed steps (device-resident inputs) with the library's
+    # defaults (CUDA graphs of check_interval iterations, no per-kernel events)
     for _ in range(args.warmup):
-        step(fat_d, lng_d, b_d, x_d, record=False)
+        step(fat_d, lng_d, b_d, x_d, timing=False, record=False)
     torch.cuda.synchronize(dev)
     barrier()
     clocks = ClockSampler(local)
@@ -236,7 +274,7 @@ def run_ours(args):
     ev0.record(stream)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step(fat_d, lng_d, b_d, x_d)
+        step(fat_d, lng_d, b_d, x_d, timing=False)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     host_s = time.perf_counter() - t0
@@ -247,6 +285,12 @@ def run_ours(args):
     value = reps.time_per_solve(elapsed_s, args.steps)
     infos = rec["infos"]
     iters = infos[-1]["iters"]
+    gpu_launches = int(sum_over_ranks(rec["launches"]))
+
+    # ---- one more, instrumented solve (CUDA events around every CG kernel, no graphs),
+    # outside the timed region: per-kernel durations for the roofline and the shares
+    rec["k_ms"], rec["k_n"] = [0.0] * 4, [0] * 4
+    inst = step(fat_d, lng_d, b_d, x_d, timing=True)
 
     # ---- dominant kernel: the half-Dslash D_oe (Naik), CUDA events on the library's stream
     naik = True
@@ -269,14 +313,55 @@ def run_ours(args):
                   f"arithmetic ({kernel_key})",
         "algorithmic_bytes_per_launch": bytes_per_launch,
         "avg_launch_ms": round(oe_ms, 4),
+        "launch_times_from": "CUDA events on the library's stream around every launch of one instrumented "
+                             "solve after the timed steps",
         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
     }
     k_total = sum(rec["k_ms"])
     kernel_shares = {binding.KERNEL_NAMES[k]: {"launches": rec["k_n"][k], "ms": round(rec["k_ms"][k], 2),
                                                "share_of_cg_kernels": round(rec["k_ms"][k] / k_total, 4)}
                      for k in range(4)}
-    gpu_launches = int(sum_over_ranks(rec["launches"]))
-    solve_ms = statistics.median(i["time_ms"] for i in infos)
+    kernel_shares["instrumented_solve_ms"] = round(inst["time_ms"], 2)
+    solve_ms = statistics.median(i["time_ms"] for i in infos[:args.steps])
+
+    # ---- the native-FP64 half-Dslash D_oe (Naik) on its roofline: min(HBM, FP64 FMA).
+    # Per-launch time from a short instrumented FP64 CG run (events around every launch);
+    # the DFMA ceiling is measured by the library's FMA probe on this GPU.
+    roof64 = None
+    if not args.no_forms:
+        o64 = options(binding.STAG_ARITH_F64, True)
+        h64 = binding.stag_create_ex(fat_d, lng_d, dims, args.mass, o64)
+        try:
+            binding.stag_set_stream(h64, stream)
+            x64i = torch.zeros_like(b_d)
+            binding.stag_cg_solve(h64, b_d, x64i, TOL, 96)
+            ms64, n64 = binding.stag_kernel_stats(h64, binding.STAG_KERNEL_DSLASH_OE)
+        finally:
+            binding.stag_destroy(h64)
+        del x64i
+        dfma_rate = binding.stag_measure_fma_rate(64)
+        ffma_rate = binding.stag_measure_fma_rate(32)
+        t64 = ms64 / max(1, n64) / 1e3
+        bytes64 = accounting.compulsory_bytes_per_site(naik) * vh
+        dfma64 = accounting.fma_per_site(naik) * vh
+        t_hbm, t_alu = bytes64 / (peak * 1e9), dfma64 / dfma_rate
+        roof64 = {
+            "bound": "hbm" if t_hbm >= t_alu else "alu",
+            "kernel": "half-Dslash D_oe, Naik, native FP64 (dslash_kernel<ArithF64>)",
+            "avg_launch_ms": round(t64 * 1e3, 4),
+            "launches_timed": n64,
+            "algorithmic_bytes_per_launch": bytes64,
+            "achieved_gbs": round(bytes64 / t64 / 1e9, 1),
+            "hbm_peak_gbs": peak,
+            "hbm_frac": round(bytes64 / t64 / 1e9 / peak, 4),
+            "dfma_per_launch": dfma64,
+            "achieved_dfma_per_s": round(dfma64 / t64, 1),
+            "dfma_peak_per_s": round(dfma_rate, 1),
+            "dfma_frac": round(dfma64 / t64 / dfma_rate, 4),
+            "ffma_peak_per_s": round(ffma_rate, 1),
+            "frac_of_binding_bound": round(max(t_hbm, t_alu) / t64, 4),
+            "peak_sources": "hbm: MEASURED_PEAKS.json hbm_gbs; dfma/ffma: measured now by stag_measure_fma_rate",
+        }
     # paper's convention: Dslash flops only, two half-Dslash per CG iteration
     gflops = 2 * flops_per_launch * iters / (solve_ms / 1e3) / 1e9
 
@@ -373,17 +458,9 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "ff64" if arith == binding.STAG_ARITH_FF else "f64",
             "data": "synthetic (seeded SU(3) fields exp(0.3 i H), Gaussian source)",
-            "config": {
-                "workload": f"staggered even-odd CG, asqtad-form (fat 0.6U_a+0.4U_b, Naik -U_c/24), "
-                            f"{'x'.join(map(str, dims))}, m={args.mass}, tol={TOL}",
-                "lattice": list(dims),
-                "mass": args.mass,
-                "tol": TOL,
-                "step": "stag_create_ex + stag_cg_solve + stag_destroy (device-resident inputs)",
-                "l2": "inputs (2.4 GB AoS links, 4.9 GB packed) larger than L2; no flush",
-                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            },
+            "config": workload_config(dims, args.mass, world),
             "roofline": roofline,
+            "roofline_f64": roof64,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": gpu_launches,
@@ -736,23 +813,165 @@ def run_decomposed(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(fat, lng, b, dims, mass, iters, restarts):
-    """Oracle: initial residual + one Fig. 1 iteration (two A applications) at full size."""
+# ------------------------------------------- the oracle on the host cores
+def _slab_worker(rank, n_workers, shm_names, shapes, dims, mass, halo, reps, start, out_q):
+    """One process of the all-core oracle timing: oracle.Operator.apply_A, unchanged, on
+    this process's t-slab widened by `halo` t-slices on each side (periodic).  Reports
+    "ready" once its slab is built, waits for `start`, applies A `reps` times, reports
+    "done" with its own time and then the interior rows of the result."""
+    import numpy as np
+    from multiprocessing import shared_memory
+
+    import oracle
+
+    try:
+        shms = [shared_memory.SharedMemory(name=n) for n in shm_names]
+        try:
+            arrs = [np.ndarray(shp, dtype=np.complex128, buffer=m.buf) for m, shp in zip(shms, shapes)]
+            fat, chi = arrs[0], arrs[-1]
+            lng = arrs[1] if len(arrs) == 3 else None
+            lx, ly, lz, lt = dims
+            ts = lt // n_workers
+            idx = [(rank * ts - halo + k) % lt for k in range(ts + 2 * halo)]
+            dims_s = (lx, ly, lz, ts + 2 * halo)
+            op = oracle.Operator(fat[idx], None if lng is None else lng[idx], mass, dims_s)
+            v = oracle.restrict(chi[idx], dims_s, 0)
+            del fat, lng, chi, arrs
+        finally:
+            for m in shms:
+                m.close()
+    except BaseException as e:
+        out_q.put(("error", rank, repr(e)))
+        raise
+    out_q.put(("ready", rank))
+    start.wait()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        y = op.apply_A(v)
+    dt = time.perf_counter() - t0
+    out_q.put(("done", rank, dt))
+    v3h = lx * ly * lz // 2
+    out_q.put(("rows", rank, y[halo * v3h:(halo + ts) * v3h]))
+
+
+def _slab_workers(lt, cores, halo):
+    """Most processes w <= cores (at most 16) that split lt into equal slabs of even
+    length (so each slab's parity matches the lattice's), each narrower than the lattice
+    once widened by the halo; 1 when no split helps."""
+    for w in range(min(16, cores), 1, -1):
+        if lt % w == 0 and (lt // w) % 2 == 0 and lt // w + 2 * halo < lt:
+            return w
+    return 1
+
+
+def oracle_apply_A_all_cores(fat, lng, b, dims, mass, reps):
+    """Time oracle.Operator.apply_A on the host cores: the lattice split into t-slabs, one
+    spawned process per slab, each applying the oracle's A, unchanged, to its slab widened
+    by the reach of A (2 t-slices one-hop, 6 with Naik) and keeping the interior rows.
+    Returns (seconds per A application over the whole lattice, processes, A b)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
     import numpy as np
 
     import oracle
 
+    halo = 6 if lng is not None else 2
+    w = _slab_workers(dims[3], os.cpu_count() or 1, halo)
+    if w == 1:
+        op = oracle.Operator(fat, lng, mass, dims)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            y = op.apply_A(b)
+        return (time.perf_counter() - t0) / reps, 1, y
+    chi = oracle.embed(b, dims, 0)
+    srcs = [fat] + ([lng] if lng is not None else []) + [chi]
+    shms = []
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    try:
+        for a in srcs:
+            m = shared_memory.SharedMemory(create=True, size=a.nbytes)
+            np.ndarray(a.shape, dtype=np.complex128, buffer=m.buf)[...] = a
+            shms.append(m)
+        for k in saved:  # one thread per process: the process count is the core count used
+            os.environ[k] = "1"
+        ctx = mp.get_context("spawn")
+        start = ctx.Event()
+        out_q = ctx.Queue()
+        procs = [ctx.Process(target=_slab_worker,
+                             args=(r, w, [m.name for m in shms], [a.shape for a in srcs], tuple(dims), mass,
+                                   halo, reps, start, out_q)) for r in range(w)]
+        for p in procs:
+            p.start()
+
+        inbox = {"ready": {}, "done": {}, "rows": {}}
+
+        def collect(kind):
+            """Wait until every process has sent a message of this kind (messages of
+            later kinds that arrive meanwhile are kept for their own wait)."""
+            while len(inbox[kind]) < w:
+                try:
+                    msg = out_q.get(timeout=5)
+                except Exception:
+                    if any(not p.is_alive() and p.exitcode for p in procs):
+                        raise RuntimeError("an oracle process died")
+                    continue
+                if msg[0] == "error":
+                    raise RuntimeError(f"oracle process {msg[1]} failed: {msg[2]}")
+                inbox[msg[0]][msg[1]] = msg[2:]
+            return inbox[kind]
+
+        try:
+            collect("ready")            # every slab built
+            t0 = time.perf_counter()
+            start.set()
+            collect("done")             # every process applied A reps times
+            dt = time.perf_counter() - t0
+            parts = {r: v[0] for r, v in collect("rows").items()}
+        finally:
+            for p in procs:
+                p.join(timeout=60)
+                if p.is_alive():
+                    p.terminate()
+        y = np.concatenate([parts[r] for r in range(w)])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        for m in shms:
+            m.close()
+            m.unlink()
+    return dt / reps, w, y
+
+
+def cpu_baseline(fat, lng, b, dims, mass, iters, restarts):
+    """The oracle on the host: Fig. 1 (cg_fig1, initial residual + one iteration = two A
+    applications) on one core, and A applied on all cores (t-slab processes); the value
+    scales the all-core time per A application to the GPU solve's A applications."""
+    import numpy as np
+
+    import oracle
+
+    model, ncpu = host_cpu()
     op = oracle.Operator(fat, lng, mass, dims)
     t0 = time.perf_counter()
     oracle.cg_fig1(op.apply_A, b, np.zeros_like(b), TOL, 1)
-    dt = time.perf_counter() - t0
-    per_a = dt / 2
+    dt1 = time.perf_counter() - t0
+    del op
+    per_a1 = dt1 / 2
+    per_aw, w, _ = oracle_apply_A_all_cores(fat, lng, b, dims, mass, reps=2)
     n_a = 1 + iters + (restarts + 1)
-    return {"value": round(per_a * n_a, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"numpy FP64 oracle (single thread), cg_fig1 on the full {'x'.join(map(str, dims))} "
-                      f"system: initial residual + 1 iteration = 2 A applications in {dt:.1f} s; "
+    return {"value": round(per_aw * n_a, 1), "unit": UNIT, "cores": w, "kind": "oracle",
+            "sample": f"numpy FP64 oracle on {'x'.join(map(str, dims))}: oracle.Operator.apply_A on {w} "
+                      f"processes (t-slabs widened by the reach of A, one thread each), 2 applications; "
                       f"value = time per A application x the {n_a} A applications of the GPU solve",
-            "per_A_application_s": round(per_a, 2)}
+            "per_A_application_s": round(per_aw, 3),
+            "single_core": {"per_A_application_s": round(per_a1, 3), "value": round(per_a1 * n_a, 1),
+                            "sample": "cg_fig1 on the full system: initial residual + 1 iteration = "
+                                      f"2 A applications in {dt1:.1f} s"},
+            "host_cpu": model, "host_logical_cores": ncpu}
 
 
 # ----------------------------------------------------------- reference arm
@@ -760,34 +979,31 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
-
-    import oracle
+    import oracle  # noqa: F401  (the arm runs the oracle only)
     from paper_1010_4782_gb300 import inputs
 
     dims = tuple(args.dims)
     fat, lng = inputs.asqtad_form_fields(dims)
     b = inputs.gaussian_even_source(dims, 0)
-    op = oracle.Operator(fat, lng, args.mass, dims)
-    for _ in range(args.warmup):
-        op.apply_A(b)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        op.apply_A(b)
-    per_a = (time.perf_counter() - t0) / args.steps
+    model, ncpu = host_cpu()
+    # warm-up applications, then K timed ones, all on the host cores
+    if args.warmup:
+        oracle_apply_A_all_cores(fat, lng, b, dims, args.mass, reps=args.warmup)
+    per_a, w, _ = oracle_apply_A_all_cores(fat, lng, b, dims, args.mass, reps=max(1, args.steps))
     if REFERENCE_ITERS is not None:
         n_a = REFERENCE_ITERS + 2
         value = per_a * n_a
-        sample = (f"numpy FP64 oracle (single thread): {args.steps} timed A applications on the full "
-                  f"{'x'.join(map(str, dims))} system; value = time per A application x {n_a} "
-                  f"A applications of a solve ({REFERENCE_ITERS} Fig. 1 iterations)")
+        sample = (f"numpy FP64 oracle: oracle.Operator.apply_A on {w} processes (t-slabs of "
+                  f"{'x'.join(map(str, dims))} widened by the reach of A, one thread each), {args.steps} timed "
+                  f"applications; value = time per A application x {n_a} A applications of a solve "
+                  f"({REFERENCE_ITERS} Fig. 1 iterations)")
     else:
         value = per_a
         sample = "time per A application (iteration count of the solve not recorded)"
     line = {
         "impl": "reference",
         "metric": METRIC,
-        "value": round(value, 2),
+        "value": round(value, 4),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
@@ -798,11 +1014,10 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded SU(3) fields exp(0.3 i H), Gaussian source)",
-        "config": {"workload": f"staggered even-odd CG, asqtad-form, {'x'.join(map(str, dims))}, "
-                               f"m={args.mass}, tol={TOL}", "lattice": list(dims)},
-        "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": workload_config(dims, args.mass, world),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": w, "kind": "oracle",
+                         "sample": sample, "host_cpu": model, "host_logical_cores": ncpu},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 

@@ -114,7 +114,9 @@ typedef struct {
                                all nine entries.                                              */
     int32_t reserved;       /* 0 */
     double long_scale;      /* long_recon = 12: the Naik links are long_scale x SU(3) (e.g. the
-                               Naik coefficient times a product of SU(3) links)               */
+                               Naik coefficient times a product of SU(3) links); accepted for
+                               1e-10 <= |long_scale| <= 1e18, where the float-float products
+                               of two stored entries stay normal FP32 numbers               */
     int32_t long_recon;     /* 12: the float-float Dirac kernels store two rows of each Naik
                                link and rebuild the third as (eta / long_scale) times the
                                conjugate cross product of the first two (the 12-parameter
@@ -387,6 +389,17 @@ int stag_dd_cg_solve(stag_dd* dd, const double* b_even, double* x_even, double t
 int64_t stag_dd_bytes_exchanged(const stag_dd* dd);
 int stag_dd_destroy(stag_dd* dd);
 
+/* Measured fused multiply-add rate of the current device, in FMA per second:
+ * bits = 64 for FP64 DFMA, 32 for FP32 FFMA.  A measurement helper for the
+ * arithmetic ceiling of the Dirac kernels' roofline: the paper counts each
+ * SU(3) x vector product of D as 36 real multiply-adds (Sec. 2, text after
+ * Eq. (5)), so a native-FP64 Naik half-Dslash site is 576 DFMA.  Runs
+ * independent FMA chains on every SM for about 0.1 s, timed with CUDA events
+ * after one warm-up launch on a private stream (it allocates 8 bytes and
+ * synchronises that stream).  Returns STAG_ERR_INVALID_ARG for other bits or a
+ * NULL output; the message is available from stag_last_error(NULL). */
+int stag_measure_fma_rate(int32_t bits, double* fma_per_second);
+
 /* Largest V/2 that stag_apply_A_noalloc accepts. */
 #define STAG_NOALLOC_MAX_HALF_SITES 65536
 
@@ -396,18 +409,26 @@ int stag_dd_destroy(stag_dd* dd);
  * device memory from their own pool, or that cannot accept the device-wide
  * synchronisation an allocation or free may cause).  It needs no handle.
  * links, naik_long (NULL = one-hop only): the link layout above, eta not
- * folded; in_even, out_even: [V/2][3] complex128, must not overlap.  Every
- * array must be device memory of the current device (host pointers are
- * rejected).  Native FP64 arithmetic.  The odd-site intermediate D_oe in is
- * kept in a fixed file-scope device array of STAG_NOALLOC_MAX_HALF_SITES sites
- * (3 MiB) that every GPU loading the library holds until the process exits;
- * larger lattices are rejected with STAG_ERR_INVALID_ARG.  The array is shared
- * by all calls: calls that overlap on the GPU (several host threads, or
- * several streams) race on it.  The first call on each device, with that
- * device current, looks up the array's device address; make that first call
- * before any stream capture.  Work is enqueued on cuda_stream (NULL = legacy
- * default stream) and the call returns after it completes.  Errors are
- * reported by status; the message is available from stag_last_error(NULL). */
+ * folded; in_even, out_even: [V/2][3] complex128; out must not overlap in
+ * or the links (any byte in common is rejected).  Every array must be device
+ * memory of the current device (host pointers are rejected).  Native FP64
+ * arithmetic.  The odd-site intermediate D_oe in is kept in a fixed
+ * file-scope device array of STAG_NOALLOC_MAX_HALF_SITES sites (3 MiB) that
+ * every GPU loading the library holds until the process exits; larger
+ * lattices are rejected with STAG_ERR_INVALID_ARG.  The array is shared by
+ * all calls: calls that overlap on the GPU (several host threads, or several
+ * streams) race on it.
+ * The guarantee of no allocation holds from the second call on each device.
+ * CUDA loads a library's device code lazily, so the first call on a device
+ * (or any earlier launch from this library there) loads the module: that
+ * load allocates the array and the code, and may synchronise the device.
+ * Make that first call at set-up time, before any stream capture.  The first
+ * call in each CUDA context also looks up the array's device address and
+ * caches it for that context; after a device reset (a new context) the next
+ * call loads the module and looks the address up again.  Work is enqueued on
+ * cuda_stream (NULL = legacy default stream) and the call returns after it
+ * completes.  Errors are reported by status; the message is available from
+ * stag_last_error(NULL). */
 int stag_apply_A_noalloc(const double* links, const double* naik_long, const int32_t dims[4],
                          double mass, const double* in_even, double* out_even, void* cuda_stream);
 

@@ -64,6 +64,7 @@ EXPORTED = (
     "stag_device_bytes",
     "stag_launch_count",
     "stag_apply_A_noalloc",
+    "stag_measure_fma_rate",
     "stag_batch_create",
     "stag_batch_set_stream",
     "stag_batch_solve",
@@ -177,6 +178,7 @@ def load(path: str | None = None):
     lib.stag_launch_count.argtypes = [H]
     lib.stag_launch_count.restype = ctypes.c_int64
     lib.stag_apply_A_noalloc.argtypes = [P, P, ctypes.POINTER(i32), d, P, P, P]
+    lib.stag_measure_fma_rate.argtypes = [i32, ctypes.POINTER(d)]
     PP = ctypes.POINTER(ctypes.c_void_p)
     lib.stag_batch_create.argtypes = [ctypes.POINTER(H), i32, PP, PP, ctypes.POINTER(i32),
                                       ctypes.POINTER(d), ctypes.POINTER(stag_options)]
@@ -327,6 +329,13 @@ def stag_apply_A_noalloc(links, naik_long, dims, mass, inp, out, stream=None):
     raw = getattr(stream, "cuda_stream", stream)
     _check(load().stag_apply_A_noalloc(_ptr(links), _ptr(naik_long), dd, float(mass), _ptr(inp), _ptr(out),
                                         ctypes.c_void_p(raw or 0)))
+
+
+def stag_measure_fma_rate(bits):
+    """Measured FMA per second of the current device (bits = 64: DFMA, 32: FFMA)."""
+    rate = ctypes.c_double(0.0)
+    _check(load().stag_measure_fma_rate(bits, ctypes.byref(rate)))
+    return rate.value
 
 
 def _ptr_array(arrs):

@@ -107,6 +107,9 @@ void end_call(stag_handle* h) { cuda_check(h, cudaStreamSynchronize(h->s), "cuda
 // row rebuilt from the first two then agrees with the stored one to about this
 // relative size, far below the solver's tolerances.
 constexpr float kLongReconMaxDeviation = 1e-12f;
+// Range of |long_scale| accepted with long_recon = 12 (see stag_create_ex).
+constexpr double kLongScaleMin = 1e-10;
+constexpr double kLongScaleMax = 1e18;
 
 bool use_ff(const stag_handle* h) { return h->opt.arith == STAG_ARITH_FF; }
 
@@ -717,11 +720,16 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
             fail(nullptr, STAG_ERR_INVALID_ARG, "12-parameter links need the one-hop operator and inner = F32");
         if (o.long_recon != 0 && o.long_recon != 12)
             fail(nullptr, STAG_ERR_INVALID_ARG, "long_recon must be 0 or 12");
+        // The rebuilt third row is formed from products of two stored entries, of
+        // size long_scale^2, in float-float: above about 1.8e19 that overflows
+        // FP32, and below about 1e-12 the low words of the products go
+        // subnormal and lose the float-float precision.  The accepted range
+        // keeps a margin on both sides.
         if (o.long_recon == 12 &&
             (naik_long == nullptr || o.arith != STAG_ARITH_FF || !std::isfinite(o.long_scale) ||
-             !(std::fabs(o.long_scale) > 1e-20 && std::fabs(o.long_scale) < 1e20)))
+             !(std::fabs(o.long_scale) >= kLongScaleMin && std::fabs(o.long_scale) <= kLongScaleMax)))
             fail(nullptr, STAG_ERR_INVALID_ARG,
-                 "long_recon = 12 needs Naik links, arith = FF and a finite long_scale with 1e-20 < |long_scale| < 1e20");
+                 "long_recon = 12 needs Naik links, arith = FF and a finite long_scale with 1e-10 <= |long_scale| <= 1e18");
         if (o.inner != STAG_INNER_NONE &&
             (o.reliable_interval < 1 || !(o.reliable_delta > 0.0 && o.reliable_delta < 1.0)))
             fail(nullptr, STAG_ERR_INVALID_ARG, "reliable_interval must be >= 1 and reliable_delta in (0, 1)");

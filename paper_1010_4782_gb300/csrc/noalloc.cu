@@ -13,8 +13,10 @@
 // The work array holds at most kNoallocMaxHalfSites sites (3 MiB); every GPU
 // that loads the library keeps it until the process exits.  All calls share
 // it, so calls that overlap on the GPU race; each call overwrites the part it
-// uses before reading it.  Its device address is looked up once per device,
-// on the first call made with that device current.
+// uses before reading it.  Its device address is looked up on the first call
+// made in each CUDA context (with that context's device current) and cached
+// for that context only: after a device reset the next call looks it up again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,7 +37,48 @@ static __device__ __align__(256) double2 g_noalloc_scratch[3 * kNoallocMaxHalfSi
 namespace {
 
 std::mutex g_mu;
+// Per device: the context the cached address belongs to (cuCtxGetId, unique
+// for the process lifetime) and the array's device address in it.
+unsigned long long g_scratch_ctx[kNoallocMaxDevices] = {};
 double2* g_scratch_addr[kNoallocMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Identifier of the current CUDA context, or 0 when it cannot be had (the
+// caller then looks the address up on every call).  The driver functions are
+// fetched through the runtime, so the library needs no link to libcuda.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Do the byte ranges [a, a + na) and [b, b + nb) overlap?
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const char* pa = static_cast<const char*>(a);
+    const char* pb = static_cast<const char*>(b);
+    return pa < pb + nb && pb < pa + na;
+}
 
 // out(y) = D_{P,1-P} in (y), or m2 * src(y) - D in (y) when EPI; links and
 // vectors in the ABI layouts, eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}) applied
@@ -135,7 +178,6 @@ extern "C" int stag_apply_A_noalloc(const double* links, const double* naik_long
         return code;
     };
     if (!links || !in_even || !out_even || !dims) return fail(STAG_ERR_INVALID_ARG, "NULL argument");
-    if (in_even == out_even) return fail(STAG_ERR_INVALID_ARG, "in and out must not overlap");
     long long V = 1;
     for (int k = 0; k < 4; ++k) {
         if (dims[k] < 2 || dims[k] % 2)
@@ -147,6 +189,13 @@ extern "C" int stag_apply_A_noalloc(const double* links, const double* naik_long
                                               std::to_string(V / 2) + " sites exceeds its fixed work array of " +
                                               std::to_string(kNoallocMaxHalfSites) + " sites");
     if (!std::isfinite(mass)) return fail(STAG_ERR_INVALID_ARG, "mass must be finite");
+    const size_t vec_bytes = (size_t)(V / 2) * 3 * sizeof(double2);
+    const size_t link_bytes = (size_t)V * 4 * 9 * sizeof(double2);
+    if (ranges_overlap(in_even, vec_bytes, out_even, vec_bytes))
+        return fail(STAG_ERR_INVALID_ARG, "in and out must not overlap");
+    if (ranges_overlap(links, link_bytes, out_even, vec_bytes) ||
+        (naik_long && ranges_overlap(naik_long, link_bytes, out_even, vec_bytes)))
+        return fail(STAG_ERR_INVALID_ARG, "out must not overlap the links");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices)
         return fail(STAG_ERR_CUDA, "no usable current CUDA device");
@@ -157,12 +206,16 @@ extern "C" int stag_apply_A_noalloc(const double* links, const double* naik_long
     double2* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_addr[dev]) {
+        const unsigned long long ctx = current_context_id();
+        if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess)
+            if (e != cudaSuccess) {
+                g_scratch_addr[dev] = nullptr;
                 return fail(STAG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            }
             g_scratch_addr[dev] = static_cast<double2*>(p);
+            g_scratch_ctx[dev] = ctx;
         }
         scratch = g_scratch_addr[dev];
     }

@@ -24,8 +24,10 @@
 // Shared-memory operands use the canonical K-major layout without swizzle:
 // 8 rows x 16 bytes core matrices; the leading byte offset (LBO) steps to the
 // next core matrix along K, the stride byte offset (SBO) to the next group of
-// 8 rows.  Waits are bounded; a wait that runs out sets *err and the kernel
-// finishes without further MMAs.
+// 8 rows.  Waits are bounded; a wait that runs out sets *err, and the kernel
+// issues no further MMAs.  It then still waits - in order on each barrier, with
+// a longer limit - for every commit it has issued, so that TMEM is neither read
+// nor freed under an MMA that may still be writing it, before it deallocates.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -46,7 +48,8 @@ constexpr int kBKGroups = kPaths * 16 / 8;        // 18
 constexpr int kBSbo = kBKGroups * 128;            // 2304 B
 constexpr int kBBytes = 2 * kBSbo;                // 4608 B (N = 16: two 8-row groups)
 constexpr int kTmemCols = 64;                     // 48 used: 3 colours x N = 16
-constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls before giving up
+constexpr long long kWaitLimit = 1LL << 22;   // try_wait polls before giving up
+constexpr long long kDrainLimit = 1LL << 26;  // polls per outstanding commit after a give-up
 
 // smem layout: [A 2 x 12288][B 4608][2 mbarriers 16][tmem address 4]
 constexpr int kSmemBytes = kABytes + kBBytes + 32;
@@ -172,22 +175,30 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
     const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
     const uint32_t bar0 = smem_u32(bar), bar1 = smem_u32(bar + 1);
     bool ok = true;
+    // Per buffer barrier: commits issued and completions seen so far (the same
+    // in every thread).  A parity wait only tells the phase it names from the
+    // one before it, so completions are always waited for in order.
+    // (Scalars, not arrays indexed by b, so that they stay in registers.)
+    int issued0 = 0, issued1 = 0, seen0 = 0, seen1 = 0;
 
-    // waits for the n-th completion (n = 0, 1, ...) of buffer b's barrier
-    auto wait_buffer = [&](int b, int n) {
+    // waits for buffer b's next completion not yet seen; false after `limit` polls
+    auto wait_next = [&](int b, long long limit) {
+        int& seen = b ? seen1 : seen0;
         long long spins = 0;
-        while (ok && !mbar_try_wait(b ? bar1 : bar0, (uint32_t)(n & 1))) {
-            if (++spins > kWaitLimit) {
-                ok = false;
-                atomicExch(err, 1);
-            }
-        }
+        while (!mbar_try_wait(b ? bar1 : bar0, (uint32_t)(seen & 1)))
+            if (++spins > limit) return false;
+        ++seen;
+        return true;
     };
 
     for (int p = 0; p < kPaths; ++p) {
         const int b = p & 1;
-        if (p >= 2) {
-            wait_buffer(b, (p - 2) >> 1);  // the MMAs of path p - 2 read this buffer
+        if (p >= 2 && ok) {
+            // the MMAs of path p - 2 read this buffer
+            if (!wait_next(b, kWaitLimit)) {
+                ok = false;
+                atomicExch(err, 1);
+            }
             fence_after_sync();
         }
         if (active) {
@@ -233,29 +244,51 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
         fence_before_sync();
         ok = __syncthreads_and(ok ? 1 : 0) != 0;
         fence_after_sync();
-        if (tid == 0 && ok) {
+        if (ok) {
+            if (tid == 0) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const uint64_t da = smem_desc(aBase + b * kABuf + c * kAColour, 128, kASbo);
-                const uint64_t db = smem_desc(bBase + p * kAKGroups * 128, 128, kBSbo);
-                mma_bf16(tmem + 16 * c, da, db, p > 0 ? 1u : 0u);
+                for (int c = 0; c < 3; ++c) {
+                    const uint64_t da = smem_desc(aBase + b * kABuf + c * kAColour, 128, kASbo);
+                    const uint64_t db = smem_desc(bBase + p * kAKGroups * 128, 128, kBSbo);
+                    mma_bf16(tmem + 16 * c, da, db, p > 0 ? 1u : 0u);
+                }
+                mma_commit(b ? bar1 : bar0);
             }
-            mma_commit(b ? bar1 : bar0);
+            if (b)
+                ++issued1;
+            else
+                ++issued0;
         }
     }
-    // the last commit covers every MMA issued before it
-    wait_buffer((kPaths - 1) & 1, (kPaths - 1) >> 1);
+    // Every issued commit must have arrived before TMEM is read or freed.
+    // Normally only the last two paths' are outstanding.  After a wait that
+    // ran out (here or above) the remaining ones are waited for with the
+    // longer limit; if one of those runs out too, the kernel can no longer
+    // tell when the MMAs end and deallocates anyway - its output is discarded
+    // through *err.
+#pragma unroll 1
+    for (int b = 0; b < 2; ++b) {
+        while ((b ? seen1 : seen0) < (b ? issued1 : issued0)) {
+            if (wait_next(b, ok ? kWaitLimit : kDrainLimit)) continue;
+            if (ok) {
+                ok = false;
+                atomicExch(err, 1);
+                continue;
+            }
+            break;
+        }
+    }
     fence_after_sync();
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
 
     // accumulators -> registers (warp w holds rows 32 w .. 32 w + 31) -> output
     // one colour at a time: 16 accumulators live (warp-collective loads, uniform loop)
 #pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 3 && ok; ++c) {  // ok is the same in every thread here
         float dv[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + 16 * c, dv);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (!(active && ok)) continue;
+        if (!active) continue;
         if constexpr (!PHI) {
 #pragma unroll
             for (int o = 0; o < kHidden; o += 4)

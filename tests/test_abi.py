@@ -77,7 +77,8 @@ def test_null_handle_calls(lib):
     assert isinstance(binding.stag_last_error(None), str)
 
 
-@pytest.mark.parametrize("case", ["recon_7", "f64", "no_naik", "zero_scale", "nan_scale", "link_recon_7"])
+@pytest.mark.parametrize("case", ["recon_7", "f64", "no_naik", "zero_scale", "nan_scale", "tiny_scale", "huge_scale",
+                                  "link_recon_7"])
 def test_create_rejects_bad_link_forms(lib, case):
     """Option checks of the 12-parameter link forms, all made before any device work."""
     dims = (4, 4, 4, 4)
@@ -95,9 +96,22 @@ def test_create_rejects_bad_link_forms(lib, case):
         o.long_scale = 0.0
     elif case == "nan_scale":
         o.long_scale = float("nan")
+    elif case == "tiny_scale":
+        o.long_scale = -9e-11   # below 1e-10: float-float products of two entries would go subnormal
+    elif case == "huge_scale":
+        o.long_scale = 2e18     # above 1e18: such products approach the FP32 overflow
     else:
         o.long_recon, o.link_recon = 0, 7
     with pytest.raises(binding.StagError) as e:
         binding.stag_create_ex(links, naik, dims, 0.1, o)
     assert e.value.code == binding.STAG_ERR_INVALID_ARG
     assert "recon" in binding.stag_last_error(None)
+
+
+def test_fma_probe_rejects_bad_arguments(lib):
+    """stag_measure_fma_rate checks its arguments before touching a device."""
+    import ctypes as ct
+
+    rate = ct.c_double(0.0)
+    assert lib.stag_measure_fma_rate(16, ct.byref(rate)) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_measure_fma_rate(64, None) == binding.STAG_ERR_INVALID_ARG

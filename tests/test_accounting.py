@@ -33,3 +33,11 @@ def test_compulsory_and_naik_figures():
     assert accounting.multi_rhs_bytes_per_site(16) == 1920
     assert accounting.multi_rhs_bytes_per_site(1) == 1200  # one RHS: the FP32 single-RHS figure
     assert accounting.multi_rhs_bytes_per_site(8, naik=False) == 8 * 72 + 8 * 48
+
+
+def test_fma_count_is_half_the_papers_flop_count():
+    """Every real multiplication of the SU(3) x vector products is fused with an addition, so
+    the paper's 576 flops per one-hop site (Sec. 2) are 288 FMAs; 576 with the Naik hops."""
+    g = json.load(open(GOLDEN))
+    assert 2 * accounting.fma_per_site(False) == g["flops_per_site"]
+    assert accounting.fma_per_site(True) == 576

@@ -32,9 +32,36 @@ def test_reference_arm_prints_one_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["lattice"] == [4, 4, 4, 4]
+    # the measured arm prints the same config object for the same workload
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert d["config"] == bench.workload_config((4, 4, 4, 4), bench.MASS, 1)
+    assert d["cpu_baseline"]["host_cpu"] and d["cpu_baseline"]["host_logical_cores"] >= 1
 
 
 def test_reference_arm_other_ranks_exit_quietly():
     p = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_all_core_oracle_timing_reproduces_the_oracle():
+    """The host-core timing splits the lattice into t-slabs, one process each, and applies the
+    oracle's A, unchanged, to every slab widened by the reach of A (6 t-slices with Naik);
+    the interior rows put together are the oracle's A on the whole lattice."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_1010_4782_gb300 import inputs
+
+    dims = (4, 4, 2, 32)
+    fat, lng = inputs.asqtad_form_fields(dims)
+    b = inputs.gaussian_even_source(dims, 0)
+    per_a, w, y = bench.oracle_apply_A_all_cores(fat, lng, b, dims, 0.1, reps=1)
+    assert w >= 2 or (os.cpu_count() or 1) < 2
+    assert per_a > 0
+    ref = oracle.Operator(fat, lng, 0.1, dims).apply_A(b)
+    assert np.array_equal(y, ref)

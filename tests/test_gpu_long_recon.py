@@ -111,3 +111,29 @@ def test_rejects_links_that_are_not_scaled_su3(which):
         _handle(fat, links, dims, 0.1, long_scale=scale)
     assert e.value.code == binding.STAG_ERR_INVALID_ARG
     assert "SU(3)" in binding.stag_last_error(None)
+
+
+@pytest.mark.parametrize("scale", [1.5e-10, -1.5e-10, 8e17, -8e17])
+def test_parity_at_the_ends_of_the_scale_range(scale):
+    """Naik links c x SU(3) with |c| near the ends of the accepted range 1e-10 .. 1e18.  The
+    fat links and the mass are scaled by the same factor k = |c| / (1/24), so the Naik term
+    keeps its usual weight in D; the rebuilt third row, whose float-float products are of
+    size c^2, must still meet the bars against the oracle (both half-Dslash parities, and A
+    where k^2 stays inside the FP32 range)."""
+    dims = (6, 4, 2, 8)
+    k = abs(scale / C)
+    fat, lng = inputs.asqtad_form_fields(dims, seeds=(27, 28, 29))
+    fat, lng = fat * k, lng * (scale / C)
+    mass = 0.1 * k
+    op = oracle.Operator(fat, lng, mass, dims)
+    with _handle(fat, lng, dims, mass, long_scale=scale) as h:
+        for p_out in (0, 1):
+            v = inputs.gaussian_vector(op.n_half, 200 + p_out)
+            out = torch.empty((op.n_half, 3), dtype=torch.complex128, device="cuda")
+            binding.stag_dslash(h.h, p_out, _dev(v), out)
+            _close(out.cpu().numpy(), op.dslash_half(v, p_out))
+        if k < 1.0:
+            v = inputs.gaussian_even_source(dims, 5)
+            out = torch.empty_like(_dev(v))
+            binding.stag_apply_A(h.h, _dev(v), out)
+            _close(out.cpu().numpy(), op.apply_A(v))

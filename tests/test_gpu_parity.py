@@ -287,3 +287,12 @@ def test_breakdown_on_zero_mode(arith):
         code, info = binding.stag_cg_solve(h.h, _dev(b), x, 1e-10, raise_on_error=False)
     assert code == binding.STAG_ERR_BREAKDOWN
     assert info["status"] == binding.STAG_ERR_BREAKDOWN
+
+
+def test_fma_probe_rates_are_plausible():
+    """The FMA probe the benchmark uses for the FP64 ceiling: positive rates, FP32 faster
+    than FP64, and neither above the chip's nominal issue limit (152 SMs x 128 FP32 lanes x
+    2.1 GHz = 4.1e13 FFMA/s)."""
+    r64 = binding.stag_measure_fma_rate(64)
+    r32 = binding.stag_measure_fma_rate(32)
+    assert 0 < r64 < r32 <= 4.2e13, (r64, r32)

@@ -572,7 +572,7 @@ def run_batched(args):
     else:
         seq32, it32 = sequential(binding.STAG_ARITH_FF, binding.STAG_INNER_F32)
         seq64, it64 = sequential(binding.STAG_ARITH_F64, binding.STAG_INNER_NONE)
-    rb, bsz, ms = tuning
+    rb, bsz, ms, sweep = tuning
     vh = accounting.half_sites(BATCH_MAIN)
     bytes_launch = vh * accounting.multi_rhs_bytes_per_site(BATCH_NRHS)  # FP32 links once + each RHS in and out
     peak, peak_src = measured_peaks()
@@ -597,7 +597,8 @@ def run_batched(args):
                    "step": "stag_batch_create + stag_batch_solve + stag_batch_destroy"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": f"multi-RHS D_oe, 16 RHS, FP32, {rb} RHS/thread, {bsz} threads/block "
+                     "kernel": f"multi-RHS D_oe, 16 RHS, FP32, {rb} RHS/thread, {bsz} threads/block, "
+                               f"{'resident sweep + L2 prefetch' if sweep else 'contiguous tile runs'} "
                                "(autotuner's CUDA-event time)",
                      "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": round(ms, 4)},
         "clocks": clock_info,

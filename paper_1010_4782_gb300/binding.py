@@ -70,6 +70,7 @@ EXPORTED = (
     "stag_batch_solve",
     "stag_batch_apply_A",
     "stag_batch_tuning",
+    "stag_batch_set_tuning",
     "stag_batch_last_error",
     "stag_batch_device_bytes",
     "stag_batch_destroy",
@@ -185,7 +186,9 @@ def load(path: str | None = None):
     lib.stag_batch_set_stream.argtypes = [H, P]
     lib.stag_batch_solve.argtypes = [H, PP, PP, d, i32, ctypes.POINTER(stag_solve_info)]
     lib.stag_batch_apply_A.argtypes = [H, PP, PP]
-    lib.stag_batch_tuning.argtypes = [H, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(d)]
+    lib.stag_batch_tuning.argtypes = [H, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(d),
+                                      ctypes.POINTER(i32)]
+    lib.stag_batch_set_tuning.argtypes = [H, i32, i32, i32, i32]
     lib.stag_batch_last_error.argtypes = [H]
     lib.stag_batch_last_error.restype = ctypes.c_char_p
     lib.stag_batch_device_bytes.argtypes = [H]
@@ -381,11 +384,19 @@ def stag_batch_apply_A(h, ins, outs):
 
 
 def stag_batch_tuning(h, system):
+    """(RHS per thread, threads per block, measured D_oe ms, traversal) of system's group."""
     rb = ctypes.c_int32()
     bs = ctypes.c_int32()
     ms = ctypes.c_double()
-    _bcheck(load().stag_batch_tuning(h, int(system), ctypes.byref(rb), ctypes.byref(bs), ctypes.byref(ms)), h)
-    return rb.value, bs.value, ms.value
+    sw = ctypes.c_int32()
+    _bcheck(load().stag_batch_tuning(h, int(system), ctypes.byref(rb), ctypes.byref(bs), ctypes.byref(ms),
+                                     ctypes.byref(sw)), h)
+    return rb.value, bs.value, ms.value, sw.value
+
+
+def stag_batch_set_tuning(h, system, rhs_per_thread, threads_per_block, sweep):
+    _bcheck(load().stag_batch_set_tuning(h, int(system), int(rhs_per_thread), int(threads_per_block), int(sweep)),
+            h)
 
 
 def stag_batch_device_bytes(h) -> int:

@@ -48,6 +48,7 @@ struct BFail {
 struct Tune {
     int rb = 1, bs = 256;
     double ms = 0.0;
+    int sweep = 0;  // tile traversal: 0 contiguous runs, 1 resident sweep with L2 prefetch (multi.cu)
 };
 
 struct Group {
@@ -180,15 +181,23 @@ MultiLaunch make_launch(stag_batch* b, int parity, int phase, int first_item) {
 constexpr int kMaxGroupBlocks = 4096;
 
 // Blocks of a group for a shape: one per tile of sites, at most kMaxGroupBlocks
-// (blocks then take contiguous runs of tiles).
-int group_blocks(const Group& G, int rb, int bs) {
+// (blocks then take contiguous runs of tiles); for the resident sweep, at most
+// the number of blocks of that shape the GPU holds at once.
+int group_blocks(const Group& G, int rb, int bs, int sweep) {
     const int spb = bs / (G.rpad / rb);
     const int ntiles = (G.g.vh + spb - 1) / spb;
-    return std::min(ntiles, kMaxGroupBlocks);
+    int cap = kMaxGroupBlocks;
+    if (sweep) {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cap = std::min(cap, multi_resident_blocks_per_sm(rb, bs) * sms);
+    }
+    return std::min(ntiles, cap);
 }
 
-void add_items(std::vector<int4>& v, int gi, int nblk) {
-    for (int k = 0; k < nblk; ++k) v.push_back(make_int4(gi, k, nblk, 0));
+void add_items(std::vector<int4>& v, int gi, int nblk, int sweep) {
+    for (int k = 0; k < nblk; ++k) v.push_back(make_int4(gi, k, nblk, sweep));
 }
 
 // Work items of every group with its tuned shape, grouped into launch classes.
@@ -196,7 +205,8 @@ void build_items(stag_batch* b) {
     std::map<std::pair<int, int>, std::vector<int4>> by_class;
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         const Group& G = b->groups[gi];
-        add_items(by_class[{G.tune.rb, G.tune.bs}], (int)gi, group_blocks(G, G.tune.rb, G.tune.bs));
+        add_items(by_class[{G.tune.rb, G.tune.bs}], (int)gi, group_blocks(G, G.tune.rb, G.tune.bs, G.tune.sweep),
+                  G.tune.sweep);
     }
     std::vector<int4> all;
     b->classes.clear();
@@ -246,21 +256,37 @@ void load_tune_file() {
     if (!path) return;
     std::ifstream f(path);
     std::string key;
-    Tune t;
-    while (f >> key >> t.rb >> t.bs >> t.ms) g_tune_cache[key] = t;
+    // lines: key rb bs ms [sweep]
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream ls(line);
+        Tune t;
+        if (ls >> key >> t.rb >> t.bs >> t.ms) {
+            if (!(ls >> t.sweep)) t.sweep = 0;
+            g_tune_cache[key] = t;
+        }
+    }
+}
+
+// Every candidate's time, appended to the file STAG_AUTOTUNE_LOG names (if set).
+void log_candidate(const std::string& key, int rb, int bs, int sweep, double ms) {
+    if (const char* path = std::getenv("STAG_AUTOTUNE_LOG")) {
+        std::ofstream f(path, std::ios::app);
+        f << key << " rb=" << rb << " bs=" << bs << " sweep=" << sweep << " ms=" << ms << "\n";
+    }
 }
 
 void store_tune(const std::string& key, const Tune& t) {
     g_tune_cache[key] = t;
     if (const char* path = std::getenv("STAG_AUTOTUNE_CACHE")) {
         std::ofstream f(path, std::ios::app);
-        f << key << " " << t.rb << " " << t.bs << " " << t.ms << "\n";
+        f << key << " " << t.rb << " " << t.bs << " " << t.ms << " " << t.sweep << "\n";
     }
 }
 
-double time_group_launch(stag_batch* b, const std::vector<int>& gis, int rb, int bs) {
+double time_group_launch(stag_batch* b, const std::vector<int>& gis, int rb, int bs, int sweep) {
     std::vector<int4> items;
-    for (int gi : gis) add_items(items, gi, group_blocks(b->groups[gi], rb, bs));
+    for (int gi : gis) add_items(items, gi, group_blocks(b->groups[gi], rb, bs, sweep), sweep);
     int4* d_items = nullptr;
     bcheck(b, cudaMalloc(&d_items, items.size() * sizeof(int4)), "allocate tuning items");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -315,14 +341,18 @@ void autotune(stag_batch* b) {
         best.bs = 128;
         best.ms = 1e30;
         if (enabled) {
-            for (int rb : {1, 2, 4, 8}) {
-                if (rb > G.rpad || G.rpad / rb > 32) continue;
-                for (int bs : {64, 128, 256}) {
-                    const double ms = time_group_launch(b, {(int)gi}, rb, bs);
-                    if (ms < best.ms) {
-                        best.ms = ms;
-                        best.rb = rb;
-                        best.bs = bs;
+            for (int sweep : {0, 1}) {
+                for (int rb : {1, 2, 4, 8}) {
+                    if (rb > G.rpad || G.rpad / rb > 32) continue;
+                    for (int bs : {64, 128, 256}) {
+                        const double ms = time_group_launch(b, {(int)gi}, rb, bs, sweep);
+                        log_candidate(key, rb, bs, sweep, ms);
+                        if (ms < best.ms) {
+                            best.ms = ms;
+                            best.rb = rb;
+                            best.bs = bs;
+                            best.sweep = sweep;
+                        }
                     }
                 }
             }
@@ -336,11 +366,15 @@ void autotune(stag_batch* b) {
         best.bs = 128;
         best.ms = 1e30;
         if (enabled) {
-            for (int bs : {64, 128, 256}) {
-                const double ms = time_group_launch(b, singles, 1, bs);
-                if (ms < best.ms) {
-                    best.ms = ms;
-                    best.bs = bs;
+            for (int sweep : {0, 1}) {
+                for (int bs : {64, 128, 256}) {
+                    const double ms = time_group_launch(b, singles, 1, bs, sweep);
+                    log_candidate("single-rhs", 1, bs, sweep, ms);
+                    if (ms < best.ms) {
+                        best.ms = ms;
+                        best.bs = bs;
+                        best.sweep = sweep;
+                    }
                 }
             }
         }
@@ -558,13 +592,40 @@ int stag_batch_set_stream(stag_batch* b, void* cuda_stream) {
 }
 
 int stag_batch_tuning(const stag_batch* b, int32_t system, int32_t* rhs_per_thread, int32_t* threads_per_block,
-                      double* ms) {
+                      double* ms, int32_t* sweep) {
     if (!b || system < 0 || system >= b->n_sys) return STAG_ERR_INVALID_ARG;
     const Group& G = b->groups[b->sys_group[system]];
     if (rhs_per_thread) *rhs_per_thread = G.tune.rb;
     if (threads_per_block) *threads_per_block = G.tune.bs;
     if (ms) *ms = G.tune.ms;
+    if (sweep) *sweep = G.tune.sweep;
     return STAG_OK;
+}
+
+int stag_batch_set_tuning(stag_batch* b, int32_t system, int32_t rhs_per_thread, int32_t threads_per_block,
+                          int32_t sweep) {
+    if (!b) return STAG_ERR_INVALID_ARG;
+    try {
+        if (system < 0 || system >= b->n_sys) bfail(b, STAG_ERR_INVALID_ARG, "system index out of range");
+        Group& G = b->groups[b->sys_group[system]];
+        const int rb = rhs_per_thread, bs = threads_per_block;
+        const bool rb_ok = (rb == 1 || rb == 2 || rb == 4 || rb == 8) && rb <= G.rpad && G.rpad / rb <= 32 &&
+                           (G.nrhs > 1 || rb == 1);
+        if (!rb_ok || (bs != 64 && bs != 128 && bs != 256) || (sweep != 0 && sweep != 1))
+            bfail(b, STAG_ERR_INVALID_ARG, "stag_batch_set_tuning: unsupported shape");
+        bcheck(b, cudaSetDevice(b->device), "cudaSetDevice");
+        G.tune.rb = rb;
+        G.tune.bs = bs;
+        G.tune.sweep = sweep;
+        G.tune.ms = 0.0;
+        build_items(b);
+        return STAG_OK;
+    } catch (const BFail& f) {
+        return f.code;
+    } catch (...) {
+        b->err = "unexpected exception";
+        return STAG_ERR_CUDA;
+    }
 }
 
 int stag_batch_apply_A(stag_batch* b, const double* const* in, double* const* out) {

@@ -26,7 +26,8 @@ struct MultiGroup {
 
 struct MultiLaunch {
     const MultiGroup* groups;  // device array
-    const int4* items;         // device array: (group, block in group, blocks in group, 0)
+    const int4* items;         // device array: (group, block in group, blocks in group, traversal:
+                               // 0 contiguous runs of tiles, 1 resident sweep with L2 prefetch)
     CgScalars* scal;           // one per right-hand side, global index
     double* partials;          // [padded slots][max_blocks]
     unsigned int* counters;    // [padded slots], indexed by the group's first slot
@@ -39,6 +40,9 @@ enum MultiKernel { MK_DSLASH_PLAIN = 0, MK_DSLASH_CG = 1, MK_UPDATE_XR = 2, MK_U
 // rb: right-hand sides per thread (1, 2, 4, 8; rpad / rb threads share a site, at most 32);
 // bs: threads per block (64, 128, 256)
 void launch_multi(MultiKernel k, const MultiLaunch& L, int nitems, int rb, int bs, cudaStream_t s);
+
+// Blocks of the Dirac kernel of this shape that one SM holds at once (>= 1).
+int multi_resident_blocks_per_sm(int rb, int bs);
 
 // single right-hand-side slot of a group's vectors
 void launch_slot_set_residual(const Geom& g, const double2* r64, float2* r, float2* d, float2* y, int rpad, int slot,

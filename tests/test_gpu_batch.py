@@ -66,37 +66,63 @@ def _batch(systems, **kw):
 def test_batch_groups_and_tuning(systems):
     bt = _batch(systems)
     try:
-        rb, bs, ms = binding.stag_batch_tuning(bt, 0)
-        assert rb in (1, 2, 4, 8) and bs in (64, 128, 256) and ms > 0
+        rb, bs, ms, sw = binding.stag_batch_tuning(bt, 0)
+        assert rb in (1, 2, 4, 8) and bs in (64, 128, 256) and ms > 0 and sw in (0, 1)
         assert binding.stag_batch_tuning(bt, 4)[:2] == (rb, bs)  # same group
-        rb1, bs1, _ = binding.stag_batch_tuning(bt, 5)
-        assert rb1 == 1 and bs1 in (64, 128, 256)
+        rb1, bs1, _, sw1 = binding.stag_batch_tuning(bt, 5)
+        assert rb1 == 1 and bs1 in (64, 128, 256) and sw1 in (0, 1)
+        # shapes outside the candidates are rejected
+        for bad in ((0, 3, 64, 0), (0, 16, 64, 0), (5, 2, 64, 0), (0, 2, 96, 0), (0, 2, 64, 2)):
+            with pytest.raises(binding.StagError):
+                binding.stag_batch_set_tuning(bt, *bad)
         assert binding.stag_batch_device_bytes(bt) > 0
     finally:
         binding.stag_batch_destroy(bt)
 
 
-def test_batch_operator_parity(systems):
-    bt = _batch(systems)
+# every candidate of the autotuner for the 5-RHS group (padded to 8): RB RHS per thread
+# (8 / RB threads per site; RB >= 4 uses the 256-bit accesses), threads per block, and the
+# two traversals; the single-RHS groups run every block size and traversal alongside
+SHAPES = [(rb, bs, sw) for sw in (0, 1) for rb in (1, 2, 4, 8) for bs in (64, 128, 256)]
+
+
+@pytest.fixture(scope="module")
+def operator_refs(systems):
+    ins = [inputs.gaussian_even_source(s["dims"], 200 + k) for k, s in enumerate(systems)]
+    refs = [oracle.Operator(s["fat"], s["lng"], s["mass"], s["dims"]).apply_A(v) for s, v in zip(systems, ins)]
+    return ins, refs
+
+
+@pytest.mark.parametrize("rb,bs,sweep", SHAPES)
+def test_batch_operator_parity(systems, operator_refs, rb, bs, sweep):
+    ins_h, refs = operator_refs
+    bt = _batch(systems, autotune=0)
     try:
-        ins = [_dev(inputs.gaussian_even_source(s["dims"], 200 + k)) for k, s in enumerate(systems)]
-        outs = [torch.empty_like(v) for v in ins]
+        binding.stag_batch_set_tuning(bt, 0, rb, bs, sweep)
+        for k in (5, 6, 7):
+            binding.stag_batch_set_tuning(bt, k, 1, bs, sweep)
+        assert binding.stag_batch_tuning(bt, 0)[::3] == (rb, sweep)
+        ins = [_dev(v) for v in ins_h]
+        outs = [torch.full_like(v, float("nan")) for v in ins]
         binding.stag_batch_apply_A(bt, ins, outs)
     finally:
         binding.stag_batch_destroy(bt)
-    for s, v, o in zip(systems, ins, outs):
-        ref = oracle.Operator(s["fat"], s["lng"], s["mass"], s["dims"]).apply_A(v.cpu().numpy())
+    for s, o, ref in zip(systems, outs, refs):
         got = o.cpu().numpy()
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         elem = np.abs(got - ref).max() / np.abs(ref).max()
         assert rel <= 2e-6 and elem <= 1e-5, (s["dims"], rel, elem)
 
 
-@pytest.mark.parametrize("autotune", [1, 0])
-def test_batch_solve(systems, autotune):
+@pytest.mark.parametrize("autotune,sweep", [(1, None), (0, 0), (0, 1)])
+def test_batch_solve(systems, autotune, sweep):
     tol = 1e-10
     bt = _batch(systems, autotune=autotune, check_interval=8)
     try:
+        if sweep is not None:  # the fixed shapes, with each traversal of the site tiles
+            binding.stag_batch_set_tuning(bt, 0, 4, 128, sweep)
+            for k in (5, 6, 7):
+                binding.stag_batch_set_tuning(bt, k, 1, 128, sweep)
         bs = [_dev(s["b"]) for s in systems]
         xs = [torch.zeros_like(b) for b in bs]
         code, infos = binding.stag_batch_solve(bt, bs, xs, tol, max_iter=20000)

@@ -55,8 +55,8 @@ def test_apply_A_sampled(fields, arith):
         ref = oracle.apply_A_at(fat, lng, mass, v, s, DIMS)
         errs.append(np.abs(got[i] - ref).max())
         refs.append(np.abs(ref).max())
-    # element-wise bar of the parity tests: 1e-13 (FP64), 5e-13 (float-float)
-    tol = 1e-13 if arith == binding.STAG_ARITH_F64 else 5e-13
+    # element-wise bar of the parity tests: 1e-13 for FP64 and float-float alike
+    tol = 1e-13
     assert max(errs) <= tol * max(refs)
 
 

@@ -6,7 +6,8 @@ kernel stores their first two rows and rebuilds the third as
 matrix).  Same bars as the nine-entry float-float kernels: the rebuilt entries
 carry a few float-float roundings (about 2^-48 each) and the stored SU(3)
 matrices are unitary to FP64 rounding, so
-  * operator parity: norm <= 1e-13, elem <= 5e-13 against the FP64 oracle;
+  * operator parity: norm and elem <= 1e-13 against the FP64 oracle (worst
+    element error measured on GB300: 4.0e-14);
   * solves: true residual <= 1e-10, |x - x_oracle| / |x_oracle| <= 1e-8, and the
     iteration count of the nine-entry float-float solve within 2.
 Links that are not c x SU(3) (the fat links, or the right matrices with the
@@ -21,7 +22,7 @@ from paper_1010_4782_gb300 import binding, inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL_OP, TOL_ELEM = 1e-13, 5e-13
+TOL_OP, TOL_ELEM = 1e-13, 1e-13
 C = inputs.NAIK_COEFF
 
 

@@ -6,10 +6,13 @@ max |ref|):
     component is a sum of at most 96 real products and only the summation
     order differs from the oracle, so the error is a few units of 2^-53
     times sqrt(96) - far below the bar.
-  * float-float Dirac kernels: norm <= 1e-13 (the FP64 bar), elem <= 5e-13.
-    Each product and sum carries about 2^-48 = 3.6e-15 relative rounding;
-    96 terms per component give a worst case of 96 * 2^-48 = 3.4e-13 of the
-    largest term, which bounds the element-wise error.
+  * float-float Dirac kernels: norm and elem <= 1e-13, the FP64 bar.  Each
+    product and sum carries about 2^-48 = 3.6e-15 relative rounding.  The
+    kernels sum each hop's 3x3 row locally and merge it once into the site
+    sum, so only 16 large-magnitude roundings reach an output component:
+    16 * 2^-48 = 5.7e-14 of the largest term.  Measured on GB300 over every
+    case below, the worst element error is 2.6e-14 (nine-entry links) and
+    4.0e-14 (two-row Naik links).
   * solves: true residual |b - A x| / |b| <= 1e-10 and |x - x_oracle| / |x_oracle|
     <= 1e-8 against an oracle solution taken to 1e-13.
 """
@@ -24,7 +27,7 @@ pytestmark = pytest.mark.gpu
 
 ARITHS = [binding.STAG_ARITH_F64, binding.STAG_ARITH_FF]
 TOL_OP = 1e-13
-TOL_ELEM = {binding.STAG_ARITH_F64: 1e-13, binding.STAG_ARITH_FF: 5e-13}
+TOL_ELEM = {binding.STAG_ARITH_F64: 1e-13, binding.STAG_ARITH_FF: 1e-13}
 
 
 @pytest.fixture(scope="module", autouse=True)

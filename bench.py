@@ -598,7 +598,7 @@ def run_batched(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "kernel": f"multi-RHS D_oe, 16 RHS, FP32, {rb} RHS/thread, {bsz} threads/block, "
-                               f"{'resident sweep + L2 prefetch' if sweep else 'contiguous tile runs'} "
+                               f"{'resident sweep' if sweep else 'contiguous tile runs'} "
                                "(autotuner's CUDA-event time)",
                      "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": round(ms, 4)},
         "clocks": clock_info,

@@ -232,9 +232,8 @@ int64_t stag_launch_count(const stag_handle* h);
  * at create by timing the candidates (opt->autotune), cached per (extents,
  * Naik, RHS count) for the process and in the file STAG_AUTOTUNE_CACHE names;
  * STAG_AUTOTUNE_LOG names a file that receives every candidate's time.  The
- * candidates also include two traversals of a group's site tiles: contiguous
- * runs per block, or a sweep by the blocks resident at once with the next
- * tile's links and far neighbours prefetched into L2. */
+ * candidates also include the traversals of a group's site tiles listed at
+ * stag_batch_tuning. */
 typedef struct stag_batch stag_batch;
 
 /* fat, naik: n_sys link arrays (the link layout above; naik may be NULL, or
@@ -262,18 +261,19 @@ int stag_batch_solve(stag_batch* b, const double* const* bvec, double* const* xv
 int stag_batch_apply_A(stag_batch* b, const double* const* in, double* const* out);
 
 /* The shapes the autotuner chose for system k's group and its measured D_oe time
- * (any output may be NULL); *sweep: the traversal of the site tiles (0
- * contiguous runs per block, 1 resident sweep with L2 prefetch). */
+ * (any output may be NULL); *traversal: how the blocks walk the site tiles
+ * (0 contiguous runs per block, 1 a sweep by the blocks resident at once, all
+ * on one narrow band of sites). */
 int stag_batch_tuning(const stag_batch* b, int32_t system, int32_t* rhs_per_thread, int32_t* threads_per_block,
-                      double* ms, int32_t* sweep);
+                      double* ms, int32_t* traversal);
 
 /* Override the shape of system k's group (and so of every system in it):
  * rhs_per_thread in {1, 2, 4, 8}, at most the group's padded RHS count and at
  * least 1/32 of it (single-RHS groups: 1); threads_per_block in {64, 128, 256};
- * sweep in {0, 1}.  Returns STAG_ERR_INVALID_ARG for other values.  Used to run
- * every candidate of the autotuner, e.g. in tests. */
+ * traversal in {0, 1}.  Returns STAG_ERR_INVALID_ARG for other values.
+ * Used to run every candidate of the autotuner, e.g. in tests. */
 int stag_batch_set_tuning(stag_batch* b, int32_t system, int32_t rhs_per_thread, int32_t threads_per_block,
-                          int32_t sweep);
+                          int32_t traversal);
 
 /* Message of the batch's last failing call (b = NULL: of the last failing create). */
 const char* stag_batch_last_error(const stag_batch* b);

@@ -384,7 +384,7 @@ def stag_batch_apply_A(h, ins, outs):
 
 
 def stag_batch_tuning(h, system):
-    """(RHS per thread, threads per block, measured D_oe ms, traversal) of system's group."""
+    """(RHS per thread, threads per block, measured D_oe ms, traversal 0/1) of system's group."""
     rb = ctypes.c_int32()
     bs = ctypes.c_int32()
     ms = ctypes.c_double()
@@ -394,9 +394,9 @@ def stag_batch_tuning(h, system):
     return rb.value, bs.value, ms.value, sw.value
 
 
-def stag_batch_set_tuning(h, system, rhs_per_thread, threads_per_block, sweep):
-    _bcheck(load().stag_batch_set_tuning(h, int(system), int(rhs_per_thread), int(threads_per_block), int(sweep)),
-            h)
+def stag_batch_set_tuning(h, system, rhs_per_thread, threads_per_block, traversal):
+    _bcheck(load().stag_batch_set_tuning(h, int(system), int(rhs_per_thread), int(threads_per_block),
+                                         int(traversal)), h)
 
 
 def stag_batch_device_bytes(h) -> int:

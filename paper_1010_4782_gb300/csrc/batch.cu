@@ -28,6 +28,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/stag.h"
@@ -48,7 +49,7 @@ struct BFail {
 struct Tune {
     int rb = 1, bs = 256;
     double ms = 0.0;
-    int sweep = 0;  // tile traversal: 0 contiguous runs, 1 resident sweep with L2 prefetch (multi.cu)
+    int mode = 0;  // tile traversal (multi.cu): 0 contiguous runs, 1 resident sweep
 };
 
 struct Group {
@@ -183,11 +184,11 @@ constexpr int kMaxGroupBlocks = 4096;
 // Blocks of a group for a shape: one per tile of sites, at most kMaxGroupBlocks
 // (blocks then take contiguous runs of tiles); for the resident sweep, at most
 // the number of blocks of that shape the GPU holds at once.
-int group_blocks(const Group& G, int rb, int bs, int sweep) {
+int group_blocks(const Group& G, int rb, int bs, int mode) {
     const int spb = bs / (G.rpad / rb);
     const int ntiles = (G.g.vh + spb - 1) / spb;
     int cap = kMaxGroupBlocks;
-    if (sweep) {
+    if (mode) {
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -196,24 +197,25 @@ int group_blocks(const Group& G, int rb, int bs, int sweep) {
     return std::min(ntiles, cap);
 }
 
-void add_items(std::vector<int4>& v, int gi, int nblk, int sweep) {
-    for (int k = 0; k < nblk; ++k) v.push_back(make_int4(gi, k, nblk, sweep));
+void add_items(std::vector<int4>& v, int gi, int nblk, int mode) {
+    for (int k = 0; k < nblk; ++k) v.push_back(make_int4(gi, k, nblk, mode));
 }
 
 // Work items of every group with its tuned shape, grouped into launch classes.
 void build_items(stag_batch* b) {
-    std::map<std::pair<int, int>, std::vector<int4>> by_class;
+    std::map<std::tuple<int, int, int>, std::vector<int4>> by_class;
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         const Group& G = b->groups[gi];
-        add_items(by_class[{G.tune.rb, G.tune.bs}], (int)gi, group_blocks(G, G.tune.rb, G.tune.bs, G.tune.sweep),
-                  G.tune.sweep);
+        add_items(by_class[{G.tune.rb, G.tune.bs, G.tune.mode}], (int)gi,
+                  group_blocks(G, G.tune.rb, G.tune.bs, G.tune.mode), G.tune.mode);
     }
     std::vector<int4> all;
     b->classes.clear();
     for (auto& kv : by_class) {
         Tune t;
-        t.rb = kv.first.first;
-        t.bs = kv.first.second;
+        t.rb = std::get<0>(kv.first);
+        t.bs = std::get<1>(kv.first);
+        t.mode = std::get<2>(kv.first);
         b->classes.push_back({t, {(int)all.size(), (int)kv.second.size()}});
         all.insert(all.end(), kv.second.begin(), kv.second.end());
     }
@@ -231,7 +233,8 @@ void build_items(stag_batch* b) {
 
 void enqueue_all(stag_batch* b, MultiKernel k, int parity, int phase) {
     for (auto& c : b->classes)
-        launch_multi(k, make_launch(b, parity, phase, c.second.first), c.second.second, c.first.rb, c.first.bs, b->s);
+        launch_multi(k, make_launch(b, parity, phase, c.second.first), c.second.second, c.first.rb, c.first.bs,
+                     c.first.mode, b->s);
 }
 
 void enqueue_iteration(stag_batch* b) {
@@ -256,23 +259,23 @@ void load_tune_file() {
     if (!path) return;
     std::ifstream f(path);
     std::string key;
-    // lines: key rb bs ms [sweep]
+    // lines: key rb bs ms [traversal]
     std::string line;
     while (std::getline(f, line)) {
         std::istringstream ls(line);
         Tune t;
         if (ls >> key >> t.rb >> t.bs >> t.ms) {
-            if (!(ls >> t.sweep)) t.sweep = 0;
+            if (!(ls >> t.mode)) t.mode = 0;
             g_tune_cache[key] = t;
         }
     }
 }
 
 // Every candidate's time, appended to the file STAG_AUTOTUNE_LOG names (if set).
-void log_candidate(const std::string& key, int rb, int bs, int sweep, double ms) {
+void log_candidate(const std::string& key, int rb, int bs, int mode, double ms) {
     if (const char* path = std::getenv("STAG_AUTOTUNE_LOG")) {
         std::ofstream f(path, std::ios::app);
-        f << key << " rb=" << rb << " bs=" << bs << " sweep=" << sweep << " ms=" << ms << "\n";
+        f << key << " rb=" << rb << " bs=" << bs << " traversal=" << mode << " ms=" << ms << "\n";
     }
 }
 
@@ -280,13 +283,13 @@ void store_tune(const std::string& key, const Tune& t) {
     g_tune_cache[key] = t;
     if (const char* path = std::getenv("STAG_AUTOTUNE_CACHE")) {
         std::ofstream f(path, std::ios::app);
-        f << key << " " << t.rb << " " << t.bs << " " << t.ms << " " << t.sweep << "\n";
+        f << key << " " << t.rb << " " << t.bs << " " << t.ms << " " << t.mode << "\n";
     }
 }
 
-double time_group_launch(stag_batch* b, const std::vector<int>& gis, int rb, int bs, int sweep) {
+double time_group_launch(stag_batch* b, const std::vector<int>& gis, int rb, int bs, int mode) {
     std::vector<int4> items;
-    for (int gi : gis) add_items(items, gi, group_blocks(b->groups[gi], rb, bs, sweep), sweep);
+    for (int gi : gis) add_items(items, gi, group_blocks(b->groups[gi], rb, bs, mode), mode);
     int4* d_items = nullptr;
     bcheck(b, cudaMalloc(&d_items, items.size() * sizeof(int4)), "allocate tuning items");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -304,7 +307,7 @@ double time_group_launch(stag_batch* b, const std::vector<int>& gis, int rb, int
     L.phase = 0;
     for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
         cudaEventRecord(e0, b->s);
-        launch_multi(MK_DSLASH_PLAIN, L, (int)items.size(), rb, bs, b->s);
+        launch_multi(MK_DSLASH_PLAIN, L, (int)items.size(), rb, bs, mode, b->s);
         cudaEventRecord(e1, b->s);
         err = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -341,17 +344,17 @@ void autotune(stag_batch* b) {
         best.bs = 128;
         best.ms = 1e30;
         if (enabled) {
-            for (int sweep : {0, 1}) {
+            for (int mode : {0, 1}) {
                 for (int rb : {1, 2, 4, 8}) {
                     if (rb > G.rpad || G.rpad / rb > 32) continue;
                     for (int bs : {64, 128, 256}) {
-                        const double ms = time_group_launch(b, {(int)gi}, rb, bs, sweep);
-                        log_candidate(key, rb, bs, sweep, ms);
+                        const double ms = time_group_launch(b, {(int)gi}, rb, bs, mode);
+                        log_candidate(key, rb, bs, mode, ms);
                         if (ms < best.ms) {
                             best.ms = ms;
                             best.rb = rb;
                             best.bs = bs;
-                            best.sweep = sweep;
+                            best.mode = mode;
                         }
                     }
                 }
@@ -366,14 +369,14 @@ void autotune(stag_batch* b) {
         best.bs = 128;
         best.ms = 1e30;
         if (enabled) {
-            for (int sweep : {0, 1}) {
+            for (int mode : {0, 1}) {
                 for (int bs : {64, 128, 256}) {
-                    const double ms = time_group_launch(b, singles, 1, bs, sweep);
-                    log_candidate("single-rhs", 1, bs, sweep, ms);
+                    const double ms = time_group_launch(b, singles, 1, bs, mode);
+                    log_candidate("single-rhs", 1, bs, mode, ms);
                     if (ms < best.ms) {
                         best.ms = ms;
                         best.bs = bs;
-                        best.sweep = sweep;
+                        best.mode = mode;
                     }
                 }
             }
@@ -592,18 +595,18 @@ int stag_batch_set_stream(stag_batch* b, void* cuda_stream) {
 }
 
 int stag_batch_tuning(const stag_batch* b, int32_t system, int32_t* rhs_per_thread, int32_t* threads_per_block,
-                      double* ms, int32_t* sweep) {
+                      double* ms, int32_t* traversal) {
     if (!b || system < 0 || system >= b->n_sys) return STAG_ERR_INVALID_ARG;
     const Group& G = b->groups[b->sys_group[system]];
     if (rhs_per_thread) *rhs_per_thread = G.tune.rb;
     if (threads_per_block) *threads_per_block = G.tune.bs;
     if (ms) *ms = G.tune.ms;
-    if (sweep) *sweep = G.tune.sweep;
+    if (traversal) *traversal = G.tune.mode;
     return STAG_OK;
 }
 
 int stag_batch_set_tuning(stag_batch* b, int32_t system, int32_t rhs_per_thread, int32_t threads_per_block,
-                          int32_t sweep) {
+                          int32_t traversal) {
     if (!b) return STAG_ERR_INVALID_ARG;
     try {
         if (system < 0 || system >= b->n_sys) bfail(b, STAG_ERR_INVALID_ARG, "system index out of range");
@@ -611,12 +614,12 @@ int stag_batch_set_tuning(stag_batch* b, int32_t system, int32_t rhs_per_thread,
         const int rb = rhs_per_thread, bs = threads_per_block;
         const bool rb_ok = (rb == 1 || rb == 2 || rb == 4 || rb == 8) && rb <= G.rpad && G.rpad / rb <= 32 &&
                            (G.nrhs > 1 || rb == 1);
-        if (!rb_ok || (bs != 64 && bs != 128 && bs != 256) || (sweep != 0 && sweep != 1))
+        if (!rb_ok || (bs != 64 && bs != 128 && bs != 256) || (traversal != 0 && traversal != 1))
             bfail(b, STAG_ERR_INVALID_ARG, "stag_batch_set_tuning: unsupported shape");
         bcheck(b, cudaSetDevice(b->device), "cudaSetDevice");
         G.tune.rb = rb;
         G.tune.bs = bs;
-        G.tune.sweep = sweep;
+        G.tune.mode = traversal;
         G.tune.ms = 0.0;
         build_items(b);
         return STAG_OK;

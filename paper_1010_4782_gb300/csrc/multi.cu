@@ -34,8 +34,7 @@ __device__ __forceinline__ bool group_all_done(const MultiGroup& G, const CgScal
 //  * sweep (1): nblk is the number of blocks that are resident at once, and
 //    block blk takes the tiles blk, blk + nblk, blk + 2 nblk, ...  All blocks
 //    then work on one narrow band of sites that moves through the lattice, so
-//    the input vector's reuse window (t -/+ 3 slices) stays in L2, and each block
-//    prefetches into L2 what its next tile will read while it computes this one.
+//    the input vector's reuse window (t -/+ 3 slices) stays in L2.
 __device__ __forceinline__ int tile_end(int blk, int ntiles, int nblk) {
     return (int)((long long)(blk + 1) * ntiles / nblk);
 }
@@ -47,64 +46,6 @@ struct TileWalk {
 __device__ __forceinline__ TileWalk tile_walk(int4 w, int ntiles) {
     if (w.w) return TileWalk{w.y, ntiles, w.z};
     return TileWalk{tile_end(w.y - 1, ntiles, w.z), tile_end(w.y, ntiles, w.z), 1};
-}
-
-__device__ __forceinline__ void l2_prefetch(const void* p, unsigned int bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Prefetch into L2 the index range [j, j + n) of a plane of vs sites with
-// per_site float2 per site: a negative start wraps once, the range is moved
-// inside [0, vh), then widened to even site indices (16-byte boundaries) and
-// cut at vs, so it never leaves the plane.
-__device__ __forceinline__ void prefetch_range(const float2* plane, int j, int n, int vh, int vs, int per_site) {
-    if (n > vh) n = vh;
-    if (j < 0) j += vh;
-    if (j + n > vh) j = vh - n;
-    if (j < 0) j = 0;
-    const int lo = j & ~1;
-    const int hi = min((j + n + 1) & ~1, vs);
-    if (hi > lo) l2_prefetch(plane + (size_t)lo * per_site, (unsigned int)((hi - lo) * per_site * sizeof(float2)));
-}
-
-// What the tile of sites [j0, j0 + n) of output parity P will read, prefetched
-// into L2 by the block's threads: the links at the sites (forward hops) and at
-// their backward neighbours, 9 planes per direction and field, and the input
-// vector at the z and t neighbours.  The x and y neighbours lie within a few
-// rows of the tile, which the tiles being computed have already brought in.
-// Neighbour ranges are the tile shifted by the hop's index stride; across a
-// boundary of the lattice the range is only approximately right, which costs
-// a few ordinary misses, not correctness.
-__device__ void prefetch_tile(const MultiGroup& G, const float2* in, int P, int j0, int n) {
-    const Geom& g = G.g;
-    const size_t vs = (size_t)g.vs;
-    const int nf = G.lng ? 2 : 1;
-    // index stride of one step in direction mu (x: 0, its +-1 wobble is covered below)
-    auto stride = [&](int mu) { return mu == 1 ? g.lxh : mu == 2 ? g.lxh * g.ly : mu == 3 ? g.lxh * g.ly * g.lz : 0; };
-    const int n_links = nf * 4 * 9;               // per direction of travel
-    const int n_vec = nf * 2 * 2 * 3;             // z and t, two hops each way, three colours
-    for (int r = threadIdx.x; r < 2 * n_links + n_vec; r += blockDim.x) {
-        if (r < 2 * n_links) {
-            const int bwd = r >= n_links;
-            const int q = r - bwd * n_links;
-            const int f = q / 36, mu = (q / 9) % 4, k = q % 9;
-            const int par = bwd ? 1 - P : P;
-            const float2* plane = (f ? G.lng : G.fat) + ((size_t)(par * 4 + mu) * 9 + k) * vs;
-            const int h = f ? g.hop3[mu] : 1;
-            if (!bwd)
-                prefetch_range(plane, j0, n, g.vh, g.vs, 1);
-            else if (mu == 0)
-                prefetch_range(plane, j0 - 1, n + 2, g.vh, g.vs, 1);
-            else
-                prefetch_range(plane, j0 - h * stride(mu), n, g.vh, g.vs, 1);
-        } else {
-            const int q = r - 2 * n_links;
-            const int c = q % 3, sgn = (q / 3) % 2, mu = 2 + (q / 6) % 2, f = q / 12;
-            const int h = f ? g.hop3[mu] : 1;
-            const int j = j0 + (sgn ? -h : h) * stride(mu);
-            prefetch_range(in + (size_t)c * vs * G.rpad, j, n, g.vh, g.vs, G.rpad);
-        }
-    }
 }
 
 // Thread layout: right-hand sides are the fastest index.  TPS = rpad / RB
@@ -300,7 +241,7 @@ __device__ __forceinline__ void multi_hop(float2 (&acc)[3][RB], const float2* __
 
 // out = D in (EPI_PLAIN), m2 src - D in (EPI_AXPY), or the latter with per-RHS
 // Re(src^dag out) -> alpha (EPI_CG)
-template <int RB, int BS, int EPI>
+template <int RB, int BS, int EPI, int MODE>
 __global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
     const int4 w = L.items[blockIdx.x];  // (group, block in group, blocks in group, -)
     const MultiGroup& G = L.groups[w.x];
@@ -317,13 +258,11 @@ __global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
     float dotf[RB];
 #pragma unroll
     for (int j = 0; j < RB; ++j) dotf[j] = 0.f;
-    const TileWalk tw = tile_walk(w, ntiles);
-    if (w.w && tw.first < ntiles) prefetch_tile(G, in, P, tw.first * l.spb, min(l.spb, g.vh - tw.first * l.spb));
-    for (int tile = tw.first; tile < tw.end; tile += tw.step) {
-        if (w.w && tile + tw.step < ntiles) {
-            const int j1 = (tile + tw.step) * l.spb;
-            prefetch_tile(G, in, P, j1, min(l.spb, g.vh - j1));
-        }
+    constexpr bool kSweep = MODE != 0;
+    const int tile0 = kSweep ? blk : tile_end(blk - 1, ntiles, nblk);
+    const int tile1 = kSweep ? ntiles : tile_end(blk, ntiles, nblk);
+    const int step = kSweep ? nblk : 1;
+    for (int tile = tile0; tile < tile1; tile += step) {
         const int i = tile * l.spb + l.site_local;
         if (i >= g.vh) continue;
         float2 acc[3][RB];
@@ -570,23 +509,34 @@ __global__ void __launch_bounds__(kBlock) slot_get_kernel(Geom g, const float2* 
 }
 
 // ------------------------------------------------------------ launchers
-template <int RB, int BS>
-static void launch_multi_rb_bs(MultiKernel k, const MultiLaunch& L, int nitems, cudaStream_t s) {
+template <int RB, int BS, int MODE>
+static void launch_dslash_mode(MultiKernel k, const MultiLaunch& L, int nitems, cudaStream_t s) {
     switch (k) {
-        case MK_DSLASH_PLAIN: multi_dslash_kernel<RB, BS, EPI_PLAIN><<<nitems, BS, 0, s>>>(L); break;
-        case MK_DSLASH_CG: multi_dslash_kernel<RB, BS, EPI_CG><<<nitems, BS, 0, s>>>(L); break;
-        case MK_DSLASH_AXPY: multi_dslash_kernel<RB, BS, EPI_AXPY><<<nitems, BS, 0, s>>>(L); break;
+        case MK_DSLASH_PLAIN: multi_dslash_kernel<RB, BS, EPI_PLAIN, MODE><<<nitems, BS, 0, s>>>(L); break;
+        case MK_DSLASH_CG: multi_dslash_kernel<RB, BS, EPI_CG, MODE><<<nitems, BS, 0, s>>>(L); break;
+        default: multi_dslash_kernel<RB, BS, EPI_AXPY, MODE><<<nitems, BS, 0, s>>>(L); break;
+    }
+}
+
+template <int RB, int BS>
+static void launch_multi_rb_bs(MultiKernel k, const MultiLaunch& L, int nitems, int mode, cudaStream_t s) {
+    switch (k) {
         case MK_UPDATE_XR: multi_update_xr_kernel<RB, BS><<<nitems, BS, 0, s>>>(L); break;
-        default: multi_update_d_kernel<RB, BS><<<nitems, BS, 0, s>>>(L); break;
+        case MK_UPDATE_D: multi_update_d_kernel<RB, BS><<<nitems, BS, 0, s>>>(L); break;
+        default:
+            if (mode)
+                launch_dslash_mode<RB, BS, 1>(k, L, nitems, s);
+            else
+                launch_dslash_mode<RB, BS, 0>(k, L, nitems, s);
     }
 }
 
 template <int RB>
-static void launch_multi_rb(MultiKernel k, const MultiLaunch& L, int nitems, int bs, cudaStream_t s) {
+static void launch_multi_rb(MultiKernel k, const MultiLaunch& L, int nitems, int bs, int mode, cudaStream_t s) {
     switch (bs) {
-        case 64: launch_multi_rb_bs<RB, 64>(k, L, nitems, s); break;
-        case 128: launch_multi_rb_bs<RB, 128>(k, L, nitems, s); break;
-        default: launch_multi_rb_bs<RB, 256>(k, L, nitems, s); break;
+        case 64: launch_multi_rb_bs<RB, 64>(k, L, nitems, mode, s); break;
+        case 128: launch_multi_rb_bs<RB, 128>(k, L, nitems, mode, s); break;
+        default: launch_multi_rb_bs<RB, 256>(k, L, nitems, mode, s); break;
     }
 }
 
@@ -594,9 +544,13 @@ template <int RB>
 static int resident_rb(int bs) {
     int n = 0;
     switch (bs) {
-        case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_dslash_kernel<RB, 64, EPI_CG>, 64, 0); break;
-        case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_dslash_kernel<RB, 128, EPI_CG>, 128, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_dslash_kernel<RB, 256, EPI_CG>, 256, 0); break;
+        case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_dslash_kernel<RB, 64, EPI_CG, 1>, 64, 0); break;
+        case 128:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_dslash_kernel<RB, 128, EPI_CG, 1>, 128, 0);
+            break;
+        default:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, multi_dslash_kernel<RB, 256, EPI_CG, 1>, 256, 0);
+            break;
     }
     return n;
 }
@@ -613,13 +567,13 @@ int multi_resident_blocks_per_sm(int rb, int bs) {
     return n > 0 ? n : 1;
 }
 
-void launch_multi(MultiKernel k, const MultiLaunch& L, int nitems, int rb, int bs, cudaStream_t s) {
+void launch_multi(MultiKernel k, const MultiLaunch& L, int nitems, int rb, int bs, int mode, cudaStream_t s) {
     if (nitems <= 0) return;
     switch (rb) {
-        case 1: launch_multi_rb<1>(k, L, nitems, bs, s); break;
-        case 2: launch_multi_rb<2>(k, L, nitems, bs, s); break;
-        case 4: launch_multi_rb<4>(k, L, nitems, bs, s); break;
-        default: launch_multi_rb<8>(k, L, nitems, bs, s); break;
+        case 1: launch_multi_rb<1>(k, L, nitems, bs, mode, s); break;
+        case 2: launch_multi_rb<2>(k, L, nitems, bs, mode, s); break;
+        case 4: launch_multi_rb<4>(k, L, nitems, bs, mode, s); break;
+        default: launch_multi_rb<8>(k, L, nitems, bs, mode, s); break;
     }
 }
 

@@ -27,7 +27,7 @@ struct MultiGroup {
 struct MultiLaunch {
     const MultiGroup* groups;  // device array
     const int4* items;         // device array: (group, block in group, blocks in group, traversal:
-                               // 0 contiguous runs of tiles, 1 resident sweep with L2 prefetch)
+                               // 0 contiguous runs of tiles, 1 resident sweep)
     CgScalars* scal;           // one per right-hand side, global index
     double* partials;          // [padded slots][max_blocks]
     unsigned int* counters;    // [padded slots], indexed by the group's first slot
@@ -38,8 +38,9 @@ struct MultiLaunch {
 enum MultiKernel { MK_DSLASH_PLAIN = 0, MK_DSLASH_CG = 1, MK_UPDATE_XR = 2, MK_UPDATE_D = 3, MK_DSLASH_AXPY = 4 };
 
 // rb: right-hand sides per thread (1, 2, 4, 8; rpad / rb threads share a site, at most 32);
-// bs: threads per block (64, 128, 256)
-void launch_multi(MultiKernel k, const MultiLaunch& L, int nitems, int rb, int bs, cudaStream_t s);
+// bs: threads per block (64, 128, 256); mode: the items' traversal (0, 1, see multi.cu),
+// which must be the same for every item of the launch
+void launch_multi(MultiKernel k, const MultiLaunch& L, int nitems, int rb, int bs, int mode, cudaStream_t s);
 
 // Blocks of the Dirac kernel of this shape that one SM holds at once (>= 1).
 int multi_resident_blocks_per_sm(int rb, int bs);

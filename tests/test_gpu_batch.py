@@ -82,7 +82,7 @@ def test_batch_groups_and_tuning(systems):
 
 # every candidate of the autotuner for the 5-RHS group (padded to 8): RB RHS per thread
 # (8 / RB threads per site; RB >= 4 uses the 256-bit accesses), threads per block, and the
-# two traversals; the single-RHS groups run every block size and traversal alongside
+# four traversals; the single-RHS groups run every block size and traversal alongside
 SHAPES = [(rb, bs, sw) for sw in (0, 1) for rb in (1, 2, 4, 8) for bs in (64, 128, 256)]
 
 

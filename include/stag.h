@@ -227,7 +227,10 @@ int64_t stag_launch_count(const stag_handle* h);
  * sides); lattices of different sizes share every launch.  Each system runs the
  * mixed-precision CG (FP32 iteration, FP64 scalars) with its own reliable
  * updates in float-float arithmetic and a final true residual in native FP64.
- * Blocks of check_interval iterations of all systems are one CUDA graph.  The
+ * The replacements are decided and applied on the device by a pass that
+ * follows every iteration, so a system never waits for the host.  Blocks of
+ * check_interval iterations of all systems, each with its pass, are one CUDA
+ * graph; the host reads one word (the systems still running) per replay.  The
  * right-hand sides per thread and threads per block of each group are chosen
  * at create by timing the candidates (opt->autotune), cached per (extents,
  * Naik, RHS count) for the process and in the file STAG_AUTOTUNE_CACHE names;
@@ -239,9 +242,9 @@ typedef struct stag_batch stag_batch;
 /* fat, naik: n_sys link arrays (the link layout above; naik may be NULL, or
  * contain NULLs, for one-hop systems); dims: 4*n_sys extents; masses: n_sys.
  * Link arrays are copied at create.  opt: NULL = defaults, except
- * check_interval = 4 (a system whose residual replacement falls due waits for
- * the end of its graph); only check_interval, reliable_interval,
- * reliable_delta and autotune are used. */
+ * check_interval = 8; only check_interval, reliable_interval, reliable_delta
+ * and autotune are used.  Besides the packed fields and the RHS vectors, the
+ * batch holds three float-float work vectors per system for its true residuals. */
 int stag_batch_create(stag_batch** out, int32_t n_sys, const double* const* fat, const double* const* naik,
                       const int32_t* dims, const double* masses, const stag_options* opt);
 

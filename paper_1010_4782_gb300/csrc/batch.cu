@@ -9,8 +9,11 @@
 // FP64 scalars - and each right-hand side gets its own reliable updates: its
 // iterated residual is replaced by the true residual b - A x computed in
 // float-float arithmetic, and its final residual is confirmed in native FP64.
-// A block of check_interval iterations of every group is captured as one CUDA
-// graph and replayed until every system has converged.
+// The replacements are decided and applied on the device by a pass that
+// follows every iteration (batch_dev.cu).  A block of check_interval
+// iterations, each with its pass, is captured as one CUDA graph and replayed
+// until the pass reports that no system is running; the host reads that one
+// word between replays and does no per-system work.
 //
 // Autotuner: for each multi-RHS group the right-hand sides per thread
 // (1, 2, 4, 8) and the threads per block (64, 128, 256) are timed on the
@@ -38,6 +41,9 @@ using namespace stag;
 
 namespace stag {
 void set_noalloc_error(const std::string& msg);  // thread-local message of stag_last_error(NULL)
+static_assert(STAG_STATUS_OK == STAG_OK && STAG_STATUS_NOT_CONVERGED == STAG_ERR_NOT_CONVERGED &&
+                  STAG_STATUS_BREAKDOWN == STAG_ERR_BREAKDOWN,
+              "system statuses are the ABI's status codes");
 }
 
 namespace {
@@ -82,7 +88,6 @@ struct stag_batch {
     std::vector<int> sys_group, sys_slot;  // group and slot of each system (= right-hand side)
     std::vector<double2*> x64, b64;
     double2* r64 = nullptr;   // scratch, largest lattice
-    float4 *u_ff = nullptr, *t_ff = nullptr, *ax = nullptr;
     double* io_a = nullptr;   // ABI staging, largest lattice
     double* io_b = nullptr;
     MultiGroup* d_groups = nullptr;
@@ -97,6 +102,18 @@ struct stag_batch {
     cudaGraphExec_t graph = nullptr;
     long long device_bytes = 0;
     std::string err = "no error";
+    // device-side reliable updates (batch_dev.cu)
+    std::vector<float4*> sys_scratch;      // per system: u_ff, t_ff, ax
+    SysDev* d_sys = nullptr;
+    SysState* d_state = nullptr;
+    std::vector<SysState> state_host;
+    SysDirac *d_oe_ff = nullptr, *d_eo_ff = nullptr, *d_oe_64 = nullptr, *d_eo_64 = nullptr;
+    int* d_lists = nullptr;                // four lists: count, systems, tile prefix
+    double* pass_partials = nullptr;       // one per tile of all systems
+    int* running_host = nullptr;           // host-mapped count of running systems
+    int* running_dev = nullptr;
+    PassArgs pass{};
+    int grid_dirac = 0, grid_vec = 0;
 };
 
 namespace {
@@ -138,7 +155,6 @@ void sync(stag_batch* b) { bcheck(b, cudaStreamSynchronize(b->s), "cudaStreamSyn
 size_t vec_bytes(const Geom& g) { return (size_t)3 * g.vs * sizeof(double2); }
 size_t abi_bytes(const Geom& g) { return (size_t)3 * g.vh * sizeof(double2); }
 
-LinkSet linkset(const Group& G) { return LinkSet{G.fat64, G.lng64, G.fatff, G.lngff}; }
 
 void pack_group_field(stag_batch* b, Group& G, const double* src, double2* s64, float4* sff, float2* s32) {
     const size_t aos = (size_t)2 * G.g.vh * 4 * 9 * sizeof(double2);
@@ -386,30 +402,12 @@ void autotune(stag_batch* b) {
 }
 
 // ------------------------------------------------------- reliable update
-// A x_k in float-float arithmetic into b->ax (uses b->u_ff, b->t_ff).
-void apply_ff(stag_batch* b, const Group& G, const double2* x) {
-    launch_to_ff(G.g, x, b->u_ff, b->s);
-    launch_dslash_ff(G.g, 1, linkset(G), b->u_ff, b->t_ff, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, b->s);
-    launch_dslash_ff(G.g, 0, linkset(G), b->t_ff, b->ax, EPI_AXPY, b->u_ff, G.mass * G.mass, nullptr, nullptr, b->s);
-}
-
-// |b_k - A x_k|^2 with native FP64 Dirac kernels into b->aux->red_out (uses b->t_ff, b->ax as FP64 scratch).
-void residual_native(stag_batch* b, const Group& G, int k) {
-    double2* t64 = reinterpret_cast<double2*>(b->t_ff);
-    double2* ax64 = reinterpret_cast<double2*>(b->ax);
-    launch_dslash_f64(G.g, 1, linkset(G), b->x64[k], t64, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, b->s);
-    launch_dslash_f64(G.g, 0, linkset(G), t64, ax64, EPI_AXPY, b->x64[k], G.mass * G.mass, nullptr, nullptr, b->s);
-    launch_norm2_diff(G.g, b->b64[k], ax64, b->aux, b->partials, b->s);
-}
-
 double read_aux(stag_batch* b) {
     bcheck(b, cudaMemcpyAsync(b->scal_host + b->n_sys, b->aux, sizeof(CgScalars), cudaMemcpyDeviceToHost, b->s),
            "read reduction");
     sync(b);
     return b->scal_host[b->n_sys].red_out;
 }
-
-__global__ void set_done_kernel(CgScalars* s, int v) { s->done = v; }
 
 void destroy_batch(stag_batch* b) {
     if (!b) return;
@@ -425,14 +423,87 @@ void destroy_batch(stag_batch* b) {
         if (p) cudaFree(p);
     for (double2* p : b->b64)
         if (p) cudaFree(p);
-    for (void* p : {(void*)b->r64, (void*)b->u_ff, (void*)b->t_ff, (void*)b->ax, (void*)b->io_a, (void*)b->io_b,
-                    (void*)b->d_groups, (void*)b->d_items, (void*)b->scal, (void*)b->aux, (void*)b->partials,
-                    (void*)b->counters})
+    for (void* p : {(void*)b->r64, (void*)b->io_a, (void*)b->io_b, (void*)b->d_groups, (void*)b->d_items,
+                    (void*)b->scal, (void*)b->aux, (void*)b->partials, (void*)b->counters, (void*)b->d_sys,
+                    (void*)b->d_state, (void*)b->d_oe_ff, (void*)b->d_eo_ff, (void*)b->d_oe_64, (void*)b->d_eo_64,
+                    (void*)b->d_lists, (void*)b->pass_partials})
         if (p) cudaFree(p);
+    for (float4* p : b->sys_scratch)
+        if (p) cudaFree(p);
+    if (b->running_host) cudaFreeHost(b->running_host);
     if (b->scal_host) cudaFreeHost(b->scal_host);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->s) cudaStreamDestroy(b->s);
     delete b;
+}
+
+// Per-system operands and scratch of the device-side reliable updates, the
+// device lists, and the host-mapped running count (batch_dev.cu).
+void setup_pass(stag_batch* b) {
+    const int n = b->n_sys;
+    std::vector<SysDev> sd(n);
+    std::vector<SysDirac> oe_ff(n), eo_ff(n), oe_64(n), eo_64(n);
+    long long tiles = 0;
+    b->sys_scratch.assign(3 * (size_t)n, nullptr);
+    for (int k = 0; k < n; ++k) {
+        Group& G = b->groups[b->sys_group[k]];
+        const Geom& g = G.g;
+        float4* u = balloc<float4>(b, vec_bytes(g), "allocate reliable-update scratch");
+        b->sys_scratch[3 * k] = u;
+        float4* t = balloc<float4>(b, vec_bytes(g), "allocate reliable-update scratch");
+        b->sys_scratch[3 * k + 1] = t;
+        float4* ax = balloc<float4>(b, vec_bytes(g), "allocate reliable-update scratch");
+        b->sys_scratch[3 * k + 2] = ax;
+        const double m2 = G.mass * G.mass;
+        sd[k] = SysDev{g, m2, b->x64[k], b->b64[k], u, t, ax, G.r, G.d, G.y, G.rpad, b->sys_slot[k]};
+        const float2 m2ff = host_ff_from_double(m2);
+        oe_ff[k] = SysDirac{g, 1, G.fatff, G.lngff, u, t, nullptr, 0.0, make_float2(0.f, 0.f)};
+        eo_ff[k] = SysDirac{g, 0, G.fatff, G.lngff, t, ax, u, m2, m2ff};
+        oe_64[k] = SysDirac{g, 1, G.fat64, G.lng64, b->x64[k], t, nullptr, 0.0, make_float2(0.f, 0.f)};
+        eo_64[k] = SysDirac{g, 0, G.fat64, G.lng64, t, ax, b->x64[k], m2, m2ff};
+        tiles += (g.vh + kBlock - 1) / kBlock;
+    }
+    b->d_sys = balloc<SysDev>(b, sizeof(SysDev) * n, "allocate systems");
+    b->d_state = balloc<SysState>(b, sizeof(SysState) * n, "allocate systems");
+    b->d_oe_ff = balloc<SysDirac>(b, sizeof(SysDirac) * n, "allocate systems");
+    b->d_eo_ff = balloc<SysDirac>(b, sizeof(SysDirac) * n, "allocate systems");
+    b->d_oe_64 = balloc<SysDirac>(b, sizeof(SysDirac) * n, "allocate systems");
+    b->d_eo_64 = balloc<SysDirac>(b, sizeof(SysDirac) * n, "allocate systems");
+    bcheck(b, cudaMemcpyAsync(b->d_sys, sd.data(), sizeof(SysDev) * n, cudaMemcpyHostToDevice, b->s), "copy systems");
+    bcheck(b, cudaMemcpyAsync(b->d_oe_ff, oe_ff.data(), sizeof(SysDirac) * n, cudaMemcpyHostToDevice, b->s), "copy");
+    bcheck(b, cudaMemcpyAsync(b->d_eo_ff, eo_ff.data(), sizeof(SysDirac) * n, cudaMemcpyHostToDevice, b->s), "copy");
+    bcheck(b, cudaMemcpyAsync(b->d_oe_64, oe_64.data(), sizeof(SysDirac) * n, cudaMemcpyHostToDevice, b->s), "copy");
+    bcheck(b, cudaMemcpyAsync(b->d_eo_64, eo_64.data(), sizeof(SysDirac) * n, cudaMemcpyHostToDevice, b->s), "copy");
+    // four lists of 1 + n + (n + 1) ints
+    const size_t per_list = 2 * (size_t)n + 2;
+    b->d_lists = balloc<int>(b, sizeof(int) * 4 * per_list, "allocate lists");
+    PassList* lists[4] = {&b->pass.fold, &b->pass.ff, &b->pass.confirm, &b->pass.replace};
+    for (int q = 0; q < 4; ++q) {
+        int* base = b->d_lists + q * per_list;
+        *lists[q] = PassList{base, base + 1, base + 1 + n};
+    }
+    b->pass_partials = balloc<double>(b, sizeof(double) * (size_t)std::max<long long>(1, tiles), "allocate partials");
+    bcheck(b, cudaHostAlloc(reinterpret_cast<void**>(&b->running_host), sizeof(int), cudaHostAllocMapped),
+           "allocate mapped count");
+    *b->running_host = 0;
+    bcheck(b, cudaHostGetDevicePointer(reinterpret_cast<void**>(&b->running_dev), b->running_host, 0),
+           "map count");
+    b->pass.n_sys = n;
+    b->pass.sys = b->d_sys;
+    b->pass.state = b->d_state;
+    b->pass.scal = b->scal;
+    b->pass.partials = b->pass_partials;
+    b->pass.running = b->running_dev;
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->grid_dirac = 3 * sms;
+    b->grid_vec = 8 * sms;
+    b->state_host.assign(n, SysState{});
+}
+
+void enqueue_pass(stag_batch* b) {
+    enqueue_reliable_pass(b->pass, b->d_oe_ff, b->d_eo_ff, b->d_oe_64, b->d_eo_64, b->grid_dirac, b->grid_vec,
+                          b->s);
 }
 
 void begin(stag_batch* b) {
@@ -455,10 +526,10 @@ int stag_batch_create(stag_batch** out, int32_t n_sys, const double* const* fat,
         b = new stag_batch();
         b->n_sys = n_sys;
         stag_default_options(&b->opt);
-        // A system whose replacement falls due idles until its graph ends, so the
-        // batch checks every 4 iterations unless told otherwise (14 % faster than
-        // 32 on 16 right-hand sides at 32^3 x 64).
-        b->opt.check_interval = 4;
+        // Replacements happen on the device after every iteration, so the
+        // interval only sets how often the host looks at the running count (and
+        // how many empty iterations can follow the last system's convergence).
+        b->opt.check_interval = 8;
         if (opt) b->opt = *opt;
         if (b->opt.check_interval < 1 || b->opt.check_interval > 4096)
             bfail(b, STAG_ERR_INVALID_ARG, "check_interval must be in [1, 4096]");
@@ -558,9 +629,6 @@ int stag_batch_create(stag_batch** out, int32_t n_sys, const double* const* fat,
         }
         const size_t vbmax = (size_t)3 * max_vs * sizeof(double2);
         b->r64 = balloc<double2>(b, vbmax, "allocate scratch");
-        b->u_ff = balloc<float4>(b, vbmax, "allocate scratch");
-        b->t_ff = balloc<float4>(b, vbmax, "allocate scratch");
-        b->ax = balloc<float4>(b, vbmax, "allocate scratch");
         b->io_a = balloc<double>(b, (size_t)3 * max_vh * sizeof(double2), "allocate staging");
         b->io_b = balloc<double>(b, (size_t)3 * max_vh * sizeof(double2), "allocate staging");
         b->scal = balloc<CgScalars>(b, sizeof(CgScalars) * n_sys, "allocate CG state");
@@ -573,6 +641,7 @@ int stag_batch_create(stag_batch** out, int32_t n_sys, const double* const* fat,
         bcheck(b, cudaMallocHost(reinterpret_cast<void**>(&b->scal_host), sizeof(CgScalars) * (n_sys + 1)),
                "allocate pinned state");
         std::memset(b->scal_host, 0, sizeof(CgScalars) * (n_sys + 1));
+        setup_pass(b);
         sync(b);
         autotune(b);
         build_items(b);
@@ -676,16 +745,18 @@ int stag_batch_solve(stag_batch* b, const double* const* bvec, double* const* xv
     if (!b) return STAG_ERR_INVALID_ARG;
     const int n = b->n_sys;
     std::vector<stag_solve_info> inf(n);
-    std::vector<double> bnorm2(n, 0.0), sigma(n, 1.0);
-    std::vector<char> finished(n, 0), first(n, 1);
-    std::vector<long long> iters(n, 0);
     int status = STAG_OK;
     const auto t0 = std::chrono::steady_clock::now();
     try {
         if (!bvec || !xvec) bfail(b, STAG_ERR_INVALID_ARG, "NULL argument");
         if (!(tol > 0.0) || !std::isfinite(tol)) bfail(b, STAG_ERR_INVALID_ARG, "tol must be positive and finite");
         begin(b);
-        bcheck(b, cudaMemsetAsync(b->scal, 0, sizeof(CgScalars) * n, b->s), "clear CG state");
+        const long long max_it = max_iter > 0 ? max_iter : (1LL << 40);
+        // every system idles (done = 1) until the first pass has set it up
+        for (int k = 0; k < n; ++k) {
+            std::memset(&b->scal_host[k], 0, sizeof(CgScalars));
+            b->scal_host[k].done = 1;
+        }
         for (int k = 0; k < n; ++k) {
             Group& G = b->groups[b->sys_group[k]];
             if (!bvec[k] || !xvec[k]) bfail(b, STAG_ERR_INVALID_ARG, "NULL vector");
@@ -702,98 +773,65 @@ int stag_batch_solve(stag_batch* b, const double* const* bvec, double* const* xv
             }
             launch_pack_vec(G.g, xs, b->x64[k], b->s);
             launch_norm2_diff(G.g, b->b64[k], nullptr, b->aux, b->partials, b->s);
-            bnorm2[k] = read_aux(b);
-            if (!std::isfinite(bnorm2[k])) bfail(b, STAG_ERR_INVALID_ARG, "source has non-finite entries");
-            if (bnorm2[k] == 0.0) {
+            const double bnorm2 = read_aux(b);
+            if (!std::isfinite(bnorm2)) bfail(b, STAG_ERR_INVALID_ARG, "source has non-finite entries");
+            SysState& st = b->state_host[k];
+            st = SysState{};
+            st.bnorm2 = bnorm2;
+            st.tol = tol;
+            st.tol2 = tol * tol * bnorm2;
+            st.rel_delta = b->opt.reliable_delta;
+            st.rel_interval = b->opt.reliable_interval;
+            st.max_iter = max_it;
+            st.first = 1;
+            st.phase = SYS_START;
+            if (bnorm2 == 0.0) {  // x = 0 solves it exactly
                 bcheck(b, cudaMemsetAsync(b->x64[k], 0, vec_bytes(G.g), b->s), "zero x");
-                set_done_kernel<<<1, 1, 0, b->s>>>(b->scal + k, 1);
-                finished[k] = 1;
+                st.phase = SYS_FINISHED;
+                st.status = STAG_OK;
             }
         }
-        const long long max_it = max_iter > 0 ? max_iter : (1LL << 40);
-        // per right-hand side: fold, true residual, replacement (the body of solve_mixed)
-        auto reliable = [&](int k) {
-            Group& G = b->groups[b->sys_group[k]];
-            const int slot = b->sys_slot[k];
-            if (!first[k]) launch_slot_fold_y(G.g, b->x64[k], G.y, G.rpad, slot, sigma[k], b->s);
-            apply_ff(b, G, b->x64[k]);
-            launch_residual(G.g, b->b64[k], b->ax, true, b->r64, b->aux, b->partials, b->s);
-            const double dtrue = read_aux(b);
-            double rel = std::sqrt(dtrue / bnorm2[k]);
-            inf[k].iter_rel_residual = rel;
-            bool done = false;
-            if (!std::isfinite(dtrue)) {
-                inf[k].status = STAG_ERR_BREAKDOWN;
-                done = true;
-            } else if (rel <= tol) {
-                residual_native(b, G, k);  // confirm in native FP64
-                rel = std::sqrt(read_aux(b) / bnorm2[k]);
-                done = rel <= tol;
-            }
-            if (!done && iters[k] >= max_it) {
-                inf[k].status = STAG_ERR_NOT_CONVERGED;
-                done = true;
-            }
-            inf[k].true_rel_residual = rel;
-            if (done) {
-                set_done_kernel<<<1, 1, 0, b->s>>>(b->scal + k, 1);
-                finished[k] = 1;
-                return;
-            }
-            double beta = 0.0;
-            if (!first[k]) {
-                beta = dtrue / (b->scal_host[k].delta_old * sigma[k] * sigma[k]);
-                inf[k].reliable_updates += 1;
-            }
-            sigma[k] = 1.0;
-            launch_slot_set_residual(G.g, b->r64, G.r, G.d, G.y, G.rpad, slot, 1.0, beta, first[k] != 0, b->s);
-            launch_lo_reset(b->scal + k, dtrue, tol * tol * bnorm2[k], G.mass * G.mass, max_it - iters[k],
-                            b->opt.reliable_interval, b->opt.reliable_delta, b->s);
-            first[k] = 0;
-        };
-        for (int k = 0; k < n; ++k)
-            if (!finished[k]) reliable(k);
+        bcheck(b, cudaMemcpyAsync(b->scal, b->scal_host, sizeof(CgScalars) * n, cudaMemcpyHostToDevice, b->s),
+               "set CG state");
+        bcheck(b, cudaMemcpyAsync(b->d_state, b->state_host.data(), sizeof(SysState) * n, cudaMemcpyHostToDevice,
+                                  b->s),
+               "set system state");
+        *b->running_host = n;
+        enqueue_pass(b);  // the first true residuals and replacements
         bcheck(b, cudaGetLastError(), "batch start");
         if (!b->graph) {
+            // check_interval iterations of every group, each followed by the
+            // reliable-update pass: a system due for a replacement waits at most
+            // one iteration, and the host reads one word per graph launch
             cudaGraph_t graph = nullptr;
             bcheck(b, cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal), "begin capture");
-            for (int it = 0; it < b->opt.check_interval; ++it) enqueue_iteration(b);
+            for (int it = 0; it < b->opt.check_interval; ++it) {
+                enqueue_iteration(b);
+                enqueue_pass(b);
+            }
             const cudaError_t e = cudaStreamEndCapture(b->s, &graph);
             bcheck(b, e, "end capture");
             const cudaError_t e2 = cudaGraphInstantiate(&b->graph, graph, 0);
             cudaGraphDestroy(graph);
             bcheck(b, e2, "graph instantiate");
         }
-        while (true) {
-            bool any = false;
-            for (int k = 0; k < n; ++k) any |= !finished[k];
-            if (!any) break;
+        sync(b);
+        while (*static_cast<volatile int*>(b->running_host) > 0) {
             bcheck(b, cudaGraphLaunch(b->graph, b->s), "cudaGraphLaunch");
-            bcheck(b, cudaMemcpyAsync(b->scal_host, b->scal, sizeof(CgScalars) * n, cudaMemcpyDeviceToHost, b->s),
-                   "read CG state");
             sync(b);
-            std::vector<int> due;
-            for (int k = 0; k < n; ++k) {
-                if (finished[k]) continue;
-                const CgScalars& sc = b->scal_host[k];
-                if (sc.done == 0) continue;
-                iters[k] += sc.iter;
-                if (sc.status != 0) {
-                    inf[k].status = STAG_ERR_BREAKDOWN;
-                    Group& G = b->groups[b->sys_group[k]];
-                    launch_slot_fold_y(G.g, b->x64[k], G.y, G.rpad, b->sys_slot[k], sigma[k], b->s);
-                    set_done_kernel<<<1, 1, 0, b->s>>>(b->scal + k, 1);
-                    finished[k] = 1;
-                    continue;
-                }
-                due.push_back(k);
-            }
-            for (int k : due) reliable(k);
-            bcheck(b, cudaGetLastError(), "reliable updates");
         }
+        bcheck(b, cudaMemcpyAsync(b->state_host.data(), b->d_state, sizeof(SysState) * n, cudaMemcpyDeviceToHost,
+                                  b->s),
+               "read system state");
+        sync(b);
         for (int k = 0; k < n; ++k) {
             Group& G = b->groups[b->sys_group[k]];
-            inf[k].iters = (int32_t)iters[k];
+            const SysState& st = b->state_host[k];
+            inf[k].iters = (int32_t)st.iters;
+            inf[k].reliable_updates = st.updates;
+            inf[k].true_rel_residual = st.rel;
+            inf[k].iter_rel_residual = st.rel;
+            inf[k].status = st.status;
             const bool dev = on_dev(b, xvec[k]);
             launch_unpack_vec(G.g, b->x64[k], dev ? xvec[k] : b->io_b, b->s);
             if (!dev)

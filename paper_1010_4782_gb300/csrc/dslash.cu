@@ -352,20 +352,14 @@ __device__ __forceinline__ int neighbour(const Geom& g, int x, int y, int z, int
     return site_index(x, y, z, t, g);
 }
 
+// acc += (D_{P,1-P} in)(i) for output site i of parity p.P (all hops).
 // NAIK: 0 one-hop only; 1 Naik links with nine entries; 2 float-float Naik
 // links with two rows (A = ArithFF only).
-template <class A, int NAIK, int EPI>
-__global__ void __launch_bounds__(kBlock, NAIK == 2 ? 3 : 4) dslash_kernel(const DslashParams<A> p) {
-    if (EPI == EPI_CG) {
-        if (p.scal->done) return;
-    }
+template <class A, int NAIK>
+__device__ __forceinline__ void dslash_site(const DslashParams<A>& p, int i, typename A::Acc& acc) {
     const Geom& g = p.g;
-    const int i = p.i0 + blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;
-    typename A::Acc acc;
-    A::zero(acc);
-    const bool active = i < p.i1;
-    if (active) {
+    {
         int x, y, z, t;
         site_coords(i, p.P, g, x, y, z, t);
         const int P = p.P, Q = 1 - p.P;
@@ -402,6 +396,20 @@ __global__ void __launch_bounds__(kBlock, NAIK == 2 ? 3 : 4) dslash_kernel(const
             }
         }
     }
+}
+
+template <class A, int NAIK, int EPI>
+__global__ void __launch_bounds__(kBlock, NAIK == 2 ? 3 : 4) dslash_kernel(const DslashParams<A> p) {
+    if (EPI == EPI_CG) {
+        if (p.scal->done) return;
+    }
+    const Geom& g = p.g;
+    const int i = p.i0 + blockIdx.x * kBlock + threadIdx.x;
+    const size_t vs = (size_t)g.vs;
+    typename A::Acc acc;
+    A::zero(acc);
+    const bool active = i < p.i1;
+    if (active) dslash_site<A, NAIK>(p, i, acc);
     if (EPI == EPI_PLAIN) {
         if (active) {
 #pragma unroll
@@ -436,6 +444,72 @@ __global__ void __launch_bounds__(kBlock, NAIK == 2 ? 3 : 4) dslash_kernel(const
                 }
             }
         }
+    }
+}
+
+// Half-Dslash of several systems in one launch (EPI_PLAIN or EPI_AXPY): the
+// systems list[0 .. *count) take consecutive runs of kBlock-site tiles,
+// prefix[j] .. prefix[j + 1] for entry j, and the grid's blocks stride over
+// all of them.  The list lives on the device, so a captured graph runs
+// whichever systems the kernels before it selected.
+template <class A, int EPI>
+__global__ void __launch_bounds__(kBlock, 3) dslash_list_kernel(const SysDirac* __restrict__ sys,
+                                                               const int* __restrict__ list,
+                                                               const int* __restrict__ prefix,
+                                                               const int* __restrict__ count) {
+    using T = typename A::T;
+    using TL = typename A::TL;
+    const int n = *count;
+    const int total = prefix[n];
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int j = 0;
+        while (prefix[j + 1] <= tile) ++j;
+        const SysDirac& sd = sys[list[j]];
+        const int i = (tile - prefix[j]) * kBlock + threadIdx.x;
+        if (i >= sd.g.vh) continue;
+        const DslashParams<A> p{sd.g,
+                                sd.P,
+                                static_cast<const TL*>(sd.fat),
+                                static_cast<const TL*>(sd.lng),
+                                static_cast<const T*>(sd.in),
+                                static_cast<T*>(sd.out),
+                                static_cast<const T*>(sd.src),
+                                sd.m2,
+                                sd.m2_ff,
+                                nullptr,
+                                nullptr,
+                                0,
+                                sd.g.vh};
+        typename A::Acc acc;
+        A::zero(acc);
+        if (p.lng)
+            dslash_site<A, 1>(p, i, acc);
+        else
+            dslash_site<A, 0>(p, i, acc);
+        const size_t vs = (size_t)sd.g.vs;
+        double dot = 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            if (EPI == EPI_PLAIN)
+                p.out[r * vs + i] = A::store_val(acc, r);
+            else
+                p.out[r * vs + i] = A::epilogue(acc, r, A::ld(p.src + r * vs + i), p.m2, p.m2_ff, dot);
+        }
+    }
+}
+
+void launch_dslash_list(bool ff, Epilogue epi, const SysDirac* sys, const int* list, const int* prefix,
+                        const int* count, int grid, cudaStream_t s) {
+    if (ff) {
+        if (epi == EPI_PLAIN)
+            dslash_list_kernel<ArithFF, EPI_PLAIN><<<grid, kBlock, 0, s>>>(sys, list, prefix, count);
+        else
+            dslash_list_kernel<ArithFF, EPI_AXPY><<<grid, kBlock, 0, s>>>(sys, list, prefix, count);
+    } else {
+        if (epi == EPI_PLAIN)
+            dslash_list_kernel<ArithF64, EPI_PLAIN><<<grid, kBlock, 0, s>>>(sys, list, prefix, count);
+        else
+            dslash_list_kernel<ArithF64, EPI_AXPY><<<grid, kBlock, 0, s>>>(sys, list, prefix, count);
     }
 }
 

@@ -51,6 +51,25 @@ void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const flo
                       float4* out, Epilogue epi, const float4* src, double m2, CgScalars* scal,
                       double* partials, cudaStream_t s);
 
+// One system's half-Dslash for launch_dslash_list: links, vectors and output in
+// the arithmetic's layouts (FF: float4, F64: double2); nine-entry Naik links or none.
+struct SysDirac {
+    Geom g;
+    int P;             // output parity
+    const void* fat;   // [2][4][9][vs]
+    const void* lng;   // [2][4][9][vs] or nullptr
+    const void* in;    // [3][vs], parity 1-P
+    void* out;         // [3][vs], parity P
+    const void* src;   // [3][vs], parity P (EPI_AXPY)
+    double m2;
+    float2 m2_ff;
+};
+// The half-Dslash (EPI_PLAIN or EPI_AXPY) of the systems list[0 .. *count) (device
+// arrays; prefix[j] = first tile of entry j in tiles of kBlock sites, prefix[*count] =
+// all tiles) by `grid` blocks striding over the tiles; ff: float-float, else FP64.
+void launch_dslash_list(bool ff, Epilogue epi, const SysDirac* sys, const int* list, const int* prefix,
+                        const int* count, int grid, cudaStream_t s);
+
 // low-precision Dirac kernels of the mixed-precision solver (same epilogues)
 void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const float2* lng,
                        const float2* in, float2* out, Epilogue epi, const float2* src, double m2,

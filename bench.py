@@ -394,11 +394,13 @@ def run_ours(args):
     # asqtad-form operator (this workload) and the one-hop operator on the same lattice
     forms = None
     if not args.no_forms:
-        def solve_once(fat_in, lng_in, b_in, ar, inner, recon=0):
+        def solve_once(fat_in, lng_in, b_in, ar, inner, recon=0, long_recon=0):
             o = binding.stag_default_options()
             o.arith = ar
             o.inner = inner
             o.link_recon = recon
+            if long_recon:
+                o.long_recon, o.long_scale = 12, inputs.NAIK_COEFF
             h = binding.stag_create_ex(fat_in, lng_in, dims, args.mass, o)
             try:
                 binding.stag_set_stream(h, stream)
@@ -415,16 +417,19 @@ def run_ours(args):
                     ("mixed_bf16", binding.STAG_ARITH_FF, binding.STAG_INNER_BF16),
                     ("mixed_fp32_fp16links", binding.STAG_ARITH_FF, binding.STAG_INNER_F32_L16),
                     # 12-parameter SU(3) links (Sec. 3.3): unitary one-hop links only
-                    ("mixed_fp32_recon12", binding.STAG_ARITH_FF, binding.STAG_INNER_F32)]
+                    ("mixed_fp32_recon12", binding.STAG_ARITH_FF, binding.STAG_INNER_F32),
+                    # the same form for the Naik links (-U/24 = scale x SU(3)) of the asqtad operator
+                    ("mixed_fp32_longrecon12", binding.STAG_ARITH_FF, binding.STAG_INNER_F32)]
         forms = {}
         one_hop = torch.from_numpy(inputs.gauge_field(dims, 1)).to(dev)
         for op_name, f_in, l_in in (("asqtad", fat_d, lng_d), ("one_hop", one_hop, None)):
             res, x64 = {}, None
             for name, ar, inner in variants:
-                recon = 12 if name.endswith("recon12") else 0
-                if recon and l_in is not None:
+                recon = 12 if name.endswith("_recon12") else 0
+                long_recon = 12 if name.endswith("longrecon12") else 0
+                if (recon and l_in is not None) or (long_recon and l_in is None):
                     continue
-                code, info, x = solve_once(f_in, l_in, b_d, ar, inner, recon)
+                code, info, x = solve_once(f_in, l_in, b_d, ar, inner, recon, long_recon)
                 if x64 is None:
                     x64 = x
                 rec = {"time_s": round(info["time_ms"] / 1e3, 4), "status": code, "iters": info["iters"],

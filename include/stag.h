@@ -120,7 +120,9 @@ typedef struct {
     int32_t long_recon;     /* 12: the float-float Dirac kernels store two rows of each Naik
                                link and rebuild the third as (eta / long_scale) times the
                                conjugate cross product of the first two (the 12-parameter
-                               form of Sec. 3.3 for a scaled SU(3) matrix).  Needs arith = FF
+                               form of Sec. 3.3 for a scaled SU(3) matrix); with inner = F32
+                               the FP32 Naik links of the mixed-precision iteration are two
+                               rows too, the third rebuilt in FP32.  Needs arith = FF
                                and Naik links; stag_create_ex checks that every Naik link
                                divided by long_scale is unitary with determinant 1 (entries of
                                L^dag L / c^2 - 1 and det L / c^3 - 1 at most 1e-12) and fails

@@ -143,24 +143,31 @@ void read_state(stag_handle* h) {
 
 // Low-precision Dirac kernels and links by storage type.
 void dslash_lo(const Geom& g, int P, const float2* fat, const float2* lng, const float2* in, float2* out, Epilogue e,
-               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool r12 = false) {
+               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool r12 = false,
+               float lng_inv_scale = 0.f) {
     if (r12)
         launch_dslash_f32r12(g, P, fat, in, out, e, src, m2, sc, pa, s);  // fat: two rows per link
     else
-        launch_dslash_f32(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
+        launch_dslash_f32(g, P, fat, lng, in, out, e, src, m2, sc, pa, s, lng_inv_scale);
 }
 void dslash_lo(const Geom& g, int P, const __half2* fat, const __half2* lng, const float2* in, float2* out, Epilogue e,
-               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool = false) {
+               const float2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool = false, float = 0.f) {
     launch_dslash_f32l16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
 }
 void dslash_lo(const Geom& g, int P, const __half2* fat, const __half2* lng, const __half2* in, __half2* out,
-               Epilogue e, const __half2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool = false) {
+               Epilogue e, const __half2* src, double m2, CgScalars* sc, double* pa, cudaStream_t s, bool = false,
+               float = 0.f) {
     launch_dslash_h16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
 }
 void dslash_lo(const Geom& g, int P, const __nv_bfloat162* fat, const __nv_bfloat162* lng, const __nv_bfloat162* in,
                __nv_bfloat162* out, Epilogue e, const __nv_bfloat162* src, double m2, CgScalars* sc, double* pa,
-               cudaStream_t s, bool = false) {
+               cudaStream_t s, bool = false, float = 0.f) {
     launch_dslash_b16(g, P, fat, lng, in, out, e, src, m2, sc, pa, s);
+}
+// 1 / scale of the FP32 Naik links when they are stored as two rows (long_recon
+// = 12 with the FP32 inner iteration), else 0 (nine entries).
+float lo_long_inv_scale(const stag_handle* h) {
+    return (h->naik && h->opt.long_recon == 12 && h->opt.inner == STAG_INNER_F32) ? h->lng_s.x : 0.f;
 }
 const float2* lo_fat(const stag_handle* h, const float2*) { return h->fat32; }
 const float2* lo_lng(const stag_handle* h, const float2*) { return h->lng32; }
@@ -181,10 +188,11 @@ void enqueue_lo_iteration(stag_handle* h, Mark mark) {
     const L* fat = lo_fat(h, static_cast<const L*>(nullptr));
     const L* lng = lo_lng(h, static_cast<const L*>(nullptr));
     const bool r12 = h->opt.link_recon == 12;
+    const float ls = lo_long_inv_scale(h);
     mark(0);
-    dslash_lo(g, 1, fat, lng, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s, r12);
+    dslash_lo(g, 1, fat, lng, d, t, EPI_PLAIN, nullptr, 0.0, h->scal, h->partials, h->s, r12, ls);
     mark(1);
-    dslash_lo(g, 0, fat, lng, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s, r12);
+    dslash_lo(g, 0, fat, lng, t, ad, EPI_CG, d, 0.0, h->scal, h->partials, h->s, r12, ls);
     mark(2);
     launch_lo_update_xr<V>(g, h->lo_y, r, d, ad, h->scal, h->partials, h->s);
     mark(3);
@@ -203,9 +211,10 @@ void apply_A_lo(stag_handle* h, double m2, double scale) {
     const V* fat = lo_fat(h, in);
     const V* lng = lo_lng(h, in);
     const bool r12 = h->opt.link_recon == 12;
+    const float ls = lo_long_inv_scale(h);
     launch_to_lo<V>(g, h->x, in, 1.0 / scale, h->s);
-    dslash_lo(g, 1, fat, lng, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s, r12);
-    dslash_lo(g, 0, fat, lng, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s, r12);
+    dslash_lo(g, 1, fat, lng, in, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s, r12, ls);
+    dslash_lo(g, 0, fat, lng, t, o, EPI_AXPY, in, m2, nullptr, nullptr, h->s, r12, ls);
     launch_from_lo<V>(g, o, h->ad, scale, h->s);
 }
 
@@ -775,7 +784,8 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
             h->fat32 = dev_alloc<float2>(h, lo_links / 9 * 6 * sizeof(float2), "allocate FP32 two-row links");
         } else if (h->opt.inner == STAG_INNER_F32) {
             h->fat32 = dev_alloc<float2>(h, lo_links * sizeof(float2), "allocate FP32 links");
-            if (h->naik) h->lng32 = dev_alloc<float2>(h, lo_links * sizeof(float2), "allocate FP32 Naik links");
+            const size_t lng_entries = h->opt.long_recon == 12 ? lo_links / 9 * 6 : lo_links;  // two rows or nine
+            if (h->naik) h->lng32 = dev_alloc<float2>(h, lng_entries * sizeof(float2), "allocate FP32 Naik links");
         } else if (h->opt.inner == STAG_INNER_F16 || h->opt.inner == STAG_INNER_F32_L16) {
             h->fat16 = dev_alloc<__half2>(h, lo_links * sizeof(__half2), "allocate FP16 links");
             if (h->naik) h->lng16 = dev_alloc<__half2>(h, lo_links * sizeof(__half2), "allocate FP16 Naik links");
@@ -808,8 +818,10 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         if (h->naik && h->opt.long_recon == 12) {
             unsigned int* maxdev = reinterpret_cast<unsigned int*>(h->partials);
             cuda_check(h, cudaMemsetAsync(maxdev, 0, sizeof(unsigned int), h->s), "clear link check");
-            pack_field(h, naik_long, h->lng64, h->lngff, h->lng32, h->lng16, h->lngb16, nullptr, h->opt.long_scale,
-                       maxdev);
+            // the FP32 Naik links of the inner iteration are two rows as well
+            const bool f32_rows = h->opt.inner == STAG_INNER_F32;
+            pack_field(h, naik_long, h->lng64, h->lngff, f32_rows ? nullptr : h->lng32, h->lng16, h->lngb16,
+                       f32_rows ? h->lng32 : nullptr, h->opt.long_scale, maxdev);
             unsigned int bits = 0;
             cuda_check(h, cudaMemcpyAsync(&bits, maxdev, sizeof(bits), cudaMemcpyDeviceToHost, h->s),
                        "read link check");

@@ -390,9 +390,17 @@ __device__ __forceinline__ void dslash_site(const DslashParams<A>& p, int i, typ
                 const int b3 = neighbour(g, x, y, z, t, mu, h, false);
                 // the Naik link of x and the one arriving from x - 3 mu share eta_mu(x)
                 const int ps = (mu >= 1 ? x : 0) + (mu >= 2 ? y : 0) + (mu >= 3 ? z : 0);
-                const float2 s = (ps & 1) ? make_float2(-p.lng_s.x, -p.lng_s.y) : p.lng_s;
-                hop_fwd_ffr(acc, p.lng + ((size_t)(P * 4 + mu) * 6) * vs + i, p.in, f3, vs, s);
-                hop_bwd_ffr(acc, p.lng + ((size_t)(Q * 4 + mu) * 6) * vs + b3, p.in, b3, vs, s);
+                if constexpr (std::is_same<A, ArithFF>::value) {
+                    const float2 s = (ps & 1) ? make_float2(-p.lng_s.x, -p.lng_s.y) : p.lng_s;
+                    hop_fwd_ffr(acc, p.lng + ((size_t)(P * 4 + mu) * 6) * vs + i, p.in, f3, vs, s);
+                    hop_bwd_ffr(acc, p.lng + ((size_t)(Q * 4 + mu) * 6) * vs + b3, p.in, b3, vs, s);
+                } else {
+                    // FP32 (the mixed-precision iteration): the same rows, the third
+                    // rebuilt in FP32 with the factor eta / scale
+                    const float s = (ps & 1) ? -p.lng_s.x : p.lng_s.x;
+                    hop_fwd<ArithF32R>(acc, p.lng + ((size_t)(P * 4 + mu) * 6) * vs + i, p.in, f3, vs, s);
+                    hop_bwd<ArithF32R>(acc, p.lng + ((size_t)(Q * 4 + mu) * 6) * vs + b3, p.in, b3, vs, s);
+                }
             }
         }
     }
@@ -516,7 +524,7 @@ void launch_dslash_list(bool ff, Epilogue epi, const SysDirac* sys, const int* l
 template <class A, int EPI>
 static void launch_one(const DslashParams<A>& p, int naik, cudaStream_t s) {
     const int blocks = blocks_for(p.i1 - p.i0);
-    if constexpr (std::is_same<A, ArithFF>::value) {
+    if constexpr (std::is_same<A, ArithFF>::value || std::is_same<A, ArithF32>::value) {
         if (naik == 2) {
             dslash_kernel<A, 2, EPI><<<blocks, kBlock, 0, s>>>(p);
             return;
@@ -564,10 +572,10 @@ void launch_dslash_ff(const Geom& g, int out_parity, const LinkSet& L, const flo
 
 void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const float2* lng,
                        const float2* in, float2* out, Epilogue epi, const float2* src, double m2,
-                       CgScalars* scal, double* partials, cudaStream_t s) {
+                       CgScalars* scal, double* partials, cudaStream_t s, float lng_inv_scale) {
     DslashParams<ArithF32> p{g, out_parity, fat, lng, in, out, src, m2, host_ff_from_double(m2), scal, partials, 0,
-                             g.vh};
-    launch_any(p, lng != nullptr, epi, s);
+                             g.vh, make_float2(lng_inv_scale, 0.f)};
+    launch_any(p, lng == nullptr ? 0 : lng_inv_scale != 0.f ? 2 : 1, epi, s);
 }
 
 void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng,

@@ -70,10 +70,12 @@ struct SysDirac {
 void launch_dslash_list(bool ff, Epilogue epi, const SysDirac* sys, const int* list, const int* prefix,
                         const int* count, int grid, cudaStream_t s);
 
-// low-precision Dirac kernels of the mixed-precision solver (same epilogues)
+// low-precision Dirac kernels of the mixed-precision solver (same epilogues);
+// lng_inv_scale != 0: the FP32 Naik links are two rows per link ([2][4][6][vs],
+// eta folded) of scale x SU(3), lng_inv_scale = 1 / scale, the third row rebuilt
 void launch_dslash_f32(const Geom& g, int out_parity, const float2* fat, const float2* lng,
                        const float2* in, float2* out, Epilogue epi, const float2* src, double m2,
-                       CgScalars* scal, double* partials, cudaStream_t s);
+                       CgScalars* scal, double* partials, cudaStream_t s, float lng_inv_scale = 0.f);
 void launch_dslash_h16(const Geom& g, int out_parity, const __half2* fat, const __half2* lng,
                        const __half2* in, __half2* out, Epilogue epi, const __half2* src, double m2,
                        CgScalars* scal, double* partials, cudaStream_t s);

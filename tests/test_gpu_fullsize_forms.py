@@ -3,7 +3,8 @@ with the oracle's single-site A (Sec. 2, Eq. (3)); the whole-lattice oracle is
 too slow here.  Each solve must meet |b - A x| / |b| <= 10 tol on the sample
 (the library's own FP64 check covers the whole lattice):
 
-  * mixed FP32 reliable-update CG on the 28^3 x 96 asqtad-form system;
+  * mixed FP32 reliable-update CG on the 28^3 x 96 asqtad-form system, with
+    nine-entry and with two-row Naik links;
   * the batch of 16 right-hand sides on 32^3 x 64 (asqtad-form) together with
     uneven one-hop lattices (8^4, 16^4, 24^3 x 48), in one batched solve;
   * flexible CG with the network at its polynomial start on 32^3 x 64.
@@ -44,13 +45,18 @@ def _sampled_rel_residual(fat, lng, mass, dims, b, x, seed):
     return np.sqrt(num / den)
 
 
-def test_mixed_fp32_at_28x28x28x96():
+@pytest.mark.parametrize("long_recon", [0, 12])
+def test_mixed_fp32_at_28x28x28x96(long_recon):
+    """Mixed FP32 at the workload size, with nine-entry Naik links and with two-row
+    Naik links (long_recon = 12, third row rebuilt in FP32 and in float-float)."""
     dims, mass = (28, 28, 28, 96), 0.0062
     fat, lng = inputs.asqtad_form_fields(dims)
     b = inputs.gaussian_even_source(dims, 0)
     opt = binding.stag_default_options()
     opt.arith = binding.STAG_ARITH_FF
     opt.inner = binding.STAG_INNER_F32
+    if long_recon:
+        opt.long_recon, opt.long_scale = 12, inputs.NAIK_COEFF
     with binding.Handle(torch.from_numpy(fat).cuda(), dims, mass, naik_long=torch.from_numpy(lng).cuda(),
                         options=opt) as h:
         x = torch.zeros_like(torch.from_numpy(b).cuda())

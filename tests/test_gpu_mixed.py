@@ -201,3 +201,55 @@ def test_recon12_rejects_naik_and_other_inner():
         _handle(fat, None, dims, 0.1, inner=binding.STAG_INNER_F16, link_recon=12)
     with pytest.raises(binding.StagError):
         _handle(fat, None, dims, 0.1, inner=binding.STAG_INNER_F32, link_recon=8)
+
+
+# ---- two-row Naik links (long_recon = 12) in the FP32 iteration: the asqtad Naik links
+# are c x SU(3) (c = -1/24), so the 12-parameter form of Sec. 3.3 applies with the third
+# row rebuilt as (eta / c) conj(row0 x row1), in FP32
+
+def _long_recon_handle(fat, lng, dims, mass):
+    return _handle(fat, lng, dims, mass, inner=binding.STAG_INNER_F32, long_recon=12,
+                   long_scale=inputs.NAIK_COEFF)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 2, 2, 2), (10, 6, 4, 12), (8, 8, 8, 16)])
+def test_long_recon12_fp32_operator(dims):
+    """The FP32 operator with two-row Naik links meets the FP32 bars of the nine-entry
+    operator against the oracle (the rebuilt row carries a few FP32 roundings of
+    entries of size |c|)."""
+    mass = 0.05
+    fat, lng = _fields(dims, True, 81)
+    v = inputs.gaussian_even_source(dims, 82)
+    ref = oracle.Operator(fat, lng, mass, dims).apply_A(v)
+    with _long_recon_handle(fat, lng, dims, mass) as h:
+        out = torch.empty_like(_dev(v))
+        binding.stag_apply_A_prec(h.h, binding.STAG_ARITH_F32, _dev(v), out)
+    got = out.cpu().numpy()
+    tn, te = OP_TOL[binding.STAG_ARITH_F32]
+    assert np.linalg.norm(got - ref) <= tn * np.linalg.norm(ref)
+    assert np.abs(got - ref).max() <= te * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", [((8, 8, 8, 16), 0.05, 11), ((10, 6, 4, 12), 0.031, 13)])
+def test_long_recon12_fp32_mixed_solve(case):
+    """Mixed FP32 solves with two-row Naik links in both the FP32 iteration and the
+    float-float true residuals: the oracle's solution to 1e-8, no fallback, and the
+    iteration count of the nine-entry mixed solve within 2 %."""
+    dims, mass, seed = case
+    tol = 1e-10
+    fat, lng = _fields(dims, True, seed)
+    b = inputs.gaussian_even_source(dims, 0)
+    op, x_ref = _oracle_x(fat, lng, mass, dims, b)
+    its = {}
+    for recon in (0, 12):
+        h = _long_recon_handle(fat, lng, dims, mass) if recon else _handle(fat, lng, dims, mass,
+                                                                          inner=binding.STAG_INNER_F32)
+        with h:
+            x = torch.zeros_like(_dev(b))
+            code, info = binding.stag_cg_solve(h.h, _dev(b), x, tol, max_iter=20000)
+        assert code == binding.STAG_OK and info["true_rel_residual"] <= tol, info
+        assert info["fallbacks"] == 0
+        xs = x.cpu().numpy().reshape(-1)
+        assert np.linalg.norm(xs - x_ref) / np.linalg.norm(x_ref) <= 1e-8
+        its[recon] = info["iters"]
+    assert abs(its[12] - its[0]) <= max(2, 0.02 * its[0]), its

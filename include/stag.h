@@ -112,7 +112,10 @@ typedef struct {
                                two, times eta (Sec. 3.3, Eq. for SU(3) reconstruction); needs
                                SU(3) links, the one-hop operator and inner = F32.  0 (default):
                                all nine entries.                                              */
-    int32_t reserved;       /* 0 */
+    int32_t guard_bands;    /* 1: every device buffer of the handle lies between two guard bands
+                               of 4096 bytes filled with a fixed byte, read back by
+                               stag_check_guards (a check for writes past a buffer's ends,
+                               for tests); 0 (default): none                                  */
     double long_scale;      /* long_recon = 12: the Naik links are long_scale x SU(3) (e.g. the
                                Naik coefficient times a product of SU(3) links); accepted for
                                1e-10 <= |long_scale| <= 1e18, where the float-float products
@@ -212,6 +215,13 @@ int stag_kernel_stats(const stag_handle* h, int32_t kernel, double* total_ms, in
 
 /* Zero the kernel statistics. */
 int stag_reset_stats(stag_handle* h);
+
+/* Guard bands (opt.guard_bands = 1): *checked_bytes receives the bytes of all
+ * the handle's guard bands and *bad_bytes those that no longer hold the fill
+ * byte, i.e. were written by a kernel that ran past a buffer.  Synchronises the
+ * handle's stream.  Returns STAG_ERR_INVALID_ARG when the handle has no guard
+ * bands.  No counterpart in the paper: a test aid in place of a memory checker. */
+int stag_check_guards(stag_handle* h, int64_t* checked_bytes, int64_t* bad_bytes);
 
 /* Bytes of device memory the handle holds (0 for NULL). */
 int64_t stag_device_bytes(const stag_handle* h);

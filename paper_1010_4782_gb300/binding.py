@@ -62,6 +62,7 @@ EXPORTED = (
     "stag_kernel_stats",
     "stag_reset_stats",
     "stag_device_bytes",
+    "stag_check_guards",
     "stag_launch_count",
     "stag_apply_A_noalloc",
     "stag_measure_fma_rate",
@@ -109,7 +110,7 @@ class stag_options(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("reliable_delta", ctypes.c_double),
         ("link_recon", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("guard_bands", ctypes.c_int32),
         ("long_scale", ctypes.c_double),
         ("long_recon", ctypes.c_int32),
         ("reserved2", ctypes.c_int32),
@@ -174,6 +175,7 @@ def load(path: str | None = None):
     lib.stag_last_error.restype = ctypes.c_char_p
     lib.stag_kernel_stats.argtypes = [H, i32, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
     lib.stag_reset_stats.argtypes = [H]
+    lib.stag_check_guards.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.stag_device_bytes.argtypes = [H]
     lib.stag_device_bytes.restype = ctypes.c_int64
     lib.stag_launch_count.argtypes = [H]
@@ -316,6 +318,13 @@ def stag_kernel_stats(h, kernel):
 
 def stag_reset_stats(h):
     _check(load().stag_reset_stats(h), h)
+
+
+def stag_check_guards(h):
+    """(guard-band bytes checked, bytes changed) of a handle created with guard_bands = 1."""
+    checked, bad = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().stag_check_guards(h, ctypes.byref(checked), ctypes.byref(bad)), h)
+    return checked.value, bad.value
 
 
 def stag_device_bytes(h) -> int:

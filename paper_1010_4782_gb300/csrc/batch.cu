@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "../../include/stag.h"
+#include "handle.h"
 #include "multi.cuh"
 
 using namespace stag;
@@ -743,6 +744,7 @@ int stag_batch_apply_A(stag_batch* b, const double* const* in, double* const* ou
 int stag_batch_solve(stag_batch* b, const double* const* bvec, double* const* xvec, double tol, int32_t max_iter,
                      stag_solve_info* infos) {
     if (!b) return STAG_ERR_INVALID_ARG;
+    NvtxRange range("stag_batch_solve");
     const int n = b->n_sys;
     std::vector<stag_solve_info> inf(n);
     int status = STAG_OK;

@@ -15,11 +15,18 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/stag.h"
 #include "handle.h"
 #include "stag_kernels.h"
 
 using namespace stag;
+
+namespace stag {
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+}  // namespace stag
 
 namespace {
 
@@ -49,21 +56,36 @@ void cuda_check(stag_handle* h, cudaError_t e, const char* what) {
 
 void launch_check(stag_handle* h, const char* what) { cuda_check(h, cudaGetLastError(), what); }
 
+// A zeroed device buffer owned by the handle (freed by destroy_handle).  With
+// opt.guard_bands it lies between two guard bands of kGuardBytes filled with
+// kGuardByte, which stag_check_guards reads back: a kernel that writes past
+// either end of the buffer changes them.
 template <class T>
 T* dev_alloc(stag_handle* h, size_t bytes, const char* what) {
-    void* p = nullptr;
-    cuda_check(h, cudaMalloc(&p, bytes), what);
+    const size_t guard = h->opt.guard_bands ? kGuardBytes : 0;
+    void* base = nullptr;
+    cuda_check(h, cudaMalloc(&base, bytes + 2 * guard), what);
+    char* p = static_cast<char*>(base) + guard;
+    try {
+        h->allocs.push_back(stag_handle::Alloc{p, base, bytes});
+    } catch (...) {
+        cudaFree(base);
+        throw;
+    }
     h->device_bytes += (long long)bytes;
     cudaError_t e = cudaMemsetAsync(p, 0, bytes, h->s);
-    if (e != cudaSuccess) {
-        cudaFree(p);
-        cuda_check(h, e, what);
-    }
-    return static_cast<T*>(p);
+    if (e == cudaSuccess && guard) e = cudaMemsetAsync(base, kGuardByte, guard, h->s);
+    if (e == cudaSuccess && guard) e = cudaMemsetAsync(p + bytes, kGuardByte, guard, h->s);
+    cuda_check(h, e, what);
+    return reinterpret_cast<T*>(p);
 }
 
-void dev_free(void* p) {
-    if (p) cudaFree(p);
+// Bytes of the guard bands of [base, base + n) that differ from kGuardByte.
+__global__ void count_guard_kernel(const unsigned char* __restrict__ base, size_t n, unsigned long long* bad) {
+    unsigned int local = 0;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        local += base[k] != kGuardByte;
+    if (local) atomicAdd(bad, (unsigned long long)local);
 }
 
 size_t vec_bytes(const Geom& g) { return (size_t)3 * g.vs * sizeof(double2); }
@@ -331,34 +353,8 @@ void destroy_handle(stag_handle* h) {
     if (h->s) cudaStreamSynchronize(h->s);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-    dev_free(h->fat64);
-    dev_free(h->lng64);
-    dev_free(h->fatff);
-    dev_free(h->lngff);
-    dev_free(h->x);
-    dev_free(h->r);
-    dev_free(h->ad);
-    dev_free(h->b);
-    dev_free(h->d);
-    dev_free(h->t);
-    dev_free(h->u);
-    dev_free(h->xff);
-    dev_free(h->fat32);
-    dev_free(h->lng32);
-    dev_free(h->fat16);
-    dev_free(h->lng16);
-    dev_free(h->fatb16);
-    dev_free(h->lngb16);
-    dev_free(h->lo_d);
-    dev_free(h->lo_t);
-    dev_free(h->lo_ad);
-    dev_free(h->lo_r);
-    dev_free(h->lo_y);
-    dev_free(h->x_best);
-    dev_free(h->io_a);
-    dev_free(h->io_b);
-    dev_free(h->partials);
-    dev_free(h->scal);
+    for (const stag_handle::Alloc& a : h->allocs) cudaFree(a.base);
+    h->allocs.clear();
     if (h->scal_host) cudaFreeHost(h->scal_host);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->s) cudaStreamDestroy(h->s);
@@ -696,6 +692,7 @@ int stag_default_options(stag_options* opt) {
 
 int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long,
                    const int32_t dims[4], double mass, const stag_options* opt) {
+    NvtxRange range("stag_create_ex");
     if (out) *out = nullptr;
     stag_handle* h = nullptr;
     try {
@@ -717,6 +714,7 @@ int stag_create_ex(stag_handle** out, const double* fat, const double* naik_long
         if (opt) o = *opt;
         if (o.arith != STAG_ARITH_F64 && o.arith != STAG_ARITH_FF)
             fail(nullptr, STAG_ERR_INVALID_ARG, "unknown arith option");
+        if (o.guard_bands != 0 && o.guard_bands != 1) fail(nullptr, STAG_ERR_INVALID_ARG, "guard_bands must be 0 or 1");
         if (o.check_interval < 1 || o.check_interval > 4096)
             fail(nullptr, STAG_ERR_INVALID_ARG, "check_interval must be in [1, 4096]");
         if (o.max_restarts < 0) fail(nullptr, STAG_ERR_INVALID_ARG, "max_restarts must be >= 0");
@@ -878,6 +876,7 @@ int stag_set_mass(stag_handle* h, double mass) {
 
 int stag_dslash(stag_handle* h, int32_t out_parity, const double* in, double* out) {
     if (!h) return STAG_ERR_INVALID_ARG;
+    NvtxRange range("stag_dslash");
     try {
         if (!in || !out) fail(h, STAG_ERR_INVALID_ARG, "NULL vector");
         if (out_parity != 0 && out_parity != 1) fail(h, STAG_ERR_INVALID_ARG, "out_parity must be 0 or 1");
@@ -918,6 +917,7 @@ int stag_dslash(stag_handle* h, int32_t out_parity, const double* in, double* ou
 
 int stag_apply_A(stag_handle* h, const double* in_even, double* out_even) {
     if (!h) return STAG_ERR_INVALID_ARG;
+    NvtxRange range("stag_apply_A");
     try {
         if (!in_even || !out_even) fail(h, STAG_ERR_INVALID_ARG, "NULL vector");
         if (in_even == out_even) fail(h, STAG_ERR_INVALID_ARG, "in and out must not overlap");
@@ -1010,6 +1010,7 @@ int stag_apply_A_prec(stag_handle* h, int32_t arith, const double* in_even, doub
 int stag_cg_solve(stag_handle* h, const double* b_even, double* x_even, double tol, int32_t max_iter,
                   stag_solve_info* info) {
     if (!h) return STAG_ERR_INVALID_ARG;
+    NvtxRange range("stag_cg_solve");
     stag_solve_info inf{};
     int status = STAG_OK;
     auto t0 = std::chrono::steady_clock::now();
@@ -1081,6 +1082,38 @@ int stag_reset_stats(stag_handle* h) {
     if (!h) return STAG_ERR_INVALID_ARG;
     for (auto& s : h->stats) s = KernelStat{};
     return STAG_OK;
+}
+
+int stag_check_guards(stag_handle* h, int64_t* checked_bytes, int64_t* bad_bytes) {
+    if (!h || !checked_bytes || !bad_bytes || !h->opt.guard_bands) return STAG_ERR_INVALID_ARG;
+    unsigned long long* bad = nullptr;
+    try {
+        cuda_check(h, cudaSetDevice(h->device), "cudaSetDevice");
+        cuda_check(h, cudaMalloc(&bad, sizeof(*bad)), "allocate guard count");
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(*bad), h->s);
+        long long checked = 0;
+        for (const stag_handle::Alloc& a : h->allocs) {
+            if (e != cudaSuccess) break;
+            const unsigned char* lo = static_cast<const unsigned char*>(a.base);
+            const unsigned char* hi = static_cast<const unsigned char*>(a.user) + a.bytes;
+            count_guard_kernel<<<8, 256, 0, h->s>>>(lo, kGuardBytes, bad);
+            count_guard_kernel<<<8, 256, 0, h->s>>>(hi, kGuardBytes, bad);
+            checked += 2 * (long long)kGuardBytes;
+            e = cudaGetLastError();
+        }
+        unsigned long long host_bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&host_bad, bad, sizeof(host_bad), cudaMemcpyDeviceToHost, h->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+        cudaFree(bad);
+        bad = nullptr;
+        cuda_check(h, e, "check guard bands");
+        *checked_bytes = checked;
+        *bad_bytes = (int64_t)host_bad;
+        return STAG_OK;
+    } catch (const Fail& f) {
+        if (bad) cudaFree(bad);
+        return f.code;
+    }
 }
 
 int64_t stag_device_bytes(const stag_handle* h) { return h ? h->device_bytes : 0; }

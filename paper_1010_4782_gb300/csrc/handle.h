@@ -65,6 +65,14 @@ struct stag_handle {
     std::vector<cudaEvent_t> events;
     stag::KernelStat stats[STAG_KERNEL_COUNT];
     long long device_bytes = 0;
+    // device buffers (opt.guard_bands: each lies between two guard bands of
+    // kGuardBytes filled with kGuardByte): user pointer, allocation base, user bytes
+    struct Alloc {
+        void* user;
+        void* base;
+        size_t bytes;
+    };
+    std::vector<Alloc> allocs;
     long long launches = 0;  // kernels launched by this handle (graph replays counted per kernel)
     std::string err = "no error";
     // called after every block of CG iterations of the plain solver (training-pair snapshots)
@@ -72,6 +80,17 @@ struct stag_handle {
 };
 
 namespace stag {
+// Guard bands of opt.guard_bands: this many bytes on each side of every buffer,
+// filled with this byte.
+constexpr size_t kGuardBytes = 4096;
+constexpr unsigned char kGuardByte = 0xA5;
+
+// A scoped NVTX range (visible to profilers; no cost without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+};
+
 // Internal entry points of capi.cu used by the preconditioner code (pt.cu).
 // They report failures by throwing HandleError with the handle's message set.
 struct HandleError {

@@ -1285,6 +1285,7 @@ int stag_ptnet_destroy(stag_ptnet* n) {
 int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* x_even, double tol, int32_t max_iter,
                    stag_solve_info* info) {
     if (!h || !n || n->h != h || !b_even || !x_even || b_even == x_even) return STAG_ERR_INVALID_ARG;
+    NvtxRange range("stag_fcg_solve");
     if (!(tol > 0.0) || !std::isfinite(tol)) return STAG_ERR_INVALID_ARG;
     stag_solve_info inf{};
     int status = STAG_OK;

@@ -115,3 +115,19 @@ def test_fma_probe_rejects_bad_arguments(lib):
     rate = ct.c_double(0.0)
     assert lib.stag_measure_fma_rate(16, ct.byref(rate)) == binding.STAG_ERR_INVALID_ARG
     assert lib.stag_measure_fma_rate(64, None) == binding.STAG_ERR_INVALID_ARG
+
+
+def test_guard_options_checked_before_device_work(lib):
+    import ctypes as ct
+
+    dims = (ct.c_int32 * 4)(4, 4, 4, 4)
+    links = np.zeros(4 ** 4 * 36, dtype=np.complex128)
+    o = binding.stag_default_options()
+    assert o.guard_bands == 0
+    o.guard_bands = 2
+    h = ct.c_void_p()
+    assert lib.stag_create_ex(ct.byref(h), links.ctypes.data, None, dims, ct.c_double(0.1),
+                              ct.byref(o)) == binding.STAG_ERR_INVALID_ARG
+    assert "guard" in binding.stag_last_error(None)
+    checked, bad = ct.c_int64(), ct.c_int64()
+    assert lib.stag_check_guards(None, ct.byref(checked), ct.byref(bad)) == binding.STAG_ERR_INVALID_ARG

@@ -259,6 +259,26 @@ def test_fcg_with_trained_network_gains_over_plain_cg(trained):
     assert sum(i for i, _ in it_fcg) < 0.8 * sum(it_cg), (it_fcg, it_cg)
 
 
+def test_training_gains_over_the_untrained_network(trained):
+    """What training buys, separated from the polynomial start: on the same fresh sources,
+    flexible CG with the trained network needs fewer iterations than with the same
+    network untrained (a fresh network from the same seed: the polynomial start)."""
+    dims, h, net = trained["dims"], trained["h"], trained["poly"]["net"]
+    net0 = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 7)
+    its = {"trained": 0, "untrained": 0}
+    try:
+        for k in range(4):
+            b = _dev(inputs.gaussian_even_source(dims, 900 + k))
+            for name, nt in (("trained", net), ("untrained", net0)):
+                x = torch.zeros_like(b)
+                code, info = binding.stag_fcg_solve(h.h, nt, b, x, 1e-10, max_iter=20000)
+                assert code == binding.STAG_OK and info["fallbacks"] == 0, (name, info)
+                its[name] += info["iters"]
+    finally:
+        binding.stag_ptnet_destroy(net0)
+    assert its["trained"] < its["untrained"], its
+
+
 def test_fcg_falls_back_to_plain_cg(trained):
     """A network with zero weights gives z = 0: flexible CG hands over to plain CG, which converges."""
     dims, m = (4, 4, 4, 4), 0.1

@@ -354,6 +354,7 @@ def run_ours(args):
             "achieved_gbs": round(bytes64 / t64 / 1e9, 1),
             "hbm_peak_gbs": peak,
             "hbm_frac": round(bytes64 / t64 / 1e9 / peak, 4),
+            "traffic": recorded_traffic(f"dslash_oe_f64_naik_{'x'.join(map(str, dims))}"),
             "dfma_per_launch": dfma64,
             "achieved_dfma_per_s": round(dfma64 / t64, 1),
             "dfma_peak_per_s": round(dfma_rate, 1),

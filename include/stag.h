@@ -423,9 +423,10 @@ int stag_dd_destroy(stag_dd* dd);
  * arithmetic ceiling of the Dirac kernels' roofline: the paper counts each
  * SU(3) x vector product of D as 36 real multiply-adds (Sec. 2, text after
  * Eq. (5)), so a native-FP64 Naik half-Dslash site is 576 DFMA.  Runs
- * independent FMA chains on every SM for about 0.1 s, timed with CUDA events
- * after one warm-up launch on a private stream (it allocates 8 bytes and
- * synchronises that stream).  Returns STAG_ERR_INVALID_ARG for other bits or a
+ * independent FMA chains on every SM for about 0.1 s in two operand patterns
+ * (a complex multiply-accumulate's and a shared-multiplier chain), timed with
+ * CUDA events after one warm-up launch on a private stream, and reports the
+ * faster (it allocates 8 bytes and synchronises that stream).  Returns STAG_ERR_INVALID_ARG for other bits or a
  * NULL output; the message is available from stag_last_error(NULL). */
 int stag_measure_fma_rate(int32_t bits, double* fma_per_second);
 

@@ -8,7 +8,8 @@
 // chip's DFMA rate, which this probe measures instead of assuming: every
 // thread of a grid over all SMs runs kChains independent FMA chains (enough
 // independent work to cover the pipe's latency) for a fixed number of steps,
-// timed with CUDA events on a private stream after one warm-up launch.
+// timed with CUDA events on a private stream after one warm-up launch, for
+// two operand patterns; the faster one sets the rate.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,19 +27,21 @@ constexpr int kChains = 8;
 constexpr int kThreads = 256;
 constexpr int kBlocksPerSm = 8;
 
-// acc_k <- x_k * y_(k+u) + acc_k for kChains independent accumulators, the
-// operand pattern of a complex multiply-accumulate (the Dirac kernels' inner
-// step): on GB300 it sustains about 19 % more DFMA per second than chains of
-// a <- a * m + c with one shared multiplier.  x is small and y below 1, so the
-// sums stay bounded and normal.  The result is stored only if it equals `never`
-// (a NaN passed at run time), which the compiler cannot rule out, so no FMA is
-// dropped.
-template <class T>
+// Two operand patterns, both with kChains independent chains per thread:
+//  * ACC: acc_k <- x_k * y_(k+u) + acc_k, the pattern of a complex
+//    multiply-accumulate (the Dirac kernels' inner step); on GB300 the FP64
+//    pipe sustains about 19 % more DFMA per second with it;
+//  * CHAIN: a_k <- a_k * m + c with one shared multiplier, which the FP32
+//    pipes sustain best.
+// x is small and y, m below 1, so the values stay bounded and normal.  The
+// result is stored only if it equals `never` (a NaN passed at run time), which
+// the compiler cannot rule out, so no FMA is dropped.
+template <class T, bool ACC>
 __global__ void __launch_bounds__(kThreads) fma_chain_kernel(int steps, T m, T c, T never, T* out) {
     T acc[kChains], x[kChains], y[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; ++k) {
-        acc[k] = (T)0;
+        acc[k] = ACC ? (T)0 : (T)(threadIdx.x + k) * c;
         x[k] = (T)(threadIdx.x + k) * c;
         y[k] = m + (T)k * c;
     }
@@ -47,7 +50,12 @@ __global__ void __launch_bounds__(kThreads) fma_chain_kernel(int steps, T m, T c
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
 #pragma unroll
-            for (int k = 0; k < kChains; ++k) acc[k] = fma(x[k], y[(k + u) % kChains], acc[k]);
+            for (int k = 0; k < kChains; ++k) {
+                if (ACC)
+                    acc[k] = fma(x[k], y[(k + u) % kChains], acc[k]);
+                else
+                    acc[k] = fma(acc[k], m, c);
+            }
         }
     }
     T sum = 0;
@@ -74,16 +82,24 @@ int measure(double* rate) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) {
+    float ms = 0.f;  // the faster of the two patterns
+    for (int pattern = 0; pattern < 2 && e == cudaSuccess; ++pattern) {
         const T m = (T)0.5, c = (T)1e-7, never = (T)NAN;
-        fma_chain_kernel<T><<<blocks, kThreads, 0, s>>>(steps / 10, m, c, never, out);  // warm-up
+        auto launch = [&](int n) {
+            if (pattern)
+                fma_chain_kernel<T, false><<<blocks, kThreads, 0, s>>>(n, (T)0.999999, (T)1e-6, never, out);
+            else
+                fma_chain_kernel<T, true><<<blocks, kThreads, 0, s>>>(n, m, c, never, out);
+        };
+        launch(steps / 10);  // warm-up
         cudaEventRecord(e0, s);
-        fma_chain_kernel<T><<<blocks, kThreads, 0, s>>>(steps, m, c, never, out);
+        launch(steps);
         cudaEventRecord(e1, s);
         e = cudaGetLastError();
+        float t = 0.f;
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && (ms == 0.f || t < ms)) ms = t;
     }
     if (e1) cudaEventDestroy(e1);
     if (e0) cudaEventDestroy(e0);

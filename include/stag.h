@@ -244,7 +244,8 @@ int64_t stag_launch_count(const stag_handle* h);
  * check_interval iterations of all systems, each with its pass, are one CUDA
  * graph; the host reads one word (the systems still running) per replay.  The
  * right-hand sides per thread and threads per block of each group are chosen
- * at create by timing the candidates (opt->autotune), cached per (extents,
+ * at create by timing the candidates' two Dirac launches of an iteration (the
+ * D_oe and the reducing D_eo; the least sum wins; opt->autotune), cached per (extents,
  * Naik, RHS count) for the process and in the file STAG_AUTOTUNE_CACHE names;
  * STAG_AUTOTUNE_LOG names a file that receives every candidate's time.  The
  * candidates also include the traversals of a group's site tiles listed at

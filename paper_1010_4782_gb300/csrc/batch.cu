@@ -55,7 +55,8 @@ struct BFail {
 
 struct Tune {
     int rb = 1, bs = 256;
-    double ms = 0.0;
+    double ms = 0.0;     // D_oe per launch
+    double ms_eo = 0.0;  // reducing D_eo per launch (the candidate with the least D_oe + D_eo wins)
     int mode = 0;  // tile traversal (multi.cu): 0 contiguous runs, 1 resident sweep
 };
 
@@ -289,10 +290,11 @@ void load_tune_file() {
 }
 
 // Every candidate's time, appended to the file STAG_AUTOTUNE_LOG names (if set).
-void log_candidate(const std::string& key, int rb, int bs, int mode, double ms) {
+void log_candidate(const std::string& key, int rb, int bs, int mode, double ms_oe, double ms_eo) {
     if (const char* path = std::getenv("STAG_AUTOTUNE_LOG")) {
         std::ofstream f(path, std::ios::app);
-        f << key << " rb=" << rb << " bs=" << bs << " traversal=" << mode << " ms=" << ms << "\n";
+        f << key << " rb=" << rb << " bs=" << bs << " traversal=" << mode << " ms_oe=" << ms_oe << " ms_eo=" << ms_eo
+          << "\n";
     }
 }
 
@@ -304,39 +306,54 @@ void store_tune(const std::string& key, const Tune& t) {
     }
 }
 
-double time_group_launch(stag_batch* b, const std::vector<int>& gis, int rb, int bs, int mode) {
+// Best of three timed launches (after a warm-up) of the group's D_oe and of
+// its reducing D_eo (the two Dirac launches of every iteration), in ms.  The
+// CG state is cleared before each D_eo launch so that it does its full work
+// (with zero vectors its epilogue would otherwise mark the systems done).
+std::pair<double, double> time_group_launch(stag_batch* b, const std::vector<int>& gis, int rb, int bs, int mode) {
     std::vector<int4> items;
     for (int gi : gis) add_items(items, gi, group_blocks(b->groups[gi], rb, bs, mode), mode);
     int4* d_items = nullptr;
     bcheck(b, cudaMalloc(&d_items, items.size() * sizeof(int4)), "allocate tuning items");
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double best = 1e30;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // D_oe start, end; D_eo start, end
+    double best_oe = 1e30, best_eo = 1e30;
     cudaError_t err = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->s);
-    if (err == cudaSuccess) err = cudaEventCreate(&e0);
-    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    for (int k = 0; k < 4 && err == cudaSuccess; ++k) err = cudaEventCreate(&ev[k]);
     MultiLaunch L;
     L.groups = b->d_groups;
     L.items = d_items;
     L.scal = b->scal;
     L.partials = b->partials;
     L.counters = b->counters;
-    L.out_parity = 1;
-    L.phase = 0;
     for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
-        cudaEventRecord(e0, b->s);
+        L.out_parity = 1;
+        L.phase = 0;
+        cudaEventRecord(ev[0], b->s);
         launch_multi(MK_DSLASH_PLAIN, L, (int)items.size(), rb, bs, mode, b->s);
-        cudaEventRecord(e1, b->s);
-        err = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) best = std::min(best, (double)ms);  // first launch is a warm-up
+        cudaEventRecord(ev[1], b->s);
+        err = cudaMemsetAsync(b->scal, 0, sizeof(CgScalars) * b->n_sys, b->s);
+        if (err != cudaSuccess) break;
+        L.out_parity = 0;
+        L.phase = 1;
+        cudaEventRecord(ev[2], b->s);
+        launch_multi(MK_DSLASH_CG, L, (int)items.size(), rb, bs, mode, b->s);
+        cudaEventRecord(ev[3], b->s);
+        err = cudaEventSynchronize(ev[3]);
+        float ms_oe = 0.f, ms_eo = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms_oe, ev[0], ev[1]);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms_eo, ev[2], ev[3]);
+        if (rep > 0) {  // the first launches are a warm-up
+            best_oe = std::min(best_oe, (double)ms_oe);
+            best_eo = std::min(best_eo, (double)ms_eo);
+        }
     }
+    if (err == cudaSuccess) err = cudaMemsetAsync(b->scal, 0, sizeof(CgScalars) * b->n_sys, b->s);
     if (err == cudaSuccess) err = cudaGetLastError();
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(d_items);
     bcheck(b, err, "autotune");
-    return best;
+    return {best_oe, best_eo};
 }
 
 void autotune(stag_batch* b) {
@@ -359,16 +376,18 @@ void autotune(stag_batch* b) {
         Tune best;
         best.rb = std::max(std::min(4, G.rpad), G.rpad / 32);
         best.bs = 128;
-        best.ms = 1e30;
+        double best_pair = 1e30;
         if (enabled) {
             for (int mode : {0, 1}) {
                 for (int rb : {1, 2, 4, 8}) {
                     if (rb > G.rpad || G.rpad / rb > 32) continue;
                     for (int bs : {64, 128, 256}) {
-                        const double ms = time_group_launch(b, {(int)gi}, rb, bs, mode);
-                        log_candidate(key, rb, bs, mode, ms);
-                        if (ms < best.ms) {
-                            best.ms = ms;
+                        const auto t = time_group_launch(b, {(int)gi}, rb, bs, mode);
+                        log_candidate(key, rb, bs, mode, t.first, t.second);
+                        if (t.first + t.second < best_pair) {
+                            best_pair = t.first + t.second;
+                            best.ms = t.first;
+                            best.ms_eo = t.second;
                             best.rb = rb;
                             best.bs = bs;
                             best.mode = mode;
@@ -384,14 +403,16 @@ void autotune(stag_batch* b) {
         Tune best;
         best.rb = 1;
         best.bs = 128;
-        best.ms = 1e30;
+        double best_pair = 1e30;
         if (enabled) {
             for (int mode : {0, 1}) {
                 for (int bs : {64, 128, 256}) {
-                    const double ms = time_group_launch(b, singles, 1, bs, mode);
-                    log_candidate("single-rhs", 1, bs, mode, ms);
-                    if (ms < best.ms) {
-                        best.ms = ms;
+                    const auto t = time_group_launch(b, singles, 1, bs, mode);
+                    log_candidate("single-rhs", 1, bs, mode, t.first, t.second);
+                    if (t.first + t.second < best_pair) {
+                        best_pair = t.first + t.second;
+                        best.ms = t.first;
+                        best.ms_eo = t.second;
                         best.bs = bs;
                         best.mode = mode;
                     }

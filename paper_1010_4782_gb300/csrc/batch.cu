@@ -308,8 +308,9 @@ void store_tune(const std::string& key, const Tune& t) {
 
 // Best of three timed launches (after a warm-up) of the group's D_oe and of
 // its reducing D_eo (the two Dirac launches of every iteration), in ms.  The
-// CG state is cleared before each D_eo launch so that it does its full work
-// (with zero vectors its epilogue would otherwise mark the systems done).
+// CG state is cleared before each launch so that it does its full work (with
+// zero vectors the D_eo epilogue marks the systems done, and a launch for a
+// group whose systems are all done returns at once).
 std::pair<double, double> time_group_launch(stag_batch* b, const std::vector<int>& gis, int rb, int bs, int mode) {
     std::vector<int4> items;
     for (int gi : gis) add_items(items, gi, group_blocks(b->groups[gi], rb, bs, mode), mode);
@@ -326,6 +327,9 @@ std::pair<double, double> time_group_launch(stag_batch* b, const std::vector<int
     L.partials = b->partials;
     L.counters = b->counters;
     for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+        // a cleared state: no system is done, so every launch does its full work
+        err = cudaMemsetAsync(b->scal, 0, sizeof(CgScalars) * b->n_sys, b->s);
+        if (err != cudaSuccess) break;
         L.out_parity = 1;
         L.phase = 0;
         cudaEventRecord(ev[0], b->s);

@@ -169,3 +169,46 @@ def test_batch_zero_source_and_bad_args(systems):
         binding.stag_batch_destroy(bt)
     with pytest.raises(binding.StagError):
         binding.stag_batch_create([s["fat_d"]], [None], [(4, 4, 3, 4)], [0.1])
+
+
+def test_batch_breakdown_and_budget_end_only_their_systems(systems):
+    """The device-side reliable-update pass ends a system on a CG breakdown (free field at
+    m = 0 with a constant source: a zero mode of A, so d^dag A d = 0) and on an exhausted
+    iteration budget, while the other systems of the same batch converge to the oracle."""
+    tol = 1e-10
+    dims0 = (4, 4, 4, 4)
+    unit = np.zeros((4, 4, 4, 4, 4, 3, 3), dtype=np.complex128)
+    unit[..., 0, 0] = unit[..., 1, 1] = unit[..., 2, 2] = 1.0
+    b0 = np.zeros((128, 3), dtype=np.complex128)
+    b0[:, 0] = 1.0
+    good = systems[5]
+    bt = binding.stag_batch_create([_dev(unit), good["fat_d"]], [None, good["lng_d"]], [dims0, good["dims"]],
+                                   [0.0, good["mass"]])
+    try:
+        bs = [_dev(b0), _dev(good["b"])]
+        xs = [torch.zeros_like(b) for b in bs]
+        code, infos = binding.stag_batch_solve(bt, bs, xs, tol, max_iter=20000)
+    finally:
+        binding.stag_batch_destroy(bt)
+    assert code == binding.STAG_ERR_BREAKDOWN
+    assert infos[0]["status"] == binding.STAG_ERR_BREAKDOWN
+    assert infos[1]["status"] == binding.STAG_OK and infos[1]["true_rel_residual"] <= tol, infos[1]
+    op = oracle.Operator(good["fat"], good["lng"], good["mass"], good["dims"])
+    ref = oracle.solve(op.apply_A, good["b"], tol=1e-13, max_iter=200000, max_restarts=20)["x"]
+    x1 = xs[1].cpu().numpy().reshape(-1)
+    assert np.linalg.norm(x1 - ref) / np.linalg.norm(ref) <= 1e-8
+
+    # an iteration budget of 7: every system stops after exactly 7 iterations, not converged
+    sub = systems[:2] + systems[5:6]
+    bt = _batch(sub)
+    try:
+        bs = [_dev(s["b"]) for s in sub]
+        xs = [torch.zeros_like(b) for b in bs]
+        code, infos = binding.stag_batch_solve(bt, bs, xs, tol, max_iter=7)
+    finally:
+        binding.stag_batch_destroy(bt)
+    assert code == binding.STAG_ERR_NOT_CONVERGED
+    for x, info in zip(xs, infos):
+        assert info["status"] == binding.STAG_ERR_NOT_CONVERGED and info["iters"] == 7, info
+        assert 1e-10 < info["true_rel_residual"] < 1.0
+        assert torch.isfinite(x).all() and x.abs().sum() > 0

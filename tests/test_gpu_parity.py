@@ -160,9 +160,10 @@ def test_config1_solve(arith):
     assert np.linalg.norm(xs - x_ref) / np.linalg.norm(x_ref) <= 1e-8
     # iteration count of the oracle's own Fig. 1 at the same tolerance: within 2 in
     # FP64; float-float rounding (2^-48) shifts the loss of orthogonality of this
-    # ill-conditioned 384-dimensional system by a few steps (5 % allowed)
+    # ill-conditioned 384-dimensional system by a few steps (measured on GB300: 289
+    # against the oracle's 283, 2.1 %; 3 % allowed)
     ref = oracle.solve(op.apply_A, b, tol=tol, max_iter=100000)
-    slack = 2 if arith == binding.STAG_ARITH_F64 else max(2, int(0.05 * ref["iters"]))
+    slack = 2 if arith == binding.STAG_ARITH_F64 else max(2, int(0.03 * ref["iters"]))
     assert abs(info["iters"] - ref["iters"]) <= slack
 
 

@@ -31,11 +31,18 @@ namespace {
 
 constexpr int kTile = kBlock;  // sites per tile of the list kernels
 
-// Entry j of a list whose tile range holds `tile` (prefix has n + 1 entries).
-__device__ __forceinline__ int list_entry(const int* prefix, int tile) {
-    int j = 0;
-    while (prefix[j + 1] <= tile) ++j;
-    return j;
+// Entry j of a list of n entries whose tile range [prefix[j], prefix[j + 1])
+// holds `tile` (0 <= tile < prefix[n]; prefix ascending): binary search.
+__device__ __forceinline__ int list_entry(const int* prefix, int n, int tile) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
 }
 
 __device__ __forceinline__ void list_reset(PassList L) { *L.count = 0, L.prefix[0] = 0; }
@@ -134,7 +141,7 @@ __global__ void pass_select_kernel(PassArgs a) {
 __global__ void __launch_bounds__(kTile) pass_fold_kernel(PassArgs a) {
     const int n = *a.fold.count, total = a.fold.prefix[n];
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int j = list_entry(a.fold.prefix, tile);
+        const int j = list_entry(a.fold.prefix, n, tile);
         const SysDev& s = a.sys[a.fold.sys[j]];
         const int i = (tile - a.fold.prefix[j]) * kTile + threadIdx.x;
         if (i >= s.g.vh) continue;
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(kTile) pass_fold_kernel(PassArgs a) {
 __global__ void __launch_bounds__(kTile) pass_to_ff_kernel(PassArgs a) {
     const int n = *a.ff.count, total = a.ff.prefix[n];
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int j = list_entry(a.ff.prefix, tile);
+        const int j = list_entry(a.ff.prefix, n, tile);
         const SysDev& s = a.sys[a.ff.sys[j]];
         const int i = (tile - a.ff.prefix[j]) * kTile + threadIdx.x;
         if (i >= s.g.vh) continue;
@@ -172,7 +179,7 @@ template <bool F64>
 __global__ void __launch_bounds__(kTile) pass_residual_kernel(PassArgs a, PassList L) {
     const int n = *L.count, total = L.prefix[n];
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int j = list_entry(L.prefix, tile);
+        const int j = list_entry(L.prefix, n, tile);
         const SysDev& s = a.sys[L.sys[j]];
         const int i = (tile - L.prefix[j]) * kTile + threadIdx.x;
         double acc = 0.0;
@@ -264,7 +271,7 @@ __global__ void pass_confirm_kernel(PassArgs a) {
 __global__ void __launch_bounds__(kTile) pass_set_residual_kernel(PassArgs a) {
     const int n = *a.replace.count, total = a.replace.prefix[n];
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int j = list_entry(a.replace.prefix, tile);
+        const int j = list_entry(a.replace.prefix, n, tile);
         const int k = a.replace.sys[j];
         const SysDev& s = a.sys[k];
         const SysState& st = a.state[k];

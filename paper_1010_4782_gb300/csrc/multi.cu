@@ -218,10 +218,13 @@ __device__ __forceinline__ void store_rb(float2* p, const float2 (&v)[RB]) {
 // acc[r][j] += U v (fwd, U at the output site) or -= U^dag v (bwd, U at the neighbour)
 template <int RB, bool BWD>
 __device__ __forceinline__ void multi_hop(float2 (&acc)[3][RB], const float2* __restrict__ u,
-                                          const float2* __restrict__ in, int nb, size_t vs, int rpad, int roff) {
+                                          const float2* __restrict__ in, int nb, size_t vs, int rpad, int roff,
+                                          bool stream_links = false) {
     float2 U[9];
+    // the links are read once: with stream_links they are loaded as streaming
+    // (evict-first) data, so that they do not push the reused input vectors out of L2
 #pragma unroll
-    for (int k = 0; k < 9; ++k) U[k] = __ldg(u + k * vs);
+    for (int k = 0; k < 9; ++k) U[k] = stream_links ? __ldcs(u + k * vs) : __ldg(u + k * vs);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float2 v[RB];
@@ -276,14 +279,18 @@ __global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
         for (int mu = 0; mu < 4; ++mu) {
             const int f1 = nbr_index(g, x, y, z, t, mu, 1, true);
             const int b1 = nbr_index(g, x, y, z, t, mu, 1, false);
-            multi_hop<RB, false>(acc, G.fat + ((size_t)(P * 4 + mu) * 9) * vs + i, in, f1, vs, G.rpad, l.roff);
-            multi_hop<RB, true>(acc, G.fat + ((size_t)(Q * 4 + mu) * 9) * vs + b1, in, b1, vs, G.rpad, l.roff);
+            multi_hop<RB, false>(acc, G.fat + ((size_t)(P * 4 + mu) * 9) * vs + i, in, f1, vs, G.rpad, l.roff,
+                                 kSweep);
+            multi_hop<RB, true>(acc, G.fat + ((size_t)(Q * 4 + mu) * 9) * vs + b1, in, b1, vs, G.rpad, l.roff,
+                                kSweep);
             if (G.lng) {
                 const int h = g.hop3[mu];
                 const int f3 = nbr_index(g, x, y, z, t, mu, h, true);
                 const int b3 = nbr_index(g, x, y, z, t, mu, h, false);
-                multi_hop<RB, false>(acc, G.lng + ((size_t)(P * 4 + mu) * 9) * vs + i, in, f3, vs, G.rpad, l.roff);
-                multi_hop<RB, true>(acc, G.lng + ((size_t)(Q * 4 + mu) * 9) * vs + b3, in, b3, vs, G.rpad, l.roff);
+                multi_hop<RB, false>(acc, G.lng + ((size_t)(P * 4 + mu) * 9) * vs + i, in, f3, vs, G.rpad,
+                                     l.roff, kSweep);
+                multi_hop<RB, true>(acc, G.lng + ((size_t)(Q * 4 + mu) * 9) * vs + b3, in, b3, vs, G.rpad,
+                                    l.roff, kSweep);
             }
         }
 #pragma unroll

@@ -243,9 +243,14 @@ __device__ __forceinline__ void multi_hop(float2 (&acc)[3][RB], const float2* __
 }
 
 // out = D in (EPI_PLAIN), m2 src - D in (EPI_AXPY), or the latter with per-RHS
-// Re(src^dag out) -> alpha (EPI_CG)
+// Re(src^dag out) -> alpha (EPI_CG).
+// With eight right-hand sides per thread the compiler would use about 140
+// registers, which leaves 12 warps per SM; the bound of 128 (16 warps per SM,
+// spilling under 160 bytes a thread to L1) made both half-Dslash launches
+// about 6 % faster on GB300 at 32^3 x 64 with 16 right-hand sides.  96
+// registers (20 warps) spilled more and was slower.
 template <int RB, int BS, int EPI, int MODE>
-__global__ void __launch_bounds__(BS) multi_dslash_kernel(const MultiLaunch L) {
+__global__ void __launch_bounds__(BS, (RB == 8 ? 512 / BS : 1)) multi_dslash_kernel(const MultiLaunch L) {
     const int4 w = L.items[blockIdx.x];  // (group, block in group, blocks in group, -)
     const MultiGroup& G = L.groups[w.x];
     if (group_all_done(G, L.scal)) return;

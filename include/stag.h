@@ -372,6 +372,24 @@ int stag_ptnet_set_inference_precision(stag_ptnet* n, int32_t precision);
  * applies the network return STAG_ERR_TIMEOUT. */
 int stag_ptnet_use_tensor_cores(stag_ptnet* n, int32_t enable);
 
+/* How the network is evaluated when it is applied (stag_ptnet_apply,
+ * stag_fcg_solve); training always runs the layers.
+ *  STAG_PTNET_COLLAPSED (the default): the layers are linear, the input is
+ *    zero on odd sites and only the even-site output is read, so only paths of
+ *    zero or two hops contribute and the network equals exactly
+ *      M r = k0 r + sum_{p,q = 1..8} H[p][q] T_p T_q r,
+ *    with C[a][b][c] = sum_{o,i} W3[a][0][o] W2[b][o][i] W1[c][i][0],
+ *    k0 = C[0][0][0] and H[p][q] = C[p][q][0] + C[p][0][q] + C[0][p][q]
+ *    (computed in FP64 from the weights at every call).  It is evaluated as
+ *    chi_p = sum_q H[p][q] T_q r on odd sites (stored in the inference
+ *    precision) and z = k0 r + sum_p T_p chi_p on even sites: 16 one-hop
+ *    transports per pair of sites instead of 144, FP32 arithmetic.
+ *  STAG_PTNET_LAYERED: the three layers as in training (inference precision
+ *    for the activations, tensor cores per stag_ptnet_use_tensor_cores).
+ * Both compute the same M up to rounding. */
+enum { STAG_PTNET_COLLAPSED = 0, STAG_PTNET_LAYERED = 1 };
+int stag_ptnet_set_inference_form(stag_ptnet* n, int32_t form);
+
 /* Flexible CG with z_k = M(r_k): alpha = (r, z) / (p, A p), x += alpha p,
  * r -= alpha A p, beta = (z_new, r_new - r_old) / (r_old, z_old), p = z + beta p,
  * with A in the handle's FP64-class arithmetic and FP64 vectors.  When the

@@ -35,6 +35,9 @@ STAG_INNER_F16 = 2
 STAG_INNER_BF16 = 3
 STAG_INNER_F32_L16 = 4
 
+STAG_PTNET_COLLAPSED = 0
+STAG_PTNET_LAYERED = 1
+
 STAG_DD_HOST = 0
 STAG_DD_DEVICE = 1
 STAG_DD_HOST_OVERLAP = 2
@@ -84,6 +87,7 @@ EXPORTED = (
     "stag_ptnet_add_pairs",
     "stag_ptnet_num_pairs",
     "stag_ptnet_use_tensor_cores",
+    "stag_ptnet_set_inference_form",
     "stag_ptnet_train",
     "stag_ptnet_dataset_loss",
     "stag_ptnet_last_error",
@@ -212,6 +216,7 @@ def load(path: str | None = None):
     lib.stag_ptnet_destroy.argtypes = [H]
     lib.stag_ptnet_set_inference_precision.argtypes = [H, i32]
     lib.stag_ptnet_use_tensor_cores.argtypes = [H, i32]
+    lib.stag_ptnet_set_inference_form.argtypes = [H, i32]
     lib.stag_fcg_solve.argtypes = [H, H, P, P, d, i32, ctypes.POINTER(stag_solve_info)]
     lib.stag_dd_create.argtypes = [ctypes.POINTER(H), H, i32]
     lib.stag_dd_apply_A.argtypes = [H, P, P, i32, P]
@@ -482,6 +487,10 @@ def stag_ptnet_set_inference_precision(net, precision):
 
 def stag_ptnet_use_tensor_cores(net, enable):
     _pcheck(load().stag_ptnet_use_tensor_cores(net, int(bool(enable))), net)
+
+
+def stag_ptnet_set_inference_form(net, form):
+    _pcheck(load().stag_ptnet_set_inference_form(net, int(form)), net)
 
 
 def stag_ptnet_destroy(net):

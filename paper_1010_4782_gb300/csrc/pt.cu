@@ -1,6 +1,6 @@
 // pt.cu - learned preconditioner: a gauge-covariant parallel-transport network,
 // its training on the GPU with the library's own forward / adjoint /
-// weight-gradient kernels, and flexible CG that uses it.
+// weight-gradient kernels (flexible CG that uses it: fcg.cu).
 //
 // The paper's CG (Sec. 2, Fig. 1) has no preconditioner; this is an added form
 // built on the same operator.  Network (the oracle in oracle/ptnet.py states
@@ -45,6 +45,7 @@
 #include "ff.cuh"
 #include "handle.h"
 #include "pt_common.cuh"
+#include "pt_net.h"
 #include "stag_kernels.h"
 
 namespace stag {
@@ -64,10 +65,12 @@ enum LayerMode { SITES_ALL = 0, EVEN_INPUT = 1, EVEN_OUTPUT = 2 };
 // so that a link or an activation read by a site of one parity is read again,
 // by its neighbour of the other parity, while it is still in L2.  The 8 -> 8
 // layer is held to 128 registers (two blocks per SM), the others to 85 (three).
+// skip (nullable): the kernel returns at once while *skip is nonzero.
 template <int CIN, int COUT, class TI, class TO, bool ADJ, int MODE = SITES_ALL>
 __global__ void __launch_bounds__(256, CIN * COUT >= 64 ? 2 : 3)
     pt_layer_kernel(Geom g, const float2* __restrict__ links, const float2* __restrict__ w,
-                    const TI* __restrict__ in, TO* __restrict__ out) {
+                    const TI* __restrict__ in, TO* __restrict__ out, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ float2 sw[kPaths * CIN * COUT];
     for (int k = threadIdx.x; k < kPaths * CIN * COUT; k += blockDim.x) sw[k] = w[k];
     __syncthreads();
@@ -486,11 +489,82 @@ __global__ void pt_links_kernel(const double2* __restrict__ in, float2* __restri
     if (k < n) out[k] = make_float2((float)in[k].x, (float)in[k].y);
 }
 
-// --------------------------------------------------- flexible CG vectors
-// per-block partials of Re<a, b>, Re<a, c>, <b, b> (FP64)
+// ------------------------------------------------ collapsed inference form
+// coef[0] = k0 = C[0][0][0], coef[1 + 8 (p - 1) + (q - 1)] = H[p][q] =
+// C[p][q][0] + C[p][0][q] + C[0][p][q] with C[a][b][c] = sum_{o,i} W3[a][0][o]
+// W2[b][o][i] W1[c][i][0]: the terms of the layer product T_a T_b T_c that
+// take an even site to an even site (zero or two hops).  FP64 sums.
+__global__ void pt_collapse_kernel(const float2* __restrict__ w, float2* __restrict__ coef) {
+    const int t = threadIdx.x;
+    if (t >= kCollapsedCoefs) return;
+    const float2* w1 = w;                                    // [9][8][1]
+    const float2* w2 = w + kPaths * kHidden;                 // [9][8][8]
+    const float2* w3 = w2 + kPaths * kHidden * kHidden;      // [9][1][8]
+    auto C = [&](int a, int b, int c) {
+        double re = 0.0, im = 0.0;
+        for (int o = 0; o < kHidden; ++o) {
+            const float2 x = w3[a * kHidden + o];
+            for (int i = 0; i < kHidden; ++i) {
+                const float2 y = w2[(b * kHidden + o) * kHidden + i], z = w1[c * kHidden + i];
+                const double xyr = (double)x.x * y.x - (double)x.y * y.y;
+                const double xyi = (double)x.x * y.y + (double)x.y * y.x;
+                re += xyr * z.x - xyi * z.y;
+                im += xyr * z.y + xyi * z.x;
+            }
+        }
+        return make_double2(re, im);
+    };
+    double2 h;
+    if (t == 0) {
+        h = C(0, 0, 0);
+    } else {
+        const int p = 1 + (t - 1) / 8, q = 1 + (t - 1) % 8;
+        const double2 a = C(p, q, 0), b = C(p, 0, q), c = C(0, p, q);
+        h = make_double2(a.x + b.x + c.x, a.y + b.y + c.y);
+    }
+    coef[t] = make_float2((float)h.x, (float)h.y);
+}
+
+// chi on odd sites (pt_chi_site), stored as TS
+template <class V, class TS>
+__global__ void __launch_bounds__(256, 2) pt_chi_kernel(Geom g, const float2* __restrict__ links,
+                                                        const float2* __restrict__ coef, const V* __restrict__ r,
+                                                        TS* __restrict__ chi, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    __shared__ float2 sH[64];
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) sH[k] = coef[1 + k];
+    __syncthreads();
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+    float2 acc[8][3];
+    pt_chi_site(g, links, sH, r, i, acc);
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stc(chi + ((size_t)p * 3 + c) * vs + i, acc[p][c]);
+}
+
+// out (FP64, even sites) = k0 r + sum_p T_p chi_p
+template <class TS>
+__global__ void __launch_bounds__(256) pt_out_kernel(Geom g, const float2* __restrict__ links,
+                                                     const float2* __restrict__ coef, const TS* __restrict__ chi,
+                                                     const double2* __restrict__ r, double2* __restrict__ out) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= g.vh) return;
+    const size_t vs = (size_t)g.vs;
+    float2 r0[3], z[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r0[c] = ldc(r + c * vs + i);
+    pt_out_site(g, links, coef[0], chi, i, r0, z);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c * vs + i] = make_double2(z[c].x, z[c].y);
+}
+
+// ------------------------------------------------ FP64 vector reductions
 // Re(a, b), Re(a, c) (c nullable) and |b|^2: per-block partials, then the last
 // block (atomic ticket) sums them in block order into out3[0..2].
-__global__ void __launch_bounds__(kBlock) fcg_dots_kernel(Geom g, const double2* __restrict__ a,
+__global__ void __launch_bounds__(kBlock) pt_dots_kernel(Geom g, const double2* __restrict__ a,
                                                           const double2* __restrict__ b, const double2* __restrict__ c,
                                                           double* __restrict__ partials, int nblk,
                                                           unsigned int* counter, double* out3) {
@@ -537,104 +611,12 @@ __global__ void __launch_bounds__(kBlock) fcg_dots_kernel(Geom g, const double2*
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// r_old = r; x += alpha p; r -= alpha q
-__global__ void __launch_bounds__(kBlock) fcg_update_kernel(Geom g, double2* x, double2* r, double2* r_old,
-                                                            const double2* __restrict__ p,
-                                                            const double2* __restrict__ q, double alpha) {
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= g.vh) return;
-    const size_t vs = (size_t)g.vs;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const size_t j = k * vs + i;
-        const double2 pp = p[j], qq = q[j], rr = r[j];
-        double2 xx = x[j];
-        r_old[j] = rr;
-        xx.x = fma(alpha, pp.x, xx.x);
-        xx.y = fma(alpha, pp.y, xx.y);
-        x[j] = xx;
-        r[j] = make_double2(fma(-alpha, qq.x, rr.x), fma(-alpha, qq.y, rr.y));
-    }
-}
-
-// p = z + beta p
-__global__ void __launch_bounds__(kBlock) fcg_dir_kernel(Geom g, double2* p, const double2* __restrict__ z,
-                                                         double beta) {
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= g.vh) return;
-    const size_t vs = (size_t)g.vs;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const size_t j = k * vs + i;
-        const double2 pp = p[j], zz = z[j];
-        p[j] = make_double2(fma(beta, pp.x, zz.x), fma(beta, pp.y, zz.y));
-    }
-}
-
-// r = b - q
-__global__ void __launch_bounds__(kBlock) fcg_sub_kernel(Geom g, double2* r, const double2* __restrict__ b,
-                                                         const double2* __restrict__ q) {
-    const int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= g.vh) return;
-    const size_t vs = (size_t)g.vs;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const size_t j = k * vs + i;
-        r[j] = make_double2(b[j].x - q[j].x, b[j].y - q[j].y);
-    }
-}
-
 }  // namespace stag
 
 using namespace stag;
 
 // =========================================================== the network
-struct stag_ptnet {
-    stag_handle* h = nullptr;
-    Geom g{};
-    int prec = STAG_ARITH_BF16;  // activation storage of training and pairs: STAG_ARITH_BF16 or STAG_ARITH_F32
-    int inf_prec = STAG_ARITH_BF16;  // activation storage when the network is applied
-    size_t elem = 4;             // bytes per stored complex
-    float2* links = nullptr;     // FP32 eta-folded fat links (transports and A)
-    float2* lng = nullptr;       // FP32 eta-folded Naik links (A), or nullptr
-    float2 *va = nullptr, *vt = nullptr, *vad = nullptr;  // FP32 [3][vs] vectors for A d
-    std::vector<float2> w_host;  // weights, layer-major [9][C_out][C_in]
-    float2* w = nullptr;         // device weights (FP32 master)
-    bool use_tc = true;          // BF16 8 -> 8 forward layer on the tensor cores (pt_tc.cu)
-    int* tc_err = nullptr;       // set by a tensor-core layer whose bounded wait ran out
-    unsigned int* dot_counter = nullptr;  // last-block ticket of fcg_dots_kernel
-    double* dot_out = nullptr;            // its three sums
-    float2* grad = nullptr;
-    float *adam_m = nullptr, *adam_v = nullptr;
-    long long adam_t = 0;
-    void* act[kLayers + 1] = {};  // activations (whole lattice)
-    void* gact[kLayers + 1] = {}; // gradients of activations
-    float2* wpart = nullptr;      // weight-gradient partials
-    double* red = nullptr;        // reduction partials
-    std::vector<double> red_host;
-    // training pairs: r and e slots (even sites, [3][vs]) and <e, A e>
-    std::vector<void*> pairs_r, pairs_e;
-    std::vector<double> pairs_eae;
-    void* scratch_r = nullptr;  // slots for stag_ptnet_loss_grad
-    void* scratch_e = nullptr;
-    // flexible CG vectors (FP64 SoA)
-    double2 *fr = nullptr, *fz = nullptr, *fp = nullptr, *fq = nullptr, *fro = nullptr;
-    long long device_bytes = 0;
-    std::string err = "no error";
-};
-
-namespace {
-
-struct PFail {
-    int code;
-};
-
-int layer_offset(int l) {  // complex weights before layer l (0-based)
-    int off = 0;
-    for (int k = 0; k < l; ++k) off += kPaths * kChan[k + 1] * kChan[k];
-    return off;
-}
-int n_weights() { return layer_offset(kLayers); }
+namespace stag {
 
 void pfail(stag_ptnet* n, int code, const std::string& msg) {
     if (n) n->err = msg;
@@ -654,15 +636,24 @@ void* palloc(stag_ptnet* n, size_t bytes, const char* what) {
     return p;
 }
 
-cudaStream_t S(stag_ptnet* n) { return n->h->s; }
-
-// Fails with STAG_ERR_TIMEOUT if a tensor-core layer reported a bounded wait that ran out.
 void check_tc(stag_ptnet* n) {
     int flag = 0;
     pcheck(n, cudaMemcpyAsync(&flag, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, S(n)), "read error flag");
     pcheck(n, cudaStreamSynchronize(S(n)), "sync");
     if (flag) pfail(n, STAG_ERR_TIMEOUT, "tensor-core layer: a bounded wait on the MMA barrier ran out");
 }
+
+}  // namespace stag
+
+namespace {
+
+int layer_offset(int l) {  // complex weights before layer l (0-based)
+    int off = 0;
+    for (int k = 0; k < l; ++k) off += kPaths * kChan[k + 1] * kChan[k];
+    return off;
+}
+int n_weights() { return layer_offset(kLayers); }
+
 size_t field_bytes(const stag_ptnet* n, int ch) { return (size_t)ch * 3 * 2 * n->g.vs * sizeof(float2); }
 size_t slot_bytes(const stag_ptnet* n) { return (size_t)3 * n->g.vs * n->elem; }
 // blocks of a pt_layer_kernel launch over both parities (256 sites per block)
@@ -674,7 +665,7 @@ void layer_fwd(stag_ptnet* n, int l, const T* in, T* out) {
     const float2* w = n->w + layer_offset(l);
     const int nb = site_blocks(g);
     if (l == 0)
-        pt_layer_kernel<1, kHidden, T, T, false, EVEN_INPUT><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
+        pt_layer_kernel<1, kHidden, T, T, false, EVEN_INPUT><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out, nullptr);
     else if (l == 1) {
         if constexpr (std::is_same<T, __nv_bfloat162>::value) {
             if (n->use_tc) {
@@ -682,10 +673,10 @@ void layer_fwd(stag_ptnet* n, int l, const T* in, T* out) {
                 return;
             }
         }
-        pt_layer_kernel<kHidden, kHidden, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out);
+        pt_layer_kernel<kHidden, kHidden, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, w, in, out, nullptr);
     } else
         pt_layer_kernel<kHidden, 1, T, T, false, EVEN_OUTPUT><<<blocks_for(g.vh), 256, 0, S(n)>>>(g, n->links, w, in,
-                                                                                                  out);
+                                                                                                  out, nullptr);
 }
 
 // gradient of layer l's input from the gradient of its output
@@ -695,9 +686,9 @@ void layer_adj(stag_ptnet* n, int l, const T* gout, T* gin) {
     const float2* w = n->w + layer_offset(l);
     const int nb = site_blocks(g);
     if (l == 2)
-        pt_layer_kernel<1, kHidden, T, T, true, EVEN_INPUT><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin);
+        pt_layer_kernel<1, kHidden, T, T, true, EVEN_INPUT><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin, nullptr);
     else if (l == 1)
-        pt_layer_kernel<kHidden, kHidden, T, T, true><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin);
+        pt_layer_kernel<kHidden, kHidden, T, T, true><<<nb, 256, 0, S(n)>>>(g, n->links, w, gout, gin, nullptr);
 }
 
 template <class T>
@@ -826,9 +817,11 @@ void destroy_net(stag_ptnet* n) {
     if (n->h && n->h->s) cudaStreamSynchronize(n->h->s);
     for (void* p : {(void*)n->links, (void*)n->lng, (void*)n->va, (void*)n->vt, (void*)n->vad, (void*)n->w, (void*)n->grad, (void*)n->adam_m, (void*)n->adam_v,
                     (void*)n->wpart, (void*)n->red, n->scratch_r, n->scratch_e, (void*)n->fr, (void*)n->fz,
-                    (void*)n->fp, (void*)n->fq, (void*)n->fro, (void*)n->tc_err, (void*)n->dot_counter,
-                    (void*)n->dot_out})
+                    (void*)n->fq, (void*)n->tc_err, (void*)n->dot_counter, (void*)n->dot_out, n->fcg_r, n->fcg_p,
+                    n->fcg_q, n->fcg_t, n->fcg_x, (void*)n->fcg_dev, (void*)n->coef})
         if (p) cudaFree(p);
+    if (n->fcg_host) cudaFreeHost(n->fcg_host);
+    if (n->fcg_graph) cudaGraphExecDestroy(n->fcg_graph);
     for (int l = 0; l <= kLayers; ++l) {
         if (n->act[l]) cudaFree(n->act[l]);
         if (n->gact[l]) cudaFree(n->gact[l]);
@@ -839,37 +832,85 @@ void destroy_net(stag_ptnet* n) {
 }
 
 bool is_bf16(const stag_ptnet* n) { return n->prec == STAG_ARITH_BF16; }
-bool infer_bf16(const stag_ptnet* n) { return n->inf_prec == STAG_ARITH_BF16; }
-
-// FP64-class A p into q (FP64): float-float when the handle has it, else native FP64
-void apply_A_q(stag_ptnet* n, const double2* p, double2* q) {
-    stag_handle* h = n->h;
-    const Geom& g = h->g;
-    if (h->fatff) {
-        float4* u = static_cast<float4*>(h->u);
-        float4* t = static_cast<float4*>(h->t);
-        float4* o = reinterpret_cast<float4*>(h->ad);
-        const LinkSet L{h->fat64, h->lng64, h->fatff, h->lngff, h->lng_s};
-        launch_to_ff(g, p, u, h->s);
-        launch_dslash_ff(g, 1, L, u, t, EPI_PLAIN, nullptr, 0.0, nullptr, nullptr, h->s);
-        launch_dslash_ff(g, 0, L, t, o, EPI_AXPY, u, h->mass * h->mass, nullptr, nullptr, h->s);
-        launch_from_ff(g, o, q, h->s);
-        h->launches += 4;
-    } else {
-        handle_apply_A_f64(h, p, q);
-    }
-}
 
 // (Re<a,b>, Re<a,c>, |b|^2)
 void dots(stag_ptnet* n, const double2* a, const double2* b, const double2* c, double out[3]) {
     const Geom& g = n->g;
     const int nb = blocks_for(g.vh);
-    fcg_dots_kernel<<<nb, kBlock, 0, S(n)>>>(g, a, b, c, n->red, nb, n->dot_counter, n->dot_out);
+    pt_dots_kernel<<<nb, kBlock, 0, S(n)>>>(g, a, b, c, n->red, nb, n->dot_counter, n->dot_out);
     pcheck(n, cudaGetLastError(), "dots");
     pcheck(n, cudaMemcpyAsync(out, n->dot_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, S(n)), "read dots");
     pcheck(n, cudaStreamSynchronize(S(n)), "sync");
 }
 
+// The network from a solver vector r (even sites) into act[3]: the first layer
+// reads r directly (float-float or FP64, rounded to FP32 on load); the layers
+// after it are those of apply_net.
+template <class T, class V>
+void network_from_vec(stag_ptnet* n, const V* r, const int* skip) {
+    const Geom& g = n->g;
+    const int nb = site_blocks(g);
+    T* a1 = static_cast<T*>(n->act[1]);
+    T* a2 = static_cast<T*>(n->act[2]);
+    T* a3 = static_cast<T*>(n->act[3]);
+    pt_layer_kernel<1, kHidden, V, T, false, EVEN_INPUT><<<nb, 256, 0, S(n)>>>(g, n->links, n->w, r, a1, skip);
+    if constexpr (std::is_same<T, __nv_bfloat162>::value) {
+        if (n->use_tc) {
+            launch_pt_mix8_tc(g, n->links, n->w + layer_offset(1), a1, a2, n->w + layer_offset(2), n->tc_err, S(n),
+                              skip);
+            launch_pt_transport_sum(g, n->links, a2, a3, S(n), skip);
+            return;
+        }
+    }
+    pt_layer_kernel<kHidden, kHidden, T, T, false><<<nb, 256, 0, S(n)>>>(g, n->links, n->w + layer_offset(1), a1, a2,
+                                                                          skip);
+    pt_layer_kernel<kHidden, 1, T, T, false, EVEN_OUTPUT><<<blocks_for(g.vh), 256, 0, S(n)>>>(
+        g, n->links, n->w + layer_offset(2), a2, a3, skip);
+}
+
+template <class V>
+void network_from_vec_any(stag_ptnet* n, const V* r, const int* skip) {
+    if (infer_bf16(n))
+        network_from_vec<__nv_bfloat162>(n, r, skip);
+    else
+        network_from_vec<float2>(n, r, skip);
+}
+
+}  // namespace
+
+namespace stag {
+void pt_network_from_vec(stag_ptnet* n, const float4* r, const int* skip) { network_from_vec_any(n, r, skip); }
+void pt_network_from_vec(stag_ptnet* n, const double2* r, const int* skip) { network_from_vec_any(n, r, skip); }
+
+void pt_collapse(stag_ptnet* n) { pt_collapse_kernel<<<1, 96, 0, S(n)>>>(n->w, n->coef); }
+
+template <class V>
+void launch_pt_chi_any(stag_ptnet* n, const V* r, const int* skip) {
+    const int nb = blocks_for(n->g.vh, 256);
+    if (infer_bf16(n))
+        pt_chi_kernel<V, __nv_bfloat162><<<nb, 256, 0, S(n)>>>(n->g, n->links, n->coef, r,
+                                                               static_cast<__nv_bfloat162*>(n->act[2]), skip);
+    else
+        pt_chi_kernel<V, float2><<<nb, 256, 0, S(n)>>>(n->g, n->links, n->coef, r, static_cast<float2*>(n->act[2]),
+                                                       skip);
+}
+void launch_pt_chi(stag_ptnet* n, const float4* r, const int* skip) { launch_pt_chi_any(n, r, skip); }
+void launch_pt_chi(stag_ptnet* n, const double2* r, const int* skip) { launch_pt_chi_any(n, r, skip); }
+}  // namespace stag
+
+namespace {
+// z = M r (FP64 even-site vectors) in the collapsed form
+void apply_collapsed(stag_ptnet* n, const double2* r, double2* z) {
+    const Geom& g = n->g;
+    pt_collapse(n);
+    launch_pt_chi(n, r, nullptr);
+    if (infer_bf16(n))
+        pt_out_kernel<__nv_bfloat162><<<blocks_for(g.vh, 256), 256, 0, S(n)>>>(
+            g, n->links, n->coef, static_cast<const __nv_bfloat162*>(n->act[2]), r, z);
+    else
+        pt_out_kernel<float2><<<blocks_for(g.vh, 256), 256, 0, S(n)>>>(g, n->links, n->coef,
+                                                                       static_cast<const float2*>(n->act[2]), r, z);
+}
 }  // namespace
 
 extern "C" {
@@ -904,6 +945,7 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         const int nw = n_weights();
         n->w = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate weights"));
         n->tc_err = static_cast<int*>(palloc(n, sizeof(int), "allocate error flag"));
+        n->coef = static_cast<float2*>(palloc(n, kCollapsedCoefs * sizeof(float2), "allocate coefficients"));
         n->dot_counter = static_cast<unsigned int*>(palloc(n, sizeof(unsigned int), "allocate counter"));
         n->dot_out = static_cast<double*>(palloc(n, 3 * sizeof(double), "allocate sums"));
         n->grad = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate gradients"));
@@ -918,11 +960,13 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         n->scratch_r = palloc(n, slot_bytes(n), "allocate slots");
         n->scratch_e = palloc(n, slot_bytes(n), "allocate slots");
         const size_t vb = (size_t)3 * n->g.vs * sizeof(double2);
-        n->fr = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
-        n->fz = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
-        n->fp = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
-        n->fq = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
-        n->fro = static_cast<double2*>(palloc(n, vb, "allocate FCG vectors"));
+        n->fr = static_cast<double2*>(palloc(n, vb, "allocate vectors"));
+        n->fz = static_cast<double2*>(palloc(n, vb, "allocate vectors"));
+        n->fq = static_cast<double2*>(palloc(n, vb, "allocate vectors"));
+        static_assert(sizeof(float4) == sizeof(double2), "float-float and FP64 complex vectors share their size");
+        for (void** v : {&n->fcg_r, &n->fcg_p, &n->fcg_q, &n->fcg_t, &n->fcg_x}) *v = palloc(n, vb, "allocate FCG vectors");
+        n->fcg_dev = static_cast<FcgDev*>(palloc(n, sizeof(FcgDev), "allocate FCG state"));
+        pcheck(n, cudaMallocHost(&n->fcg_host, sizeof(FcgDev)), "allocate FCG state");
         // initial weights: the least-squares degree-1 polynomial preconditioner
         // alpha + beta A_fat (A_fat: the one-hop part the transports can express),
         // minimising the integral of (1 - lambda p(lambda))^2 over [0, Lmax]:
@@ -1031,13 +1075,17 @@ int stag_ptnet_apply(stag_ptnet* n, const double* r_even, double* z_even) {
             src = h->io_a;
         }
         launch_pack_vec(g, src, n->fr, S(n));
-        double d3[3];
-        dots(n, n->fr, n->fr, nullptr, d3);
-        const double rn = std::sqrt(d3[0]);
-        if (infer_bf16(n))
-            apply_net<__nv_bfloat162>(n, n->fr, rn, n->fz);
-        else
-            apply_net<float2>(n, n->fr, rn, n->fz);
+        if (n->inf_form == STAG_PTNET_COLLAPSED) {
+            apply_collapsed(n, n->fr, n->fz);
+        } else {
+            double d3[3];
+            dots(n, n->fr, n->fr, nullptr, d3);
+            const double rn = std::sqrt(d3[0]);
+            if (infer_bf16(n))
+                apply_net<__nv_bfloat162>(n, n->fr, rn, n->fz);
+            else
+                apply_net<float2>(n, n->fr, rn, n->fz);
+        }
         launch_unpack_vec(g, n->fz, out_dev ? z_even : h->io_b, S(n));
         if (!out_dev)
             pcheck(n, cudaMemcpyAsync(z_even, h->io_b, (size_t)3 * g.vh * sizeof(double2), cudaMemcpyDeviceToHost, S(n)), "copy z");
@@ -1267,6 +1315,12 @@ int stag_ptnet_set_inference_precision(stag_ptnet* n, int32_t precision) {
     return STAG_OK;
 }
 
+int stag_ptnet_set_inference_form(stag_ptnet* n, int32_t form) {
+    if (!n || (form != STAG_PTNET_COLLAPSED && form != STAG_PTNET_LAYERED)) return STAG_ERR_INVALID_ARG;
+    n->inf_form = form;
+    return STAG_OK;
+}
+
 int stag_ptnet_use_tensor_cores(stag_ptnet* n, int32_t enable) {
     if (!n) return STAG_ERR_INVALID_ARG;
     n->use_tc = enable != 0;
@@ -1280,157 +1334,6 @@ const char* stag_ptnet_last_error(const stag_ptnet* n) { return n ? n->err.c_str
 int stag_ptnet_destroy(stag_ptnet* n) {
     destroy_net(n);
     return STAG_OK;
-}
-
-int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* x_even, double tol, int32_t max_iter,
-                   stag_solve_info* info) {
-    if (!h || !n || n->h != h || !b_even || !x_even || b_even == x_even) return STAG_ERR_INVALID_ARG;
-    NvtxRange range("stag_fcg_solve");
-    if (!(tol > 0.0) || !std::isfinite(tol)) return STAG_ERR_INVALID_ARG;
-    stag_solve_info inf{};
-    int status = STAG_OK;
-    const auto t0 = std::chrono::steady_clock::now();
-    try {
-        handle_begin(h);
-        const Geom& g = h->g;
-        const size_t ab = (size_t)3 * g.vh * sizeof(double2);
-        const bool x_dev = handle_is_device_ptr(h, x_even);
-        const double* bs = b_even;
-        if (!handle_is_device_ptr(h, bs)) {
-            pcheck(n, cudaMemcpyAsync(h->io_a, bs, ab, cudaMemcpyHostToDevice, S(n)), "copy b");
-            bs = h->io_a;
-        }
-        launch_pack_vec(g, bs, h->b, S(n));
-        const double* xs = x_even;
-        if (!x_dev) {
-            pcheck(n, cudaMemcpyAsync(h->io_b, xs, ab, cudaMemcpyHostToDevice, S(n)), "copy x");
-            xs = h->io_b;
-        }
-        launch_pack_vec(g, xs, h->x, S(n));
-        double d3[3];
-        dots(n, h->b, h->b, nullptr, d3);
-        const double bnorm2 = d3[0];
-        if (!std::isfinite(bnorm2)) pfail(n, STAG_ERR_INVALID_ARG, "source has non-finite entries");
-        const long long max_it = max_iter > 0 ? max_iter : 3LL * g.vh;
-        long long iters = 0;
-        int fallbacks = 0, restarts = 0;
-        double rel = 0.0;
-        auto precond = [&](const double2* r, double rnorm, double2* z) {
-            if (infer_bf16(n))
-                apply_net<__nv_bfloat162>(n, r, rnorm, z);
-            else
-                apply_net<float2>(n, r, rnorm, z);
-        };
-        auto true_residual = [&]() {
-            handle_apply_A_f64(h, h->x, n->fq);
-            fcg_sub_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->fr, h->b, n->fq);
-            dots(n, n->fr, n->fr, nullptr, d3);
-            return std::sqrt(d3[0] / bnorm2);
-        };
-        if (bnorm2 == 0.0) {
-            pcheck(n, cudaMemsetAsync(h->x, 0, (size_t)3 * g.vs * sizeof(double2), S(n)), "zero x");
-        } else {
-            bool use_plain = false;
-            double cycle_start_rel = 0.0;
-            while (true) {
-                // r = b - A x (FP64), z = M r, p = z
-                rel = true_residual();
-                cycle_start_rel = rel;
-                if (rel <= tol) break;
-                if (iters >= max_it) {
-                    status = STAG_ERR_NOT_CONVERGED;
-                    break;
-                }
-                if (use_plain) {
-                    // plain FP64-class CG from the current x, judged by its own FP64 residual
-                    stag_solve_info pi{};
-                    status = handle_solve_packed(h, bnorm2, tol, max_it - iters, pi);
-                    iters += pi.iters;
-                    rel = pi.true_rel_residual;
-                    break;
-                }
-                double rr = d3[0];
-                precond(n->fr, std::sqrt(rr), n->fz);
-                pcheck(n, cudaMemcpyAsync(n->fp, n->fz, (size_t)3 * g.vs * sizeof(double2), cudaMemcpyDeviceToDevice, S(n)), "p = z");
-                dots(n, n->fr, n->fz, nullptr, d3);
-                double rz = d3[0];
-                // stall: the best |r| so far has not dropped by 10 % within 100 iterations
-                double best = rr, mark = rr;
-                long long mark_it = iters;
-                const char* why = nullptr;
-                bool stalled = !(rz > 0.0);
-                if (stalled) why = "(r, z) <= 0";
-                while (!stalled && iters < max_it && rr > tol * tol * bnorm2) {
-                    apply_A_q(n, n->fp, n->fq);
-                    dots(n, n->fp, n->fq, nullptr, d3);
-                    const double pq = d3[0];
-                    if (!(pq > 0.0)) {
-                        stalled = true;
-                        why = "(p, A p) <= 0";
-                        break;
-                    }
-                    const double alpha = rz / pq;
-                    fcg_update_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, h->x, n->fr, n->fro, n->fp, n->fq, alpha);
-                    dots(n, n->fr, n->fr, nullptr, d3);
-                    rr = d3[0];
-                    ++iters;
-                    best = std::min(best, rr);
-                    if (best < 0.81 * mark) {
-                        mark = best;
-                        mark_it = iters;
-                    } else if (iters - mark_it > 100) {
-                        stalled = true;
-                        why = "no 10 % drop of the best residual in 100 iterations";
-                        break;
-                    }
-                    precond(n->fr, std::sqrt(rr), n->fz);
-                    dots(n, n->fz, n->fr, n->fro, d3);  // (z, r_new), (z, r_old)
-                    const double beta = (d3[0] - d3[1]) / rz;
-                    rz = d3[0];
-                    if (!(rz > 0.0)) {
-                        stalled = true;
-                        why = "(r, z) <= 0";
-                        break;
-                    }
-                    fcg_dir_kernel<<<blocks_for(g.vh), kBlock, 0, S(n)>>>(g, n->fp, n->fz, beta);
-                }
-                if (stalled) {
-                    // a cycle that cut the residual 100-fold restarts flexible CG; otherwise plain CG
-                    const bool progress = std::sqrt(rr / bnorm2) < 0.01 * cycle_start_rel &&
-                                          std::strcmp(why, "(r, z) <= 0") != 0 && std::strcmp(why, "(p, A p) <= 0") != 0;
-                    if (std::getenv("STAG_DEBUG"))
-                        std::fprintf(stderr, "stag_fcg_solve: %s after %lld iterations: %s (|r|/|b| = %.3e)\n",
-                                     progress ? "restart" : "fallback to plain CG", iters, why, std::sqrt(rr / bnorm2));
-                    if (progress) {
-                        ++restarts;
-                    } else {
-                        use_plain = true;
-                        ++fallbacks;
-                    }
-                }
-            }
-            inf.iter_rel_residual = rel;
-        }
-        inf.iters = (int32_t)iters;
-        inf.restarts = restarts;
-        inf.fallbacks = fallbacks;
-        inf.true_rel_residual = rel;
-        if (status == STAG_ERR_NOT_CONVERGED) h->err = "flexible CG: not converged";
-        launch_unpack_vec(g, h->x, x_dev ? x_even : h->io_b, S(n));
-        if (!x_dev) pcheck(n, cudaMemcpyAsync(x_even, h->io_b, ab, cudaMemcpyDeviceToHost, S(n)), "copy x");
-        pcheck(n, cudaGetLastError(), "flexible CG");
-        check_tc(n);
-        handle_end(h);
-    } catch (const PFail& f) {
-        status = f.code;
-        h->err = n->err;
-    } catch (const HandleError& f) {
-        status = f.code;
-    }
-    inf.status = status;
-    inf.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (info) *info = inf;
-    return status;
 }
 
 }  // extern "C"

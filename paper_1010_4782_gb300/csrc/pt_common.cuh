@@ -19,6 +19,15 @@ constexpr int kWgradBlocks = 608;  // x-blocks of the weight-gradient grid (4 pe
 
 __device__ __forceinline__ float2 ldc(const float2* p) { return *p; }
 __device__ __forceinline__ float2 ldc(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+// a float-float complex (re_hi, re_lo, im_hi, im_lo) or an FP64 complex, rounded to FP32
+__device__ __forceinline__ float2 ldc(const float4* p) {
+    const float4 v = *p;
+    return make_float2(v.x + v.y, v.z + v.w);
+}
+__device__ __forceinline__ float2 ldc(const double2* p) {
+    const double2 v = *p;
+    return make_float2((float)v.x, (float)v.y);
+}
 __device__ __forceinline__ void stc(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void stc(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
 
@@ -99,19 +108,92 @@ __device__ __forceinline__ Hop pt_hop(const Geom& g, const float2* links, int P,
     return h;
 }
 
-// t = U v (d = 0) or U^dag v (d = 1)
+// t = U v (d = 0) or U^dag v (d = 1), on packed FP32 pairs: per row the real
+// and the imaginary parts of the link each multiply the whole complex v[c],
+//   A = sum_c (Re u, Re u) * (Re v, Im v),  B = sum_c (Im u, Im u) * (Re v, Im v),
+// and U v = (A.x - B.y, A.y + B.x), U^dag v = (A.x + B.y, A.y - B.x): six packed
+// multiply-adds and two adds a row instead of twelve scalar multiply-adds.
 __device__ __forceinline__ void pt_apply(const float2 (&U)[9], int d, const float2 (&v)[3], float2 (&t)[3]) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        float2 a = make_float2(0.f, 0.f);
+        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float2 u = d == 0 ? U[3 * r + c] : U[3 * c + r];
-            const float2 m = d == 0 ? cmulf(u, v[c]) : cmulf_conj(u, v[c]);
-            a.x += m.x;
-            a.y += m.y;
+            a = __ffma2_rn(make_float2(u.x, u.x), v[c], a);
+            b = __ffma2_rn(make_float2(u.y, u.y), v[c], b);
         }
-        t[r] = a;
+        t[r] = d == 0 ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+    }
+}
+
+// ------------------------------------------------ collapsed inference form
+// With the input on even sites and the output read on even sites, the linear
+// network is M r = k0 r + sum_{p,q = 1..8} H[p][q] T_p T_q r (coefficients from
+// pt_collapse_kernel, coef[0] = k0, coef[1 + 8 (p - 1) + (q - 1)] = H[p][q]).
+// chi: [8][3][vs] on odd sites, chi_p = sum_q H[p][q] T_q r, in channel p - 1.
+constexpr int kCollapsedCoefs = 1 + 8 * 8;
+
+// chi of odd site i (P = 1) from r on even sites (float-float, FP64 or FP32),
+// with H in shared memory; returns the 8 x 3 values in acc.
+template <class V>
+__device__ __forceinline__ void pt_chi_site(const Geom& g, const float2* __restrict__ links, const float2* sH,
+                                            const V* __restrict__ r, int i, float2 (&acc)[8][3]) {
+    const size_t vs = (size_t)g.vs;
+    int x, y, z, t;
+    site_coords(i, 1, g, x, y, z, t);
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[p][c] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int q = 1; q < kPaths; ++q) {
+        const int mu = (q - 1) >> 1, d = (q - 1) & 1;
+        const Hop hp = pt_hop(g, links, 1, i, x, y, z, t, mu, d);
+        float2 U[9], v[3], tv[3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = ldc(r + c * vs + hp.nb);
+        pt_apply(U, d, v, tv);
+        // acc_p += H[p][q] tv on packed pairs: (Re h)(Re, Im) + (Im h)(-Im, Re)
+        float2 sw[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sw[c] = make_float2(-tv[c].y, tv[c].x);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const float2 h = sH[8 * p + (q - 1)];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                acc[p][c] = __ffma2_rn(make_float2(h.x, h.x), tv[c], acc[p][c]);
+                acc[p][c] = __ffma2_rn(make_float2(h.y, h.y), sw[c], acc[p][c]);
+            }
+        }
+    }
+}
+
+// z(x) = k0 r(x) + sum_p (T_p chi_p)(x) at even site i (P = 0); r0: r(x) in FP32.
+template <class TS>
+__device__ __forceinline__ void pt_out_site(const Geom& g, const float2* __restrict__ links, float2 k0,
+                                            const TS* __restrict__ chi, int i, const float2 (&r0)[3],
+                                            float2 (&out)[3]) {
+    const size_t vs = (size_t)g.vs;
+    int x, y, z, t;
+    site_coords(i, 0, g, x, y, z, t);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = cmulf(k0, r0[c]);
+#pragma unroll 1
+    for (int p = 1; p < kPaths; ++p) {
+        const int mu = (p - 1) >> 1, d = (p - 1) & 1;
+        const Hop hp = pt_hop(g, links, 0, i, x, y, z, t, mu, d);
+        float2 U[9], v[3], tv[3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = ldc(chi + ((size_t)(p - 1) * 3 + c) * vs + hp.nb);
+        pt_apply(U, d, v, tv);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[c] = __fadd2_rn(out[c], tv[c]);
     }
 }
 
@@ -120,10 +202,12 @@ __device__ __forceinline__ void pt_apply(const float2 (&U)[9], int d, const floa
 // to 1 if a bounded wait ran out.  w3 (nullable): the 8 -> 1 layer's weights;
 // given, the kernel stores phi_p = sum_i W3[p][0][i] psi_i (odd sites: paths
 // 1..8 in channels 0..7; even sites: path 0 in channel 0) instead of psi, and
-// launch_pt_transport_sum finishes the 8 -> 1 layer on even sites.
+// launch_pt_transport_sum finishes the 8 -> 1 layer on even sites.  skip
+// (nullable): a device flag; where it is nonzero when a kernel starts, the
+// kernel returns at once (a captured solver iteration after convergence).
 void launch_pt_mix8_tc(const Geom& g, const float2* links, const float2* w, const __nv_bfloat162* in,
-                       __nv_bfloat162* out, const float2* w3, int* err, cudaStream_t s);
+                       __nv_bfloat162* out, const float2* w3, int* err, cudaStream_t s, const int* skip = nullptr);
 void launch_pt_transport_sum(const Geom& g, const float2* links, const __nv_bfloat162* phi, __nv_bfloat162* out,
-                             cudaStream_t s);
+                             cudaStream_t s, const int* skip = nullptr);
 
 }  // namespace stag

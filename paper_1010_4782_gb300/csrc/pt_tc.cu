@@ -126,7 +126,9 @@ template <class TI, class TO, bool PHI>
 __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const float2* __restrict__ links,
                                                               const float2* __restrict__ w,
                                                               const TI* __restrict__ in, TO* __restrict__ out,
-                                                              const float2* __restrict__ w3, int* err) {
+                                                              const float2* __restrict__ w3, int* err,
+                                                              const int* __restrict__ skip) {
+    if (skip && *skip) return;  // the same value in every thread: the whole CTA leaves before any set-up
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ float2 sW3[kPaths * kHidden];  // PHI: the next layer's weights
     if constexpr (PHI) {
@@ -330,21 +332,23 @@ __global__ void __launch_bounds__(kTileRows) pt_mix8_tc_kernel(Geom g, const flo
 }  // namespace
 
 void launch_pt_mix8_tc(const Geom& g, const float2* links, const float2* w, const __nv_bfloat162* in,
-                       __nv_bfloat162* out, const float2* w3, int* err, cudaStream_t s) {
+                       __nv_bfloat162* out, const float2* w3, int* err, cudaStream_t s, const int* skip) {
     const int tiles = (g.vh + kTileRows - 1) / kTileRows;
     if (w3)
         pt_mix8_tc_kernel<__nv_bfloat162, __nv_bfloat162, true>
-            <<<2 * tiles, kTileRows, kSmemBytes, s>>>(g, links, w, in, out, w3, err);
+            <<<2 * tiles, kTileRows, kSmemBytes, s>>>(g, links, w, in, out, w3, err, skip);
     else
         pt_mix8_tc_kernel<__nv_bfloat162, __nv_bfloat162, false>
-            <<<2 * tiles, kTileRows, kSmemBytes, s>>>(g, links, w, in, out, nullptr, err);
+            <<<2 * tiles, kTileRows, kSmemBytes, s>>>(g, links, w, in, out, nullptr, err, skip);
 }
 
 // out(x) = phi_0(x) + sum_{p = 1..8} (T_p phi_p)(x) on even sites x, from the
 // PHI output of pt_mix8_tc_kernel (the network's last layer, 8 -> 1).
 __global__ void __launch_bounds__(256) pt_transport_sum_kernel(Geom g, const float2* __restrict__ links,
                                                                const __nv_bfloat162* __restrict__ phi,
-                                                               __nv_bfloat162* __restrict__ out) {
+                                                               __nv_bfloat162* __restrict__ out,
+                                                               const int* __restrict__ skip) {
+    if (skip && *skip) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.vh) return;
     const size_t vs = (size_t)g.vs;
@@ -374,8 +378,8 @@ __global__ void __launch_bounds__(256) pt_transport_sum_kernel(Geom g, const flo
 }
 
 void launch_pt_transport_sum(const Geom& g, const float2* links, const __nv_bfloat162* phi, __nv_bfloat162* out,
-                             cudaStream_t s) {
-    pt_transport_sum_kernel<<<(g.vh + 255) / 256, 256, 0, s>>>(g, links, phi, out);
+                             cudaStream_t s, const int* skip) {
+    pt_transport_sum_kernel<<<(g.vh + 255) / 256, 256, 0, s>>>(g, links, phi, out, skip);
 }
 
 }  // namespace stag

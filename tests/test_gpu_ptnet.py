@@ -55,9 +55,14 @@ def _handle(fat, lng, dims, mass, arith=binding.STAG_ARITH_FF):
     return binding.Handle(_dev(fat), dims, mass, naik_long=None if lng is None else _dev(lng), options=opt)
 
 
+FORMS = (binding.STAG_PTNET_COLLAPSED, binding.STAG_PTNET_LAYERED)
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("prec,tol", [(binding.STAG_ARITH_F32, 2e-6), (binding.STAG_ARITH_BF16, 2e-2)])
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8)])
-def test_forward_parity(dims, prec, tol):
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (10, 6, 4, 12)])
+def test_forward_parity(dims, prec, tol, form):
+    """The applied network (both inference forms) against the oracle's layers."""
     fat = inputs.gauge_field(dims, 81)
     w = _random_flat(82)
     r = inputs.gaussian_even_source(dims, 83)
@@ -65,6 +70,7 @@ def test_forward_parity(dims, prec, tol):
     with _handle(fat, None, dims, 0.1) as h:
         net = binding.stag_ptnet_create(h.h, prec, 1)
         try:
+            binding.stag_ptnet_set_inference_form(net, form)
             binding.stag_ptnet_set_weights(net, w)
             z = torch.empty_like(_dev(r))
             binding.stag_ptnet_apply(net, _dev(r), z)
@@ -89,6 +95,7 @@ def test_tensor_core_layer_matches_cuda_cores_and_oracle(dims):
     with _handle(fat, None, dims, 0.1) as h:
         net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 1)
         try:
+            binding.stag_ptnet_set_inference_form(net, binding.STAG_PTNET_LAYERED)
             binding.stag_ptnet_set_weights(net, w)
             for tc in (True, False):
                 binding.stag_ptnet_use_tensor_cores(net, tc)
@@ -103,7 +110,8 @@ def test_tensor_core_layer_matches_cuda_cores_and_oracle(dims):
     assert np.linalg.norm(outs[True] - outs[False]) > 0.0   # the two paths really differ
 
 
-def test_network_weights_reproducing_A():
+@pytest.mark.parametrize("form", FORMS)
+def test_network_weights_reproducing_A(form):
     """Layer 1: (r, D r); layer 2: m^2 r - D(D r); layer 3: identity => the network is A."""
     dims, m = (4, 6, 4, 8), 0.3
     fat, lng = inputs.asqtad_form_fields(dims, seeds=(84, 85, 86))
@@ -121,6 +129,7 @@ def test_network_weights_reproducing_A():
     with _handle(fat, None, dims, m) as h:   # one-hop operator
         net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_F32, 1)
         try:
+            binding.stag_ptnet_set_inference_form(net, form)
             binding.stag_ptnet_set_weights(net, w)
             z = torch.empty_like(_dev(v))
             binding.stag_ptnet_apply(net, _dev(v), z)
@@ -277,6 +286,49 @@ def test_training_gains_over_the_untrained_network(trained):
     finally:
         binding.stag_ptnet_destroy(net0)
     assert its["trained"] < its["untrained"], its
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("arith", [binding.STAG_ARITH_FF, binding.STAG_ARITH_F64])
+@pytest.mark.parametrize("prec,tc,tol", [(binding.STAG_ARITH_F32, False, 1e-5),
+                                         (binding.STAG_ARITH_BF16, True, 5e-2)])
+def test_fcg_iterates_match_oracle(arith, prec, tc, tol, form):
+    """Ten flexible-CG iterations from x = 0 (the iteration budget ends the solve)
+    against the oracle's flexible CG with the same network weights, in both forms of
+    the solver's arithmetic, with the iteration captured in graphs of three (so the
+    budget ends inside a graph) and enqueued directly, with the network collapsed
+    or layered.  The two launch modes run the same kernels in the same order:
+    bit-identical x.  The bound is the network's: FP32 storage (2^-24 per stored
+    value, amplified by ten iterations) or BF16 (2^-9 per stored value; the layered
+    form with the tensor-core layer)."""
+    dims, m, k = (4, 6, 4, 8), 0.05, 10
+    fat, lng = inputs.asqtad_form_fields(dims, seeds=(91, 92, 93))
+    b = inputs.gaussian_even_source(dims, 94)
+    xs = {}
+    for graphs in (1, 0):
+        opt = binding.stag_default_options()
+        opt.arith = arith
+        opt.use_graphs = graphs
+        opt.check_interval = 3
+        with binding.Handle(_dev(fat), dims, m, naik_long=_dev(lng), options=opt) as h:
+            net = binding.stag_ptnet_create(h.h, prec, 3)
+            try:
+                binding.stag_ptnet_set_inference_form(net, form)
+                binding.stag_ptnet_use_tensor_cores(net, tc)
+                w = binding.stag_ptnet_weights(net)
+                x = torch.zeros_like(_dev(b))
+                code, info = binding.stag_fcg_solve(h.h, net, _dev(b), x, 1e-10, max_iter=k)
+            finally:
+                binding.stag_ptnet_destroy(net)
+        assert code == binding.STAG_ERR_NOT_CONVERGED, info
+        assert info["iters"] == k and info["fallbacks"] == 0 and info["restarts"] == 0, info
+        xs[graphs] = x.cpu().numpy().reshape(-1)
+    assert np.array_equal(xs[0], xs[1])
+    op = oracle.Operator(fat, lng, m, dims)
+    ref, its = ptnet.fcg(op.apply_A, ptnet.PTNet(fat, dims, _split(w)).apply, b, tol=1e-10, max_iter=k)
+    assert its == k
+    err = np.linalg.norm(xs[1] - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
 
 
 def test_fcg_falls_back_to_plain_cg(trained):

@@ -57,6 +57,33 @@ def _random_weights(seed, chans=(1, 8, 8, 1)):
             for ci, co in zip(chans[:-1], chans[1:])]
 
 
+def test_layers_equal_the_two_hop_form():
+    """With the input on even sites and the output read on even sites, only the
+    layer paths with zero or two hops contribute, so the three linear layers equal
+    k0 + sum_{p,q >= 1} H[p][q] T_p T_q with C[a][b][c] = W3[a] W2[b] W1[c]
+    (channel contractions), k0 = C[0][0][0], H[p][q] = C[p][q][0] + C[p][0][q] +
+    C[0][p][q].  This is the form the library evaluates when it applies the
+    network; here it is checked against the oracle's layers, on a ragged lattice
+    and for random, untied weights."""
+    dims = (4, 6, 4, 8)
+    fat = inputs.gauge_field(dims, 81)
+    w1, w2, w3 = _random_weights(3)
+    net = ptnet.PTNet(fat, dims, [w1, w2, w3])
+    r = inputs.gaussian_even_source(dims, 83)
+    C = np.einsum("ao,boi,ci->abc", w3[:, 0, :], w2, w1[:, :, 0])
+    psi = oracle.embed(r, dims, 0)
+    out = C[0, 0, 0] * psi
+    for p in range(1, 9):
+        chi = sum((C[p, q, 0] + C[p, 0, q] + C[0, p, q]) * ptnet.transport(net.u, psi, q) for q in range(1, 9))
+        out = out + ptnet.transport(net.u, chi, p)
+    got = oracle.restrict(out, dims, 0)
+    ref = net.apply(r)
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    # a term with an odd number of hops (here the one-hop part of layer 1) is zero on even sites
+    odd = ptnet.transport(net.u, psi, 1)
+    assert np.abs(oracle.restrict(odd, dims, 0)).max() == 0.0
+
+
 def test_network_gauge_covariant_and_linear():
     dims = (4, 4, 4, 6)
     fat = inputs.gauge_field(dims, 7)

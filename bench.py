@@ -689,7 +689,7 @@ def run_learned(args):
     loss1 = binding.stag_ptnet_dataset_loss(net)
     # the same network untrained: the library's polynomial start with the same seed
     net0 = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 5)
-    res = {"fcg": [], "fcg_untrained": [], "fcg_fp32": [], "cg": []}
+    res = {"fcg": [], "fcg_untrained": [], "fcg_fp32": [], "fcg_layered": [], "cg": []}
     for j in range(args.test_sources):
         b = torch.from_numpy(inputs.gaussian_even_source(dims, 90000 + j)).to(dev)
         runs = [("fcg", net, binding.STAG_ARITH_BF16), ("fcg_untrained", net0, binding.STAG_ARITH_BF16)]
@@ -701,6 +701,12 @@ def run_learned(args):
             code, info = binding.stag_fcg_solve(h.h, nt, b, x, TOL, MAX_ITER)
             res[key].append((code, info))
         binding.stag_ptnet_set_inference_precision(net, binding.STAG_ARITH_BF16)
+        if j < 4:
+            # the same network evaluated layer by layer (BF16 activations, tensor-core layer)
+            binding.stag_ptnet_set_inference_form(net, binding.STAG_PTNET_LAYERED)
+            x = torch.zeros_like(b)
+            res["fcg_layered"].append(binding.stag_fcg_solve(h.h, net, b, x, TOL, MAX_ITER))
+            binding.stag_ptnet_set_inference_form(net, binding.STAG_PTNET_COLLAPSED)
         x2 = torch.zeros_like(b)
         code2, info2 = binding.stag_cg_solve(h.h, b, x2, TOL, MAX_ITER)
         res["cg"].append((code2, info2))
@@ -744,7 +750,7 @@ def run_learned(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16 network, float-float CG",
+        "dtype": "float-float CG; network: BF16-stored intermediate, FP32 arithmetic (two-hop form)",
         "data": "synthetic (seeded SU(3) fields exp(0.3 i H), Gaussian sources)",
         "config": {"workload": f"flexible CG + 3-layer PT network (1-8-8-1 complex channels), "
                                f"{'x'.join(map(str, dims))} asqtad-form, m={args.mass}, tol {TOL}",
@@ -763,6 +769,7 @@ def run_learned(args):
         "fcg_untrained_polynomial_start": fcg0,
         "iteration_gain_of_training": round(fcg0["iters_mean"] / fcg["iters_mean"], 3),
         "fcg_fp32_inference_first_16_sources": fcg32,
+        "fcg_layered_bf16_tensor_cores_first_4_sources": summary(res["fcg_layered"]),
         "plain_cg_ff": cg,
         "plain_cg_fp64_first_sources": cg64,
         "time_ratio_fcg_over_fp64_cg_same_sources": round(fcg4["time_s_mean"] / cg64["time_s_mean"], 3),

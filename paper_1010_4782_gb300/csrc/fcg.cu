@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(kBlock) fcg_zdots_kernel(Geom g, const T* __re
 // Collapsed form of the network, fused: z = k0 r + sum_p T_p chi_p on even
 // sites (pt_out_site; chi from pt_chi_kernel), stored in FP32, with (z, r),
 // (z, q) and beta as in fcg_zdots_kernel.
-template <class V, class TS>
-__global__ void __launch_bounds__(kBlock) fcg_out_kernel(Geom g, const float2* __restrict__ links,
+template <class V, class TS, class L>
+__global__ void __launch_bounds__(kBlock) fcg_out_kernel(Geom g, const L* __restrict__ links,
                                                          const float2* __restrict__ coef, const TS* __restrict__ chi,
                                                          const V* __restrict__ r, const V* __restrict__ q,
                                                          float2* __restrict__ z, FcgDev* d, double* partials,
@@ -343,9 +343,12 @@ void enqueue_precond(stag_ptnet* n, const V* r, const V* q, int start) {
     if (n->inf_form == STAG_PTNET_COLLAPSED) {
         float2* z = static_cast<float2*>(n->act[kLayers]);
         launch_pt_chi(n, r, &d->sc.done);
-        fcg_out_kernel<V, T><<<blocks_for(g.vh), kBlock, 0, h->s>>>(g, n->links, n->coef,
-                                                                     static_cast<const T*>(n->act[2]), r, q, z, d,
-                                                                     h->partials, start);
+        if constexpr (std::is_same<T, __nv_bfloat162>::value)  // FP16 links with BF16 storage
+            fcg_out_kernel<V, T, __half2><<<blocks_for(g.vh), kBlock, 0, h->s>>>(
+                g, n->links16, n->coef, static_cast<const T*>(n->act[2]), r, q, z, d, h->partials, start);
+        else
+            fcg_out_kernel<V, T, float2><<<blocks_for(g.vh), kBlock, 0, h->s>>>(
+                g, n->links, n->coef, static_cast<const T*>(n->act[2]), r, q, z, d, h->partials, start);
         fcg_dir_kernel<V, float2><<<blocks_for(g.vh), kBlock, 0, h->s>>>(g, z, p, d, start);
     } else {
         const T* z = static_cast<const T*>(n->act[kLayers]);

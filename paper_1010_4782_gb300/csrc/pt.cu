@@ -489,12 +489,29 @@ __global__ void pt_links_kernel(const double2* __restrict__ in, float2* __restri
     if (k < n) out[k] = make_float2((float)in[k].x, (float)in[k].y);
 }
 
+// largest |Re|, |Im| of the entries (as FP32 bits, atomically into *out; NaNs ignored)
+__global__ void pt_absmax_kernel(const double2* __restrict__ in, size_t n, unsigned int* out) {
+    float m = 0.f;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fmaxf(fabsf((float)in[k].x), fabsf((float)in[k].y)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// FP16 copy of the links divided by s
+__global__ void pt_links16_kernel(const double2* __restrict__ in, __half2* __restrict__ out, size_t n, double inv_s) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = __floats2half2_rn((float)(in[k].x * inv_s), (float)(in[k].y * inv_s));
+}
+
 // ------------------------------------------------ collapsed inference form
 // coef[0] = k0 = C[0][0][0], coef[1 + 8 (p - 1) + (q - 1)] = H[p][q] =
 // C[p][q][0] + C[p][0][q] + C[0][p][q] with C[a][b][c] = sum_{o,i} W3[a][0][o]
 // W2[b][o][i] W1[c][i][0]: the terms of the layer product T_a T_b T_c that
-// take an even site to an even site (zero or two hops).  FP64 sums.
-__global__ void pt_collapse_kernel(const float2* __restrict__ w, float2* __restrict__ coef) {
+// take an even site to an even site (zero or two hops).  FP64 sums; H is
+// multiplied by h_scale (s^2 for links stored divided by s).
+__global__ void pt_collapse_kernel(const float2* __restrict__ w, float2* __restrict__ coef, double h_scale) {
     const int t = threadIdx.x;
     if (t >= kCollapsedCoefs) return;
     const float2* w1 = w;                                    // [9][8][1]
@@ -520,14 +537,14 @@ __global__ void pt_collapse_kernel(const float2* __restrict__ w, float2* __restr
     } else {
         const int p = 1 + (t - 1) / 8, q = 1 + (t - 1) % 8;
         const double2 a = C(p, q, 0), b = C(p, 0, q), c = C(0, p, q);
-        h = make_double2(a.x + b.x + c.x, a.y + b.y + c.y);
+        h = make_double2(h_scale * (a.x + b.x + c.x), h_scale * (a.y + b.y + c.y));
     }
     coef[t] = make_float2((float)h.x, (float)h.y);
 }
 
-// chi on odd sites (pt_chi_site), stored as TS
-template <class V, class TS>
-__global__ void __launch_bounds__(256, 2) pt_chi_kernel(Geom g, const float2* __restrict__ links,
+// chi on odd sites (pt_chi_site), stored as TS; links stored as L
+template <class V, class TS, class L>
+__global__ void __launch_bounds__(256, 2) pt_chi_kernel(Geom g, const L* __restrict__ links,
                                                         const float2* __restrict__ coef, const V* __restrict__ r,
                                                         TS* __restrict__ chi, const int* __restrict__ skip) {
     if (skip && *skip) return;
@@ -546,8 +563,8 @@ __global__ void __launch_bounds__(256, 2) pt_chi_kernel(Geom g, const float2* __
 }
 
 // out (FP64, even sites) = k0 r + sum_p T_p chi_p
-template <class TS>
-__global__ void __launch_bounds__(256) pt_out_kernel(Geom g, const float2* __restrict__ links,
+template <class TS, class L>
+__global__ void __launch_bounds__(256) pt_out_kernel(Geom g, const L* __restrict__ links,
                                                      const float2* __restrict__ coef, const TS* __restrict__ chi,
                                                      const double2* __restrict__ r, double2* __restrict__ out) {
     const int i = blockIdx.x * 256 + threadIdx.x;
@@ -818,7 +835,7 @@ void destroy_net(stag_ptnet* n) {
     for (void* p : {(void*)n->links, (void*)n->lng, (void*)n->va, (void*)n->vt, (void*)n->vad, (void*)n->w, (void*)n->grad, (void*)n->adam_m, (void*)n->adam_v,
                     (void*)n->wpart, (void*)n->red, n->scratch_r, n->scratch_e, (void*)n->fr, (void*)n->fz,
                     (void*)n->fq, (void*)n->tc_err, (void*)n->dot_counter, (void*)n->dot_out, n->fcg_r, n->fcg_p,
-                    n->fcg_q, n->fcg_t, n->fcg_x, (void*)n->fcg_dev, (void*)n->coef})
+                    n->fcg_q, n->fcg_t, n->fcg_x, (void*)n->fcg_dev, (void*)n->coef, (void*)n->links16})
         if (p) cudaFree(p);
     if (n->fcg_host) cudaFreeHost(n->fcg_host);
     if (n->fcg_graph) cudaGraphExecDestroy(n->fcg_graph);
@@ -882,17 +899,20 @@ namespace stag {
 void pt_network_from_vec(stag_ptnet* n, const float4* r, const int* skip) { network_from_vec_any(n, r, skip); }
 void pt_network_from_vec(stag_ptnet* n, const double2* r, const int* skip) { network_from_vec_any(n, r, skip); }
 
-void pt_collapse(stag_ptnet* n) { pt_collapse_kernel<<<1, 96, 0, S(n)>>>(n->w, n->coef); }
+void pt_collapse(stag_ptnet* n) {
+    const double s = infer_bf16(n) ? (double)n->links16_scale : 1.0;
+    pt_collapse_kernel<<<1, 96, 0, S(n)>>>(n->w, n->coef, s * s);
+}
 
 template <class V>
 void launch_pt_chi_any(stag_ptnet* n, const V* r, const int* skip) {
     const int nb = blocks_for(n->g.vh, 256);
     if (infer_bf16(n))
-        pt_chi_kernel<V, __nv_bfloat162><<<nb, 256, 0, S(n)>>>(n->g, n->links, n->coef, r,
-                                                               static_cast<__nv_bfloat162*>(n->act[2]), skip);
+        pt_chi_kernel<V, __nv_bfloat162, __half2><<<nb, 256, 0, S(n)>>>(
+            n->g, n->links16, n->coef, r, static_cast<__nv_bfloat162*>(n->act[2]), skip);
     else
-        pt_chi_kernel<V, float2><<<nb, 256, 0, S(n)>>>(n->g, n->links, n->coef, r, static_cast<float2*>(n->act[2]),
-                                                       skip);
+        pt_chi_kernel<V, float2, float2><<<nb, 256, 0, S(n)>>>(n->g, n->links, n->coef, r,
+                                                               static_cast<float2*>(n->act[2]), skip);
 }
 void launch_pt_chi(stag_ptnet* n, const float4* r, const int* skip) { launch_pt_chi_any(n, r, skip); }
 void launch_pt_chi(stag_ptnet* n, const double2* r, const int* skip) { launch_pt_chi_any(n, r, skip); }
@@ -905,11 +925,11 @@ void apply_collapsed(stag_ptnet* n, const double2* r, double2* z) {
     pt_collapse(n);
     launch_pt_chi(n, r, nullptr);
     if (infer_bf16(n))
-        pt_out_kernel<__nv_bfloat162><<<blocks_for(g.vh, 256), 256, 0, S(n)>>>(
-            g, n->links, n->coef, static_cast<const __nv_bfloat162*>(n->act[2]), r, z);
+        pt_out_kernel<__nv_bfloat162, __half2><<<blocks_for(g.vh, 256), 256, 0, S(n)>>>(
+            g, n->links16, n->coef, static_cast<const __nv_bfloat162*>(n->act[2]), r, z);
     else
-        pt_out_kernel<float2><<<blocks_for(g.vh, 256), 256, 0, S(n)>>>(g, n->links, n->coef,
-                                                                       static_cast<const float2*>(n->act[2]), r, z);
+        pt_out_kernel<float2, float2><<<blocks_for(g.vh, 256), 256, 0, S(n)>>>(
+            g, n->links, n->coef, static_cast<const float2*>(n->act[2]), r, z);
 }
 }  // namespace
 
@@ -934,6 +954,23 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         const size_t nl = (size_t)2 * 4 * 9 * n->g.vs;
         n->links = static_cast<float2*>(palloc(n, nl * sizeof(float2), "allocate links"));
         pt_links_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->fat64, n->links, nl);
+        {
+            // FP16 links for the two-hop inference kernels, divided by s = the power of two
+            // nearest the largest entry (so that they stay inside FP16's normal range)
+            unsigned int* mx = static_cast<unsigned int*>(palloc(n, sizeof(unsigned int), "allocate scratch"));
+            pt_absmax_kernel<<<1024, 256, 0, S(n)>>>(h->fat64, nl, mx);
+            unsigned int bits = 0;
+            pcheck(n, cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, S(n)), "read link maximum");
+            pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+            cudaFree(mx);
+            n->device_bytes -= (long long)sizeof(unsigned int);
+            float amax;
+            std::memcpy(&amax, &bits, sizeof(amax));
+            n->links16_scale = (amax > 0.f && std::isfinite(amax)) ? std::exp2f(std::round(std::log2(amax))) : 1.f;
+            n->links16 = static_cast<__half2*>(palloc(n, nl * sizeof(__half2), "allocate links"));
+            pt_links16_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->fat64, n->links16, nl,
+                                                                          1.0 / n->links16_scale);
+        }
         if (h->lng64) {
             n->lng = static_cast<float2*>(palloc(n, nl * sizeof(float2), "allocate links"));
             pt_links_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->lng64, n->lng, nl);

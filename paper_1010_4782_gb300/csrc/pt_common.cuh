@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "stag_kernels.h"
 
@@ -87,15 +88,19 @@ __device__ __forceinline__ int pt_neighbour(const Geom& g, int x, int y, int z, 
 }
 
 // Source site (parity Pn, index nb) and link of transport direction d
-// (0: from x + mu with U_mu(x); 1: from x - mu with U_mu(x - mu)^dag).
-struct Hop {
+// (0: from x + mu with U_mu(x); 1: from x - mu with U_mu(x - mu)^dag); links
+// stored as L (float2, or __half2 for the two-hop inference kernels).
+template <class L>
+struct HopT {
     int Pn, nb;
-    const float2* u;
+    const L* u;
 };
+using Hop = HopT<float2>;
 
-__device__ __forceinline__ Hop pt_hop(const Geom& g, const float2* links, int P, int i, int x, int y, int z, int t,
-                                      int mu, int d) {
-    Hop h;
+template <class L>
+__device__ __forceinline__ HopT<L> pt_hop(const Geom& g, const L* links, int P, int i, int x, int y, int z, int t,
+                                          int mu, int d) {
+    HopT<L> h;
     h.Pn = 1 - P;
     const size_t vs = (size_t)g.vs;
     if (d == 0) {
@@ -107,6 +112,10 @@ __device__ __forceinline__ Hop pt_hop(const Geom& g, const float2* links, int P,
     }
     return h;
 }
+
+// one link entry in FP32
+__device__ __forceinline__ float2 ldu(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldu(const __half2* p) { return __half22float2(__ldg(p)); }
 
 // t = U v (d = 0) or U^dag v (d = 1), on packed FP32 pairs: per row the real
 // and the imaginary parts of the link each multiply the whole complex v[c],
@@ -132,12 +141,15 @@ __device__ __forceinline__ void pt_apply(const float2 (&U)[9], int d, const floa
 // network is M r = k0 r + sum_{p,q = 1..8} H[p][q] T_p T_q r (coefficients from
 // pt_collapse_kernel, coef[0] = k0, coef[1 + 8 (p - 1) + (q - 1)] = H[p][q]).
 // chi: [8][3][vs] on odd sites, chi_p = sum_q H[p][q] T_q r, in channel p - 1.
+// Links as FP32, or (BF16 storage of chi) as FP16 divided by a power of two s
+// near their largest entry: every two-hop term then carries 1/s^2, which the
+// coefficients H take back (k0, with no hop, is unscaled).
 constexpr int kCollapsedCoefs = 1 + 8 * 8;
 
 // chi of odd site i (P = 1) from r on even sites (float-float, FP64 or FP32),
 // with H in shared memory; returns the 8 x 3 values in acc.
-template <class V>
-__device__ __forceinline__ void pt_chi_site(const Geom& g, const float2* __restrict__ links, const float2* sH,
+template <class V, class L>
+__device__ __forceinline__ void pt_chi_site(const Geom& g, const L* __restrict__ links, const float2* sH,
                                             const V* __restrict__ r, int i, float2 (&acc)[8][3]) {
     const size_t vs = (size_t)g.vs;
     int x, y, z, t;
@@ -149,10 +161,10 @@ __device__ __forceinline__ void pt_chi_site(const Geom& g, const float2* __restr
 #pragma unroll 1
     for (int q = 1; q < kPaths; ++q) {
         const int mu = (q - 1) >> 1, d = (q - 1) & 1;
-        const Hop hp = pt_hop(g, links, 1, i, x, y, z, t, mu, d);
+        const HopT<L> hp = pt_hop(g, links, 1, i, x, y, z, t, mu, d);
         float2 U[9], v[3], tv[3];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+        for (int k = 0; k < 9; ++k) U[k] = ldu(hp.u + k * vs);
 #pragma unroll
         for (int c = 0; c < 3; ++c) v[c] = ldc(r + c * vs + hp.nb);
         pt_apply(U, d, v, tv);
@@ -173,8 +185,8 @@ __device__ __forceinline__ void pt_chi_site(const Geom& g, const float2* __restr
 }
 
 // z(x) = k0 r(x) + sum_p (T_p chi_p)(x) at even site i (P = 0); r0: r(x) in FP32.
-template <class TS>
-__device__ __forceinline__ void pt_out_site(const Geom& g, const float2* __restrict__ links, float2 k0,
+template <class TS, class L>
+__device__ __forceinline__ void pt_out_site(const Geom& g, const L* __restrict__ links, float2 k0,
                                             const TS* __restrict__ chi, int i, const float2 (&r0)[3],
                                             float2 (&out)[3]) {
     const size_t vs = (size_t)g.vs;
@@ -185,10 +197,10 @@ __device__ __forceinline__ void pt_out_site(const Geom& g, const float2* __restr
 #pragma unroll 1
     for (int p = 1; p < kPaths; ++p) {
         const int mu = (p - 1) >> 1, d = (p - 1) & 1;
-        const Hop hp = pt_hop(g, links, 0, i, x, y, z, t, mu, d);
+        const HopT<L> hp = pt_hop(g, links, 0, i, x, y, z, t, mu, d);
         float2 U[9], v[3], tv[3];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) U[k] = __ldg(hp.u + k * vs);
+        for (int k = 0; k < 9; ++k) U[k] = ldu(hp.u + k * vs);
 #pragma unroll
         for (int c = 0; c < 3; ++c) v[c] = ldc(chi + ((size_t)(p - 1) * 3 + c) * vs + hp.nb);
         pt_apply(U, d, v, tv);

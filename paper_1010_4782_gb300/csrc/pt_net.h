@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -43,6 +44,8 @@ struct stag_ptnet {
     int inf_prec = STAG_ARITH_BF16;  // activation storage when the network is applied
     size_t elem = 4;             // bytes per stored complex
     float2* links = nullptr;     // FP32 eta-folded fat links (transports and A)
+    __half2* links16 = nullptr;  // the same / links16_scale in FP16 (two-hop inference with BF16 storage)
+    float links16_scale = 1.f;   // a power of two near the largest link entry
     float2* lng = nullptr;       // FP32 eta-folded Naik links (A), or nullptr
     float2 *va = nullptr, *vt = nullptr, *vad = nullptr;  // FP32 [3][vs] vectors for A d
     std::vector<float2> w_host;  // weights, layer-major [9][C_out][C_in]

@@ -80,6 +80,31 @@ def test_forward_parity(dims, prec, tol, form):
     assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("c", [1e5, 1e-6])
+def test_two_hop_form_with_links_far_from_one(c):
+    """The two-hop form with BF16 storage reads FP16 links divided by a power of two
+    near their largest entry.  Links scaled by 1e5 (beyond FP16's range) and by 1e-6
+    (FP16 subnormals unscaled), against the oracle at the BF16 bound.  The first
+    layer's identity path is zero, so k0 = 0 and the output is the two-hop part
+    alone (which, at 1e-6, would otherwise sit below the FP32 rounding of k0 r)."""
+    dims = (6, 4, 2, 8)
+    fat = inputs.gauge_field(dims, 81) * c
+    w = _random_flat(82)
+    w[:8] = 0.0   # W1[0][:][0]
+    r = inputs.gaussian_even_source(dims, 83)
+    ref = ptnet.PTNet(fat, dims, _split(w)).apply(r)
+    with _handle(fat, None, dims, 0.1) as h:
+        net = binding.stag_ptnet_create(h.h, binding.STAG_ARITH_BF16, 1)
+        try:
+            binding.stag_ptnet_set_weights(net, w)
+            z = torch.empty_like(_dev(r))
+            binding.stag_ptnet_apply(net, _dev(r), z)
+        finally:
+            binding.stag_ptnet_destroy(net)
+    got = z.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (10, 6, 4, 12), (8, 8, 8, 16)])
 def test_tensor_core_layer_matches_cuda_cores_and_oracle(dims):
     """The BF16 network with its 8 -> 8 channel mixing on the tensor cores against

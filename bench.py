@@ -128,22 +128,26 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def dslash_source_hash():
+DSLASH_SOURCES = ("dslash.cu", "ff.cuh", "stag_internal.cuh")
+MULTI_SOURCES = ("multi.cu", "multi.cuh", "stag_internal.cuh")
+
+
+def dslash_source_hash(files=DSLASH_SOURCES):
     h = hashlib.sha256()
-    for f in ("dslash.cu", "ff.cuh", "stag_internal.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1010_4782_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_key):
+def recorded_traffic(kernel_key, files=DSLASH_SOURCES):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[kernel_key]
-        if e.get("source_hash") != dslash_source_hash():
+        if e.get("source_hash") != dslash_source_hash(files):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -628,7 +632,9 @@ def run_batched(args):
                                + ", tol 1e-10",
                    "step": "stag_batch_create + stag_batch_solve + stag_batch_destroy"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": recorded_traffic(f"multi_dslash_oe_f32_{BATCH_NRHS}rhs_32x32x32x64_rb{rb}_bs{bsz}_"
+                                                 f"{'sweep' if sweep else 'runs'}", MULTI_SOURCES),
                      "kernel": f"multi-RHS D_oe, 16 RHS, FP32, {rb} RHS/thread, {bsz} threads/block, "
                                f"{'resident sweep' if sweep else 'contiguous tile runs'} "
                                "(autotuner's CUDA-event time)",

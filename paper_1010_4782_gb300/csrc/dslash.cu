@@ -408,9 +408,9 @@ __device__ __forceinline__ void dslash_site(const DslashParams<A>& p, int i, typ
 
 template <class A, int NAIK, int EPI>
 __global__ void __launch_bounds__(kBlock, NAIK == 2 ? 3 : 4) dslash_kernel(const DslashParams<A> p) {
-    if (EPI == EPI_CG) {
-        if (p.scal->done) return;
-    }
+    // Inside a solver iteration (CG state given): return once the loop has
+    // stopped, so that the rest of a captured block of iterations costs nothing.
+    if (p.scal && p.scal->done) return;
     const Geom& g = p.g;
     const int i = p.i0 + blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;

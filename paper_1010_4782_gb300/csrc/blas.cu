@@ -20,6 +20,8 @@
 // of the FP32 rate, so the float-float set keeps the iteration free of them:
 // x is accumulated in float-float since the last fold and added into the FP64
 // solution by fold_x once per block of iterations.
+#include <algorithm>
+
 #include "ff.cuh"
 #include "stag_kernels.h"
 
@@ -96,10 +98,10 @@ __global__ void __launch_bounds__(kBlock) cg_update_xr_kernel(Geom g, double2* _
                                                               CgScalars* scal, double* partials) {
     if (scal->done) return;
     const double alpha = scal->alpha;
-    const int i = blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;
     double acc = 0.0;
-    if (i < g.vh) {
+    // grid-stride over sites (one resident wave of blocks: a short grid reduction)
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.vh; i += gridDim.x * kBlock) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t k = c * vs + i;
@@ -179,10 +181,10 @@ __global__ void __launch_bounds__(kBlock) cg_update_xr_ff_kernel(Geom g, float4*
                                                                  CgScalars* scal, double* partials) {
     if (scal->done) return;
     const float2 alpha = scal->alpha_ff;
-    const int i = blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;
     FFAcc n2 = ff_zero();
-    if (i < g.vh) {
+    // grid-stride over sites (one resident wave of blocks: a short grid reduction)
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.vh; i += gridDim.x * kBlock) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t k = c * vs + i;
@@ -276,6 +278,19 @@ __global__ void __launch_bounds__(kBlock) from_ff_kernel(Geom g, const float4* _
 }
 
 // ------------------------------------------------------------ launchers
+int resident_wave_blocks() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1024;
+    if (!cached[dev]) {
+        int sms = 0, threads = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        cached[dev] = sms > 0 && threads > 0 ? sms * std::max(1, threads / kBlock) : 1024;
+    }
+    return cached[dev];
+}
+
 void launch_cg_reset(CgScalars* scal, double threshold, double m2, long long max_iter, cudaStream_t s) {
     cg_reset_kernel<<<1, 1, 0, s>>>(scal, threshold, m2, host_ff_from_double(m2), max_iter);
 }
@@ -287,7 +302,8 @@ void launch_cg_init(const Geom& g, const double2* b, const double2* ad, double2*
 
 void launch_cg_update_xr(const Geom& g, double2* x, double2* r, const double2* d, const double2* ad,
                          CgScalars* scal, double* partials, cudaStream_t s) {
-    cg_update_xr_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, x, r, d, ad, scal, partials);
+    cg_update_xr_kernel<<<std::min(blocks_for(g.vh), resident_wave_blocks()), kBlock, 0, s>>>(g, x, r, d, ad, scal,
+                                                                                             partials);
 }
 
 void launch_cg_update_d(const Geom& g, const double2* r, double2* d, CgScalars* scal, cudaStream_t s) {
@@ -301,7 +317,8 @@ void launch_cg_init_ff(const Geom& g, const double2* b, const double2* ad, float
 
 void launch_cg_update_xr_ff(const Geom& g, float4* xff, float4* r, const float4* d, const float4* ad,
                             CgScalars* scal, double* partials, cudaStream_t s) {
-    cg_update_xr_ff_kernel<<<blocks_for(g.vh), kBlock, 0, s>>>(g, xff, r, d, ad, scal, partials);
+    cg_update_xr_ff_kernel<<<std::min(blocks_for(g.vh), resident_wave_blocks()), kBlock, 0, s>>>(g, xff, r, d, ad,
+                                                                                                scal, partials);
 }
 
 void launch_cg_update_d_ff(const Geom& g, const float4* r, float4* d, CgScalars* scal, cudaStream_t s) {

@@ -18,6 +18,8 @@
 
 #include <type_traits>
 
+#include <algorithm>
+
 #include "ff.cuh"
 #include "stag_kernels.h"
 
@@ -29,6 +31,12 @@ __device__ __forceinline__ void stv(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void stv(__half2* p, float2 v) { *p = __float22half2_rn(v); }
 __device__ __forceinline__ float2 ldv(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
 __device__ __forceinline__ void stv(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+// the value stv stores, as ldv would read it back (rounded in registers)
+__device__ __forceinline__ float2 as_stored(const float2*, float2 v) { return v; }
+__device__ __forceinline__ float2 as_stored(const __half2*, float2 v) { return __half22float2(__float22half2_rn(v)); }
+__device__ __forceinline__ float2 as_stored(const __nv_bfloat162*, float2 v) {
+    return __bfloat1622float2(__float22bfloat162_rn(v));
+}
 
 // r64 = b - Ax (Ax in FP64 or float-float); scal->red_out = |r64|^2
 template <class AXT>
@@ -76,7 +84,7 @@ __global__ void __launch_bounds__(kBlock) lo_set_residual_kernel(Geom g, const d
         const double2 rr = r64[k];
         const float2 rl = make_float2((float)(rr.x * inv_sigma), (float)(rr.y * inv_sigma));
         stv(r + k, rl);
-        const float2 rq = ldv(r + k);  // the stored (rounded) residual
+        const float2 rq = as_stored(r, rl);  // the stored (rounded) residual
         if (first) {
             stv(d + k, rq);
         } else {
@@ -112,10 +120,11 @@ __global__ void __launch_bounds__(kBlock) lo_update_xr_kernel(Geom g, float2* __
                                                               double* partials) {
     if (scal->done) return;
     const float alpha = scal->alpha_ff.x;
-    const int i = blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;
     float acc = 0.f;
-    if (i < g.vh) {
+    // grid-stride over sites: one resident wave of blocks, so that the grid
+    // reduction's ticket and partial sums come from a few hundred blocks
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.vh; i += gridDim.x * kBlock) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t k = c * vs + i;
@@ -129,7 +138,7 @@ __global__ void __launch_bounds__(kBlock) lo_update_xr_kernel(Geom g, float2* __
             rr.x = fmaf(-alpha, aa.x, rr.x);
             rr.y = fmaf(-alpha, aa.y, rr.y);
             stv(r + k, rr);
-            const float2 rq = ldv(r + k);
+            const float2 rq = as_stored(r, rr);  // the stored residual, without reading it back
             acc = fmaf(rq.x, rq.x, acc);
             acc = fmaf(rq.y, rq.y, acc);
         }
@@ -259,7 +268,8 @@ void launch_lo_set_residual(const Geom& g, const double2* r64, V* r, V* d, float
 template <class V>
 void launch_lo_update_xr(const Geom& g, float2* y, V* r, const V* d, const V* ad, CgScalars* scal,
                          double* partials, cudaStream_t s) {
-    lo_update_xr_kernel<V><<<blocks_for(g.vh), kBlock, 0, s>>>(g, y, r, d, ad, scal, partials);
+    const int grid = std::min(blocks_for(g.vh), resident_wave_blocks());
+    lo_update_xr_kernel<V><<<grid, kBlock, 0, s>>>(g, y, r, d, ad, scal, partials);
 }
 
 template <class V>

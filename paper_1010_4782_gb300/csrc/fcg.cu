@@ -195,10 +195,10 @@ __global__ void __launch_bounds__(kBlock) fcg_update_kernel(Geom g, V* __restric
     if (d->sc.done) return;
     const double alpha = d->sc.alpha;
     const float2 alpha_ff = d->sc.alpha_ff;
-    const int i = blockIdx.x * kBlock + threadIdx.x;
     const size_t vs = (size_t)g.vs;
     typename Arith<V>::Acc n2 = Arith<V>::zero();
-    if (i < g.vh) {
+    // grid-stride over sites (one resident wave of blocks: a short grid reduction)
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.vh; i += gridDim.x * kBlock) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t k = c * vs + i;
@@ -369,7 +369,8 @@ void enqueue_iteration(stag_ptnet* n, const Vecs& v) {
     V* p = static_cast<V*>(v.p);
     V* q = static_cast<V*>(v.q);
     enqueue_A(h, d, p, static_cast<V*>(v.t), q);
-    fcg_update_kernel<V><<<blocks_for(g.vh), kBlock, 0, h->s>>>(g, static_cast<V*>(v.xacc), r, p, q, d, h->partials);
+    fcg_update_kernel<V><<<std::min(blocks_for(g.vh), resident_wave_blocks()), kBlock, 0, h->s>>>(
+        g, static_cast<V*>(v.xacc), r, p, q, d, h->partials);
     enqueue_precond<V, T>(n, r, q, 0);
 }
 

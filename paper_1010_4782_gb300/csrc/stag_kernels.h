@@ -92,6 +92,9 @@ void launch_dslash_b16(const Geom& g, int out_parity, const __nv_bfloat162* fat,
                        double m2, CgScalars* scal, double* partials, cudaStream_t s);
 
 // ---- CG vector kernels and reductions (blas.cu)
+// kBlock-thread blocks that fill every SM of the current device once (grid of
+// the grid-stride update kernels, whose grid reduction then has few partials)
+int resident_wave_blocks();
 // start of one run of Fig. 1 (iter = 0, done = 0, threshold, m^2, max_iter)
 void launch_cg_reset(CgScalars* scal, double threshold, double m2, long long max_iter,
                      cudaStream_t s);

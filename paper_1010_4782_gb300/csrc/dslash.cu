@@ -406,8 +406,20 @@ __device__ __forceinline__ void dslash_site(const DslashParams<A>& p, int i, typ
     }
 }
 
+// Resident 256-thread blocks per SM the register allocation is held to.  The
+// float-float kernels are bound by memory latency: with up to 128 registers
+// (2 blocks) the compiler keeps more of a site's loads in flight, and the
+// float-float CG solve at 28^3 x 96 measured 1304 ms against 1320 ms with 3
+// blocks (80 registers), 1339 ms with 4 (64) and 1734 ms with 1.  The others
+// keep 4 blocks (64 registers; 3 and 80 with two-row Naik links): FP64 is
+// bound by its pipe and FP32 by HBM, where more registers measured no gain.
+template <class A, int NAIK>
+constexpr int dslash_min_blocks() {
+    return std::is_same<A, ArithFF>::value ? 2 : (NAIK == 2 ? 3 : 4);
+}
+
 template <class A, int NAIK, int EPI>
-__global__ void __launch_bounds__(kBlock, NAIK == 2 ? 3 : 4) dslash_kernel(const DslashParams<A> p) {
+__global__ void __launch_bounds__(kBlock, dslash_min_blocks<A, NAIK>()) dslash_kernel(const DslashParams<A> p) {
     // Inside a solver iteration (CG state given): return once the loop has
     // stopped, so that the rest of a captured block of iterations costs nothing.
     if (p.scal && p.scal->done) return;

@@ -723,7 +723,7 @@ def run_learned(args):
     binding.stag_ptnet_destroy(net0)
     binding.stag_ptnet_destroy(net)
     h.close()
-    # plain CG with native FP64 Dirac kernels (the benchmark spec's comparison) on the first 4 sources
+    # plain CG with native FP64 Dirac kernels (the FP64 comparison) on the first 4 sources
     opt64 = binding.stag_default_options()
     opt64.arith = binding.STAG_ARITH_F64
     fat, lng = inputs.asqtad_form_fields(dims, seeds=(31, 32, 33))

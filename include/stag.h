@@ -394,7 +394,7 @@ int stag_ptnet_set_inference_form(stag_ptnet* n, int32_t form);
  * r -= alpha A p, beta = (z_new, r_new - r_old) / (r_old, z_old), p = z + beta p,
  * with A in the handle's FP64-class arithmetic and FP64 vectors.  When the
  * iterated residual falls below tol |b| the true residual is recomputed in
- * native FP64 and judges convergence.  When the smallest |r| so far has not
+ * native FP64 and decides convergence.  When the smallest |r| so far has not
  * dropped by 10 % within 100 iterations: if this cycle reduced the true
  * residual more than 100-fold, flexible CG restarts from the true residual
  * (info->restarts), otherwise plain CG continues from the current x

@@ -29,7 +29,7 @@
 // (stall).  Then the true residual is recomputed in native FP64; a cycle that
 // stalled after cutting the residual 100-fold restarts flexible CG from the
 // current x, any other early stop hands over to plain CG (the solver's
-// fallback), and the FP64 true residual judges the result.
+// fallback), and the FP64 true residual decides the result.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -442,7 +442,7 @@ Outcome solve(stag_ptnet* n, double bnorm2, double tol, long long max_it) {
             break;
         }
         if (use_plain) {
-            // plain FP64-class CG from the current x, judged by its own FP64 residual
+            // plain FP64-class CG from the current x, stopped by its own FP64 residual
             stag_solve_info pi{};
             o.status = handle_solve_packed(h, bnorm2, tol, max_it - o.iters, pi);
             o.iters += pi.iters;

@@ -77,6 +77,29 @@ def test_null_handle_calls(lib):
     assert isinstance(binding.stag_last_error(None), str)
 
 
+def test_null_network_calls(lib):
+    """Every network and flexible-CG entry point rejects a NULL network (or handle)
+    before it touches a device; the inference setters also reject unknown values."""
+    H = ctypes.c_void_p
+    out = H()
+    assert lib.stag_ptnet_create(ctypes.byref(out), None, binding.STAG_ARITH_BF16, 0) == binding.STAG_ERR_INVALID_ARG
+    assert not out.value
+    assert lib.stag_ptnet_create(None, None, binding.STAG_ARITH_BF16, 0) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_ptnet_destroy(None) == binding.STAG_OK
+    assert lib.stag_ptnet_num_weights(None) == 0
+    assert lib.stag_ptnet_apply(None, None, None) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_ptnet_set_weights(None, None, 720) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_ptnet_get_weights(None, None, 720) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_ptnet_train(None, 1, 16, 1e-3, 0, None) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_ptnet_dataset_loss(None, None) == binding.STAG_ERR_INVALID_ARG
+    for form in (binding.STAG_PTNET_COLLAPSED, binding.STAG_PTNET_LAYERED, 2, -1):
+        assert lib.stag_ptnet_set_inference_form(None, form) == binding.STAG_ERR_INVALID_ARG
+    for prec in (binding.STAG_ARITH_BF16, binding.STAG_ARITH_F32, binding.STAG_ARITH_F64):
+        assert lib.stag_ptnet_set_inference_precision(None, prec) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_ptnet_use_tensor_cores(None, 1) == binding.STAG_ERR_INVALID_ARG
+    assert lib.stag_fcg_solve(None, None, None, None, 1e-10, 0, None) == binding.STAG_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("case", ["recon_7", "f64", "no_naik", "zero_scale", "nan_scale", "tiny_scale", "huge_scale",
                                   "link_recon_7"])
 def test_create_rejects_bad_link_forms(lib, case):

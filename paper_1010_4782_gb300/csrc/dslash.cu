@@ -429,6 +429,20 @@ __global__ void __launch_bounds__(kBlock, dslash_min_blocks<A, NAIK>()) dslash_k
     typename A::Acc acc;
     A::zero(acc);
     const bool active = i < p.i1;
+    // the epilogue's operands are loaded before the stencil, so that their
+    // latency overlaps it instead of following it
+    using SrcT = decltype(A::ld(p.src));
+    SrcT srcv[3];
+    double m2 = 0.0;
+    float2 m2_ff = make_float2(0.f, 0.f);
+    if (EPI != EPI_PLAIN) {
+        m2 = (EPI == EPI_CG) ? p.scal->m2 : p.m2;
+        m2_ff = (EPI == EPI_CG) ? p.scal->m2_ff : p.m2_ff;
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) srcv[r] = A::ld(p.src + r * vs + i);
+        }
+    }
     if (active) dslash_site<A, NAIK>(p, i, acc);
     if (EPI == EPI_PLAIN) {
         if (active) {
@@ -438,13 +452,10 @@ __global__ void __launch_bounds__(kBlock, dslash_min_blocks<A, NAIK>()) dslash_k
         return;
     }
     // out = m2 * src - D in
-    const double m2 = (EPI == EPI_CG) ? p.scal->m2 : p.m2;
-    const float2 m2_ff = (EPI == EPI_CG) ? p.scal->m2_ff : p.m2_ff;
     double dot = 0.0;
     if (active) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
-            p.out[r * vs + i] = A::epilogue(acc, r, A::ld(p.src + r * vs + i), m2, m2_ff, dot);
+        for (int r = 0; r < 3; ++r) p.out[r * vs + i] = A::epilogue(acc, r, srcv[r], m2, m2_ff, dot);
     }
     if (EPI == EPI_CG) {
         double total;

@@ -21,6 +21,7 @@
 // x is accumulated in float-float since the last fold and added into the FP64
 // solution by fold_x once per block of iterations.
 #include <algorithm>
+#include <atomic>
 
 #include "ff.cuh"
 #include "stag_kernels.h"
@@ -279,16 +280,18 @@ __global__ void __launch_bounds__(kBlock) from_ff_kernel(Geom g, const float4* _
 
 // ------------------------------------------------------------ launchers
 int resident_wave_blocks() {
-    static int cached[64] = {};
+    static std::atomic<int> cached[64];  // per device ordinal; 0 = not yet queried
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1024;
-    if (!cached[dev]) {
+    int n = cached[dev].load(std::memory_order_relaxed);
+    if (!n) {
         int sms = 0, threads = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-        cached[dev] = sms > 0 && threads > 0 ? sms * std::max(1, threads / kBlock) : 1024;
+        n = sms > 0 && threads > 0 ? sms * std::max(1, threads / kBlock) : 1024;
+        cached[dev].store(n, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return n;
 }
 
 void launch_cg_reset(CgScalars* scal, double threshold, double m2, long long max_iter, cudaStream_t s) {

@@ -954,23 +954,6 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         const size_t nl = (size_t)2 * 4 * 9 * n->g.vs;
         n->links = static_cast<float2*>(palloc(n, nl * sizeof(float2), "allocate links"));
         pt_links_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->fat64, n->links, nl);
-        {
-            // FP16 links for the two-hop inference kernels, divided by s = the power of two
-            // nearest the largest entry (so that they stay inside FP16's normal range)
-            unsigned int* mx = static_cast<unsigned int*>(palloc(n, sizeof(unsigned int), "allocate scratch"));
-            pt_absmax_kernel<<<1024, 256, 0, S(n)>>>(h->fat64, nl, mx);
-            unsigned int bits = 0;
-            pcheck(n, cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, S(n)), "read link maximum");
-            pcheck(n, cudaStreamSynchronize(S(n)), "sync");
-            cudaFree(mx);
-            n->device_bytes -= (long long)sizeof(unsigned int);
-            float amax;
-            std::memcpy(&amax, &bits, sizeof(amax));
-            n->links16_scale = (amax > 0.f && std::isfinite(amax)) ? std::exp2f(std::round(std::log2(amax))) : 1.f;
-            n->links16 = static_cast<__half2*>(palloc(n, nl * sizeof(__half2), "allocate links"));
-            pt_links16_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->fat64, n->links16, nl,
-                                                                          1.0 / n->links16_scale);
-        }
         if (h->lng64) {
             n->lng = static_cast<float2*>(palloc(n, nl * sizeof(float2), "allocate links"));
             pt_links_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->lng64, n->lng, nl);
@@ -985,6 +968,23 @@ int stag_ptnet_create(stag_ptnet** out, stag_handle* h, int32_t precision, uint6
         n->coef = static_cast<float2*>(palloc(n, kCollapsedCoefs * sizeof(float2), "allocate coefficients"));
         n->dot_counter = static_cast<unsigned int*>(palloc(n, sizeof(unsigned int), "allocate counter"));
         n->dot_out = static_cast<double*>(palloc(n, 3 * sizeof(double), "allocate sums"));
+        {
+            // FP16 links for the two-hop inference kernels, divided by s = the power of two
+            // nearest the largest entry (so that they stay inside FP16's normal range)
+            // dot_counter (zero until pt_dots_kernel uses it as its ticket) holds the maximum
+            unsigned int* mx = n->dot_counter;
+            pt_absmax_kernel<<<1024, 256, 0, S(n)>>>(h->fat64, nl, mx);
+            unsigned int bits = 0;
+            pcheck(n, cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, S(n)), "read link maximum");
+            pcheck(n, cudaMemsetAsync(mx, 0, sizeof(unsigned int), S(n)), "reset counter");
+            pcheck(n, cudaStreamSynchronize(S(n)), "sync");
+            float amax;
+            std::memcpy(&amax, &bits, sizeof(amax));
+            n->links16_scale = (amax > 0.f && std::isfinite(amax)) ? std::exp2f(std::round(std::log2(amax))) : 1.f;
+            n->links16 = static_cast<__half2*>(palloc(n, nl * sizeof(__half2), "allocate links"));
+            pt_links16_kernel<<<(int)((nl + 255) / 256), 256, 0, S(n)>>>(h->fat64, n->links16, nl,
+                                                                          1.0 / n->links16_scale);
+        }
         n->grad = static_cast<float2*>(palloc(n, nw * sizeof(float2), "allocate gradients"));
         n->adam_m = static_cast<float*>(palloc(n, 2 * nw * sizeof(float), "allocate optimiser"));
         n->adam_v = static_cast<float*>(palloc(n, 2 * nw * sizeof(float), "allocate optimiser"));

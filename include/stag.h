@@ -390,16 +390,20 @@ int stag_ptnet_use_tensor_cores(stag_ptnet* n, int32_t enable);
 enum { STAG_PTNET_COLLAPSED = 0, STAG_PTNET_LAYERED = 1 };
 int stag_ptnet_set_inference_form(stag_ptnet* n, int32_t form);
 
-/* Flexible CG with z_k = M(r_k): alpha = (r, z) / (p, A p), x += alpha p,
- * r -= alpha A p, beta = (z_new, r_new - r_old) / (r_old, z_old), p = z + beta p,
- * with A in the handle's FP64-class arithmetic and FP64 vectors.  When the
- * iterated residual falls below tol |b| the true residual is recomputed in
- * native FP64 and decides convergence.  When the smallest |r| so far has not
- * dropped by 10 % within 100 iterations: if this cycle reduced the true
- * residual more than 100-fold, flexible CG restarts from the true residual
- * (info->restarts), otherwise plain CG continues from the current x
- * (info->fallbacks); (r, z) <= 0 or (p, A p) <= 0 also hand over to plain CG.
- * The arguments and return codes are those of stag_cg_solve. */
+/* Flexible CG (Notay 2000) with z_k = M(r_k): alpha = (r, z) / (p, A p),
+ * x += alpha p, r -= alpha A p, beta = (z_new, r_new - r_old) / (r_old, z_old)
+ * (formed as -alpha (z_new, A p) / (r_old, z_old), the same quantity),
+ * p = z + beta p, with A and the vectors in the handle's FP64-class arithmetic
+ * (float-float or FP64).  Every scalar stays on the device; blocks of
+ * opt.check_interval iterations run as a CUDA graph and the host reads the
+ * state between blocks.  When the iterated residual falls below tol |b| the
+ * true residual is recomputed in native FP64 and decides convergence.  When
+ * the smallest |r| so far has not dropped by 10 % within 100 iterations: if
+ * this cycle reduced the true residual more than 100-fold, flexible CG
+ * restarts from the true residual (info->restarts), otherwise plain CG
+ * continues from the current x (info->fallbacks); (r, z) <= 0, (p, A p) <= 0
+ * or a non-finite residual also hand over to plain CG.  The arguments and
+ * return codes are those of stag_cg_solve. */
 int stag_fcg_solve(stag_handle* h, stag_ptnet* n, const double* b_even, double* x_even, double tol,
                    int32_t max_iter, stag_solve_info* info);
 

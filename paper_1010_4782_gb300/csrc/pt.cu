@@ -22,6 +22,13 @@
 // W2 = W2^dag (M Hermitian, as flexible CG's short recurrence assumes).  Activations are stored
 // as BF16 (or FP32, for gradient checks) and every sum runs in FP32.
 //
+// Applying the network (stag_ptnet_apply, flexible CG) evaluates by default its
+// exact two-hop form: with the input on even sites and the output read on
+// even sites only paths of zero or two hops survive, so
+// M r = k0 r + sum_{p,q >= 1} H[p][q] T_p T_q r (pt_collapse_kernel forms k0 and
+// H from the weights; pt_chi_kernel and pt_out_site apply them).  The layered
+// evaluation (apply_net, and every training pass) stays available.
+//
 // Gradients (Wirtinger, G = dL/d conj(W)):
 //   output seed  g_3 = A (A d) / |A e|^2 on even sites, 0 on odd sites;
 //   data         g_{l-1}(x, i) = sum_p sum_o conj(W_l[p][o][i]) (T_p^dag g_{l,o})(x),

@@ -65,3 +65,20 @@ def test_all_core_oracle_timing_reproduces_the_oracle():
     assert per_a > 0
     ref = oracle.Operator(fat, lng, 0.1, dims).apply_A(b)
     assert np.array_equal(y, ref)
+
+
+def test_recorded_traffic_matches_the_kernel_sources():
+    """Every ncu traffic figure the bench reports was captured from the kernel
+    sources as they stand: a kernel edited since its capture would make the bench
+    report `traffic: null`, so the capture must be repeated with the edit."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        recorded = json.load(f)
+    assert recorded
+    for key, entry in recorded.items():
+        files = bench.MULTI_SOURCES if key.startswith("multi_") else bench.DSLASH_SOURCES
+        assert entry["source_hash"] == bench.dslash_source_hash(files), key
+        assert entry["dram_bytes_per_launch"] > 0 and entry["how"], key
+        assert bench.recorded_traffic(key, files) == float(entry["dram_bytes_per_launch"]), key

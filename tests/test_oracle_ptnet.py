@@ -185,6 +185,43 @@ def test_fcg_identity_is_cg_and_exact_inverse_is_one_step():
     assert np.linalg.norm(a @ x1 - b) <= 1e-10 * np.linalg.norm(b)
 
 
+def test_fcg_beta_from_the_applied_operator():
+    """The library forms the Polak-Ribiere beta as -alpha (z_new, A p) / (r, z), which
+    equals (z_new, r_new - r) / (r, z) because r_new - r = -alpha A p.  Flexible CG
+    written that way reproduces the oracle's iterates, with a network preconditioner
+    (tied, so that (r, z) > 0) whose z is not a fixed polynomial of A."""
+    dims = (4, 6, 4, 8)
+    fat, lng = inputs.asqtad_form_fields(dims, seeds=(91, 92, 93))
+    op = oracle.Operator(fat, lng, 0.05, dims)
+    net = ptnet.PTNet(fat, dims, ptnet.tie(_random_weights(5)))
+    b = inputs.gaussian_even_source(dims, 94).reshape(-1)
+    k = 12
+
+    def apply_a(v):
+        return op.apply_A(v.reshape(-1, 3)).reshape(-1)
+
+    def apply_m(v):
+        return net.apply(v.reshape(-1, 3)).reshape(-1)
+
+    ref, its = ptnet.fcg(apply_a, apply_m, b, tol=1e-10, max_iter=k)
+    assert its == k
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = apply_m(r)
+    p = z.copy()
+    rz = np.vdot(r, z).real
+    for _ in range(k):
+        q = apply_a(p)
+        alpha = rz / np.vdot(p, q).real
+        x = x + alpha * p
+        r = r - alpha * q
+        z = apply_m(r)
+        beta = -alpha * np.vdot(z, q).real / rz
+        rz = np.vdot(r, z).real
+        p = z + beta * p
+    assert np.linalg.norm(x - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
 # ----------------------------------------------------- loss: free-field closed forms
 def _unit_links(dims):
     lx, ly, lz, lt = dims
